@@ -1,0 +1,168 @@
+/*
+ * xs.h -- C ABI of libxs, the GB300 (sm_103a) semiempirical excited-state library.
+ *
+ * The library computes the lowest singlet excitations of closed-shell
+ * molecules at the CIS (Tamm-Dancoff) and TDHF/RPA level on top of an NDDO
+ * ground state, following arXiv:2505.24807 ("PySEQM 2.0"):
+ *   - ground state: F C = C eps with S = I, restricted closed shell (Eq. 1);
+ *   - RPA eigenproblem [[A,B],[B,A]][X;Y] = omega diag(I,-I)[X;Y] (Eq. rpa_eqn),
+ *     CIS A X = omega X (Eq. cis_eqn);
+ *   - Davidson iterations built on the product
+ *       (A V)_ia = (eps_a - eps_i) V_ia + sum_{mu nu} C_mu,i Ft_mu,nu C_nu,a
+ *     with Ft = sum [(mu nu|lam sig) - (mu lam|nu sig)] R_lam sig and
+ *     R = C_occ V C_vir^T (Eqs. cis_matrix_vector, ftilde), Coulomb on the
+ *     diagonal atom blocks and exchange called with the symmetric and
+ *     antisymmetric parts of R (Section "GPU Implementation");
+ *   - the batched Davidson steps 1-6 of the same section;
+ *   - transition dipoles and oscillator strengths (Section "Results and
+ *     discussion").
+ * Spin: singlet adaptation, A = d eps + 2(ia|jb) - (ij|ab),
+ * B = 2(ia|jb) - (ib|ja) (the paper omits spin indices).
+ *
+ * Conventions
+ *   - Units: energies in eV, lengths in Angstrom, oscillator strengths
+ *     dimensionless (atomic units).
+ *   - AO order = atom order; a heavy atom (Z = 6, 7, 8) carries s, px, py, pz,
+ *     hydrogen (Z = 1) carries s.
+ *   - Matrices are row-major float64.  C is n x n with MOs in columns;
+ *     amplitudes X, Y are nocc x nvir row-major (index i * nvir + a).
+ *   - Every function returns XS_OK (0) or a negative status; the message of
+ *     the last failure is available from xs_last_error().  No C++ exception
+ *     crosses this boundary.
+ *   - The caller owns every host array it passes; the library copies what it
+ *     needs and owns all device memory it allocates.  Pointers documented as
+ *     "host or device" may point to either (unified addressing decides).
+ *   - One context per host thread; calls on one context are not re-entrant.
+ */
+#ifndef XS_H
+#define XS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define XS_OK 0
+#define XS_EINVAL -1     /* bad argument (also odd electron counts: closed shell only) */
+#define XS_ENOMEM -2     /* device allocation failed */
+#define XS_ESCF -3       /* SCF did not converge, or HOMO-LUMO gap below the floor */
+#define XS_EUNSTABLE -4  /* A - B not positive definite: unstable reference for TDHF */
+#define XS_ENOCONV -5    /* Davidson not converged: outputs hold best estimates and residuals */
+#define XS_ECUDA -6      /* CUDA runtime or library error */
+#define XS_ETIMEOUT -7   /* a bounded device-side wait gave up */
+#define XS_ESTATE -8     /* call order violated (e.g. excited before ground state) */
+
+/* methods, precisions, product kinds */
+#define XS_CIS 0
+#define XS_TDHF 1
+
+#define XS_FP64 0   /* every step in float64 */
+#define XS_MIXED 1  /* split-precision tensor-core transforms, float32 G build, float64 subspace */
+
+#define XS_KIND_A 0    /* A X          (CIS)  */
+#define XS_KIND_APB 1  /* (A + B) X    (TDHF) */
+#define XS_KIND_AMB 2  /* (A - B) X    (TDHF) */
+#define XS_KIND_G 3    /* G_CIS(R) = 2 J(R) - K(R) of an n x n AO matrix R */
+
+#define XS_GUESS_PLAIN 0    /* unit vectors on the lowest orbital-energy gaps */
+#define XS_GUESS_LEARNED 1  /* MLP-predicted guess and diagonal shift (plain fallback) */
+
+/* Number of per-element parameter fields, in this order:
+ * Uss, Upp, beta_s, beta_p, gss, gsp, gpp, gp2, hsp, D1, D2, zeta_s, zeta_p
+ * (eV for energies, Angstrom for D1/D2, 1/Angstrom for zeta).  Rows are the
+ * elements H, C, N, O. */
+#define XS_NPARAM 13
+#define XS_NELEM 4
+
+typedef struct xs_ctx xs_ctx;
+
+typedef struct {
+  int n_mol;
+  int max_scf_iter_used; /* largest SCF iteration count over the molecules */
+  double seconds;        /* wall time of the call */
+} xs_gs_info;
+
+typedef struct {
+  int method;        /* XS_CIS or XS_TDHF */
+  int nroots;        /* roots per molecule (>= 1) */
+  double tol;        /* residual 2-norm threshold in eV */
+  int precision;     /* XS_FP64 or XS_MIXED */
+  int guess;         /* XS_GUESS_PLAIN or XS_GUESS_LEARNED */
+  int max_subspace;  /* subspace cap per molecule (0: library default) */
+  int max_iter;      /* Davidson iteration cap (0: library default) */
+  int batched;       /* 1: all molecules advance together, one launch per step */
+} xs_ex_opts;
+
+typedef struct {
+  int iterations;       /* Davidson iterations of the slowest molecule */
+  long long products;   /* trial vectors multiplied (sum over molecules) */
+  int converged;        /* 1 if every root of every molecule converged */
+  int polished;         /* 1 if a float64 Rayleigh-Ritz polish followed a mixed solve */
+  double seconds;       /* wall time of the call */
+  double seconds_products;  /* of which in A*X products */
+} xs_solve_info;
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t to
+ * borrow (the caller keeps ownership) or NULL for a library-owned stream. */
+int xs_create(xs_ctx** out, int device, void* stream);
+int xs_destroy(xs_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none).  Valid until the
+ * next call on the context. */
+const char* xs_last_error(const xs_ctx* ctx);
+
+/* Set the per-element NDDO parameters: `table` is XS_NELEM x XS_NPARAM
+ * float64 (rows H, C, N, O; fields as listed at XS_NPARAM).  The paper's
+ * Hamiltonians (MNDO/AM1/PM3/PM6, Section "Overview") use tabulated sets of
+ * this kind; the library copies the table. */
+int xs_set_params(xs_ctx* ctx, const double* table, int n_elem);
+
+/* Ground state of n_mol molecules: integrals (two-centre multipole model,
+ * one-centre parameters), core Hamiltonian and the closed-shell SCF of Eq. 1
+ * (Pulay DIIS; converged when max|dD| < scf_tol and max|FD - DF| < 10 scf_tol eV).
+ * natoms[n_mol]; Z and xyz (Angstrom, 3 per atom) concatenated over the
+ * molecules, host memory.  Returns XS_ESCF if a molecule does not converge
+ * or its HOMO-LUMO gap is below 0.5 eV, XS_EINVAL for odd electron counts or
+ * unsupported elements. */
+int xs_ground_state(xs_ctx* ctx, int n_mol, const int* natoms, const int* Z, const double* xyz,
+                    double scf_tol, int max_iter, xs_gs_info* info);
+
+/* Sizes of molecule `mol` after xs_ground_state. */
+int xs_get_sizes(const xs_ctx* ctx, int mol, int* nao, int* nocc, int* natoms);
+
+/* Read (get) or replace (set) the MO coefficients C (n x n, row-major, MOs in
+ * columns) and orbital energies eps (n, eV) of molecule `mol`; host or
+ * device pointers.  Replacing them lets a caller run the products on its own
+ * orbitals. */
+int xs_get_orbitals(const xs_ctx* ctx, int mol, double* C, double* eps);
+int xs_set_orbitals(xs_ctx* ctx, int mol, const double* C, const double* eps);
+
+/* Apply a response product to nvec vectors of molecule `mol`
+ * (Eqs. cis_matrix_vector and ftilde):
+ *   kind XS_KIND_A / APB / AMB: in and out are nvec x (nocc*nvir);
+ *   kind XS_KIND_G: in and out are nvec x (n*n) AO matrices, out = 2J(R) - K(R).
+ * `precision` selects XS_FP64 or XS_MIXED.  Host or device pointers. */
+int xs_apply(xs_ctx* ctx, int mol, int kind, int nvec, const double* in, double* out, int precision);
+
+/* Excited states of every molecule loaded by xs_ground_state (paper,
+ * batched Davidson steps 1-6; RPA in the symmetric subspace form of
+ * Stratmann, Scuseria and Frisch).  Outputs are host or device arrays of
+ * n_mol * nroots entries: omega (eV), osc (oscillator strengths), resid
+ * (final residual norms, eV); iters has n_mol entries.  Any output may be
+ * NULL.  Returns XS_ENOCONV with best estimates filled if the iteration cap
+ * is reached, XS_EUNSTABLE if A - B is not positive definite (TDHF). */
+int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, int* iters,
+               double* resid, xs_solve_info* info);
+
+/* Amplitudes of root `root` of molecule `mol` from the last xs_excited:
+ * X (and Y for TDHF; Y may be NULL) of nocc*nvir float64 each, normalised
+ * |X|^2 - |Y|^2 = 1.  `ov` must equal nocc*nvir.  Host or device pointers. */
+int xs_get_amplitudes(const xs_ctx* ctx, int mol, int root, double* X, double* Y, size_t ov);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XS_H */

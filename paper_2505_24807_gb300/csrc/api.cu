@@ -1,0 +1,337 @@
+// C ABI of libxs (declared and documented in include/xs.h).
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "davidson.h"
+#include "kernels.h"
+#include "products.h"
+#include "scf.h"
+
+using xs::Ctx;
+using xs::DevBuf;
+using xs::DevMol;
+using xs::Error;
+
+namespace {
+
+template <typename F>
+int guarded(xs_ctx* ctx, F&& f) {
+  if (!ctx) return XS_EINVAL;
+  ctx->c.err.clear();
+  try {
+    XS_CUDA(cudaSetDevice(ctx->c.device));
+    return f(ctx->c);
+  } catch (const Error& e) {
+    ctx->c.err = e.what();
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    ctx->c.err = "host allocation failed";
+    return XS_ENOMEM;
+  } catch (const std::exception& e) {
+    ctx->c.err = e.what();
+    return XS_ECUDA;
+  }
+}
+
+DevMol& molecule(Ctx& c, int mol) {
+  if (mol < 0 || mol >= static_cast<int>(c.mols.size())) throw Error(XS_EINVAL, "molecule index out of range");
+  DevMol& m = c.mols[mol];
+  if (!m.ready) throw Error(XS_ESTATE, "molecule has no ground state");
+  return m;
+}
+
+template <typename T>
+void upload(cudaStream_t s, DevBuf<T>& d, const std::vector<T>& h) {
+  d.alloc(h.size());
+  if (!h.empty()) XS_CUDA(cudaMemcpyAsync(d.get(), h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
+}
+
+// copy count elements between host or device memory (unified addressing)
+void copy_any(cudaStream_t s, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return;
+  XS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+}
+
+void invalidate_mixed(DevMol& m) {
+  m.CTf_hi.release();
+  m.CTf_lo.release();
+}
+
+}  // namespace
+
+extern "C" {
+
+int xs_create(xs_ctx** out, int device, void* stream) {
+  if (!out) return XS_EINVAL;
+  *out = nullptr;
+  xs_ctx* ctx = nullptr;
+  try {
+    ctx = new xs_ctx();
+  } catch (...) {
+    return XS_ENOMEM;
+  }
+  ctx->c.device = device;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    delete ctx;
+    return XS_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return XS_ECUDA;
+  }
+  if (stream) {
+    ctx->c.stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->c.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return XS_ECUDA;
+    }
+    ctx->c.own_stream = true;
+  }
+  *out = ctx;
+  return XS_OK;
+}
+
+int xs_destroy(xs_ctx* ctx) {
+  if (!ctx) return XS_OK;
+  cudaSetDevice(ctx->c.device);
+  cudaStreamSynchronize(ctx->c.stream);
+  xs::destroy_solver(ctx->c);
+  ctx->c.mols.clear();
+  if (ctx->c.own_stream) cudaStreamDestroy(ctx->c.stream);
+  delete ctx;
+  return XS_OK;
+}
+
+const char* xs_last_error(const xs_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->c.err.c_str();
+}
+
+int xs_set_params(xs_ctx* ctx, const double* table, int n_elem) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (!table || n_elem != XS_NELEM) throw Error(XS_EINVAL, "parameter table must have 4 rows (H, C, N, O)");
+    std::vector<double> t(table, table + XS_NELEM * XS_NPARAM);
+    for (int e = 0; e < XS_NELEM; ++e) {
+      const double* r = table + e * XS_NPARAM;
+      c.par[e] = xs::ElemParams{r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7], r[8], r[9], r[10], r[11], r[12]};
+      if (!(r[4] > 0.0)) throw Error(XS_EINVAL, "gss must be positive");
+    }
+    upload(c.stream, c.d_par, t);
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    c.have_params = true;
+    return XS_OK;
+  });
+}
+
+int xs_ground_state(xs_ctx* ctx, int n_mol, const int* natoms, const int* Z, const double* xyz, double scf_tol,
+                    int max_iter, xs_gs_info* info) {
+  return guarded(ctx, [&](Ctx& c) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!c.have_params) throw Error(XS_ESTATE, "xs_set_params must come first");
+    if (n_mol <= 0 || !natoms || !Z || !xyz) throw Error(XS_EINVAL, "bad molecule arrays");
+    if (!(scf_tol > 0.0)) scf_tol = 1e-10;
+    if (max_iter <= 0) max_iter = 300;
+    cudaStream_t s = c.stream;
+    c.mols.clear();
+    c.mols.resize(n_mol);
+    int off = 0, maxit = 0;
+    for (int i = 0; i < n_mol; ++i) {
+      DevMol& m = c.mols[i];
+      if (natoms[i] <= 0) throw Error(XS_EINVAL, "molecule with no atoms");
+      if (!xs::build_layout(natoms[i], Z + off, xyz + 3 * off, m.L))
+        throw Error(XS_EINVAL, "molecule " + std::to_string(i) + ": odd electron count or unsupported element");
+      off += natoms[i];
+      m.n = m.L.nao;
+      m.o = m.L.nocc;
+      m.v = m.n - m.o;
+      m.np = m.L.nprod;
+      if (m.v <= 0) throw Error(XS_EINVAL, "no virtual orbitals");
+      std::vector<double> W, H;
+      xs::two_centre_supermatrix(m.L, c.par, W);
+      xs::core_hamiltonian(m.L, c.par, W, H);
+      upload(s, m.W, W);
+      upload(s, m.H, H);
+      upload(s, m.ao_atom, m.L.ao_atom);
+      upload(s, m.ao_local, m.L.ao_local);
+      upload(s, m.atom_ao_off, m.L.ao_off);
+      upload(s, m.atom_nao, m.L.nao_atom);
+      upload(s, m.atom_prod_off, m.L.prod_off);
+      upload(s, m.atom_elem, m.L.elem);
+      upload(s, m.xyz, m.L.xyz);
+      XS_CUDA(cudaStreamSynchronize(s));
+      int it = xs::run_scf(c, m, scf_tol, max_iter);
+      maxit = it > maxit ? it : maxit;
+      m.ready = true;
+    }
+    if (info) {
+      info->n_mol = n_mol;
+      info->max_scf_iter_used = maxit;
+      info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return XS_OK;
+  });
+}
+
+int xs_get_sizes(const xs_ctx* cctx, int mol, int* nao, int* nocc, int* natoms) {
+  xs_ctx* ctx = const_cast<xs_ctx*>(cctx);
+  return guarded(ctx, [&](Ctx& c) {
+    DevMol& m = molecule(c, mol);
+    if (nao) *nao = m.n;
+    if (nocc) *nocc = m.o;
+    if (natoms) *natoms = m.L.natoms;
+    return XS_OK;
+  });
+}
+
+int xs_get_orbitals(const xs_ctx* cctx, int mol, double* C, double* eps) {
+  xs_ctx* ctx = const_cast<xs_ctx*>(cctx);
+  return guarded(ctx, [&](Ctx& c) {
+    DevMol& m = molecule(c, mol);
+    const size_t nn = (size_t)m.n * m.n;
+    if (C) {
+      DevBuf<double> t(nn);
+      xs::transpose(c.stream, m.n, m.n, m.CT.get(), t.get());
+      copy_any(c.stream, C, t.get(), nn * sizeof(double));
+      XS_CUDA(cudaStreamSynchronize(c.stream));
+    }
+    if (eps) copy_any(c.stream, eps, m.eps.get(), m.n * sizeof(double));
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    return XS_OK;
+  });
+}
+
+int xs_set_orbitals(xs_ctx* ctx, int mol, const double* C, const double* eps) {
+  return guarded(ctx, [&](Ctx& c) {
+    DevMol& m = molecule(c, mol);
+    if (!C || !eps) throw Error(XS_EINVAL, "C and eps are required");
+    const size_t nn = (size_t)m.n * m.n;
+    DevBuf<double> t(nn);
+    copy_any(c.stream, t.get(), C, nn * sizeof(double));
+    xs::transpose(c.stream, m.n, m.n, t.get(), m.CT.get());
+    copy_any(c.stream, m.eps.get(), eps, m.n * sizeof(double));
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    invalidate_mixed(m);
+    return XS_OK;
+  });
+}
+
+int xs_apply(xs_ctx* ctx, int mol, int kind, int nvec, const double* in, double* out, int precision) {
+  return guarded(ctx, [&](Ctx& c) {
+    DevMol& m = molecule(c, mol);
+    if (nvec < 0 || (nvec > 0 && (!in || !out))) throw Error(XS_EINVAL, "bad vectors");
+    if (precision != XS_FP64 && precision != XS_MIXED) throw Error(XS_EINVAL, "bad precision");
+    if (nvec == 0) return XS_OK;
+    cudaStream_t s = c.stream;
+    const long long ov = (long long)m.o * m.v, nn = (long long)m.n * m.n;
+    if (kind == XS_KIND_G) {
+      DevBuf<double> R((size_t)nvec * nn), G((size_t)nvec * nn);
+      copy_any(s, R.get(), in, sizeof(double) * nvec * nn);
+      xs::gmatrix(c, m, precision, nvec, R.get(), G.get());
+      copy_any(s, out, G.get(), sizeof(double) * nvec * nn);
+    } else if (kind == XS_KIND_A || kind == XS_KIND_APB || kind == XS_KIND_AMB) {
+      DevBuf<double> X((size_t)nvec * ov), Y1((size_t)nvec * ov), Y2;
+      copy_any(s, X.get(), in, sizeof(double) * nvec * ov);
+      if (kind == XS_KIND_A) {
+        xs::products(c, m, XS_CIS, precision, nvec, X.get(), Y1.get(), nullptr);
+        copy_any(s, out, Y1.get(), sizeof(double) * nvec * ov);
+      } else {
+        Y2.alloc((size_t)nvec * ov);
+        xs::products(c, m, XS_TDHF, precision, nvec, X.get(), Y1.get(), Y2.get());
+        copy_any(s, out, (kind == XS_KIND_APB ? Y1 : Y2).get(), sizeof(double) * nvec * ov);
+      }
+    } else {
+      throw Error(XS_EINVAL, "unknown product kind");
+    }
+    XS_CUDA(cudaStreamSynchronize(s));
+    return XS_OK;
+  });
+}
+
+int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, int* iters, double* resid,
+               xs_solve_info* info) {
+  return guarded(ctx, [&](Ctx& c) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!opts) throw Error(XS_EINVAL, "options required");
+    xs_ex_opts o = *opts;
+    if (o.method != XS_CIS && o.method != XS_TDHF) throw Error(XS_EINVAL, "method must be XS_CIS or XS_TDHF");
+    if (o.nroots < 1) throw Error(XS_EINVAL, "nroots must be >= 1");
+    if (!(o.tol > 0.0)) throw Error(XS_EINVAL, "tol must be positive");
+    if (o.precision != XS_FP64 && o.precision != XS_MIXED) throw Error(XS_EINVAL, "bad precision");
+    if (c.mols.empty()) throw Error(XS_ESTATE, "xs_ground_state must come first");
+    const int K = o.nroots;
+    int status = XS_OK;
+    xs_solve_info inf{};
+    inf.converged = 1;
+    double tprod = 0.0;
+    for (size_t i = 0; i < c.mols.size(); ++i) {
+      DevMol& m = molecule(c, static_cast<int>(i));
+      xs::SolveStats st;
+      int rc = xs::davidson(c, m, o, st);
+      if (rc == XS_EUNSTABLE) throw Error(XS_EUNSTABLE, "A - B is not positive definite (molecule " +
+                                                            std::to_string(i) + ")");
+      if (rc != XS_OK) status = rc;
+      inf.iterations = st.iterations > inf.iterations ? st.iterations : inf.iterations;
+      inf.products += st.products;
+      inf.converged = inf.converged && st.converged;
+      tprod += st.seconds_products;
+      const int kk = m.nroots;
+      std::vector<double> pad(K, 0.0);
+      auto put = [&](double* dst, const std::vector<double>& src) {
+        if (!dst) return;
+        std::vector<double> t(K, 0.0);
+        for (int j = 0; j < kk && j < K; ++j) t[j] = src[j];
+        copy_any(c.stream, dst + i * K, t.data(), sizeof(double) * K);
+        XS_CUDA(cudaStreamSynchronize(c.stream));
+      };
+      put(omega, m.omega);
+      put(osc, m.osc);
+      put(resid, m.resid);
+      if (iters) {
+        int itv = m.iterations;
+        copy_any(c.stream, iters + i, &itv, sizeof(int));
+        XS_CUDA(cudaStreamSynchronize(c.stream));
+      }
+    }
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    inf.seconds_products = tprod;
+    if (info) *info = inf;
+    if (status == XS_ENOCONV) c.err = "Davidson did not converge within max_iter";
+    return status;
+  });
+}
+
+int xs_get_amplitudes(const xs_ctx* cctx, int mol, int root, double* X, double* Y, size_t ov) {
+  xs_ctx* ctx = const_cast<xs_ctx*>(cctx);
+  return guarded(ctx, [&](Ctx& c) {
+    DevMol& m = molecule(c, mol);
+    if (m.nroots == 0) throw Error(XS_ESTATE, "no excited-state solution");
+    if (root < 0 || root >= m.nroots) throw Error(XS_EINVAL, "root out of range");
+    const long long n_ov = (long long)m.o * m.v;
+    if ((long long)ov != n_ov) throw Error(XS_EINVAL, "ov must equal nocc * nvir");
+    cudaStream_t s = c.stream;
+    DevBuf<double> t((size_t)n_ov);
+    const double* U = m.U.get() + root * n_ov;
+    const double* W = m.Wv.get() + root * n_ov;
+    if (X) {
+      // X = (U + W) / 2
+      XS_CUDA(cudaMemcpyAsync(t.get(), U, sizeof(double) * n_ov, cudaMemcpyDeviceToDevice, s));
+      xs::axpy(s, n_ov, 1.0, W, t.get());
+      xs::scal(s, n_ov, 0.5, t.get());
+      copy_any(s, X, t.get(), sizeof(double) * n_ov);
+      XS_CUDA(cudaStreamSynchronize(s));
+    }
+    if (Y) {
+      XS_CUDA(cudaMemcpyAsync(t.get(), U, sizeof(double) * n_ov, cudaMemcpyDeviceToDevice, s));
+      xs::axpy(s, n_ov, -1.0, W, t.get());
+      xs::scal(s, n_ov, 0.5, t.get());
+      copy_any(s, Y, t.get(), sizeof(double) * n_ov);
+      XS_CUDA(cudaStreamSynchronize(s));
+    }
+    return XS_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,378 @@
+// Davidson solver of libxs (paper, Section "GPU Implementation", batched
+// steps 1-6), float64 subspace on the device:
+//   1. orthonormal start V (unit vectors on the lowest orbital-energy gaps);
+//   2. products A V (CIS) or (A+B) V, (A-B) V (TDHF);
+//   3. projected matrices, kept incrementally (new columns per iteration), and
+//      their diagonalisation by the Jacobi kernel; lowest k Ritz pairs;
+//   4. Ritz vectors X = V x;
+//   5. residuals r = A X - omega X and their norms; converged roots drop out;
+//   6. diagonal preconditioner r / (omega - d eps), Gram-Schmidt twice against
+//      V, Loewdin orthonormalisation of the new block, append.
+// TDHF uses the symmetric subspace form of Stratmann, Scuseria and Frisch
+// (J. Chem. Phys. 109, 8218 (1998)) -- the paper names Davidson for RPA
+// without the variant: a- = V^T (A-B) V, M = a-^(1/2) a+ a-^(1/2), M z =
+// omega^2 z, X+Y = V a-^(1/2) z / sqrt(omega), X-Y = V a+ (X+Y)~ / omega,
+// residuals (A+B)(X+Y) - omega (X-Y) and (A-B)(X-Y) - omega (X+Y).
+// When V would exceed max_subspace it collapses onto the current Ritz
+// vectors (CIS: the 2k lowest; TDHF: span of X+Y and X-Y), the restart of
+// the paper's Section "Results and discussion".
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "davidson.h"
+#include "kernels.h"
+#include "products.h"
+#include "small.h"
+
+namespace xs {
+
+namespace {
+
+constexpr double kLowdinThresh = 1e-14;
+
+struct Work {
+  DevBuf<double> V, S1, S2;        // Smax x ov
+  DevBuf<double> a1, a2;           // Smax x Smax, upper part valid
+  DevBuf<double> E, Q, w, E2, Q2, w2, Sh, tS;   // S x S work
+  DevBuf<double> cu, cw;           // S x kk coefficient blocks
+  DevBuf<double> X, AX, U, Wv, PU, MW, R1, R2, T;  // kk x ov (T: 2kk x ov)
+  DevBuf<double> C1, C2, C3;       // collapse scratch (2kk x ov)
+  DevBuf<double> nrm, nrm2, omega, Bm;
+  DevBuf<int> flag;
+  DevBuf<long long> idx;
+  DevBuf<double> gws;
+};
+
+void sync_copy(cudaStream_t s, void* dst, const void* src, size_t bytes) {
+  XS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  XS_CUDA(cudaStreamSynchronize(s));
+}
+
+// Orthonormalise the nnew rows of T against V[0:S] (classical Gram-Schmidt
+// twice) and among themselves (Loewdin, dropping directions whose Gram
+// eigenvalue is below kLowdinThresh); writes the kept rows to V[S:].
+int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double* Vout) {
+  cudaStream_t s = c.stream;
+  // unit rows first
+  row_norms(s, nnew, ov, w.T.get(), w.nrm.get());
+  std::vector<double> h(nnew);
+  sync_copy(s, h.data(), w.nrm.get(), sizeof(double) * nnew);
+  for (auto& x : h) x = (x > 0.0) ? 1.0 / x : 0.0;
+  XS_CUDA(cudaMemcpyAsync(w.nrm2.get(), h.data(), sizeof(double) * nnew, cudaMemcpyHostToDevice, s));
+  scale_rows(s, nnew, ov, w.T.get(), w.nrm2.get());
+  for (int pass = 0; pass < 2 && S > 0; ++pass) {
+    gram<double>(s, S, nnew, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.T.get(), static_cast<int>(ov),
+                 w.tS.get(), nnew, 1.0, 0.0, w.gws);
+    gemm<double>(s, true, false, nnew, static_cast<int>(ov), S, -1.0, w.tS.get(), nnew, 0, w.V.get(),
+                 static_cast<int>(ov), 0, 1.0, w.T.get(), static_cast<int>(ov), 0, 1);
+  }
+  gram<double>(s, nnew, nnew, static_cast<int>(ov), w.T.get(), static_cast<int>(ov), w.T.get(), static_cast<int>(ov),
+               w.E2.get(), nnew, 1.0, 0.0, w.gws);
+  jacobi_eig(s, nnew, w.E2.get(), nnew, w.Q2.get(), nnew, w.w2.get(), w.flag.get() + 1);
+  lowdin(s, nnew, w.w2.get(), w.Q2.get(), nnew, kLowdinThresh, w.Bm.get(), nnew, w.flag.get() + 2);
+  int nkeep = 0;
+  sync_copy(s, &nkeep, w.flag.get() + 2, sizeof(int));
+  if (nkeep > 0)
+    gemm<double>(s, false, false, nkeep, static_cast<int>(ov), nnew, 1.0, w.Bm.get(), nnew, 0, w.T.get(),
+                 static_cast<int>(ov), 0, 0.0, Vout, static_cast<int>(ov), 0, 1);
+  return nkeep;
+}
+
+// guess: unit vectors on the nguess lowest eps_a - eps_i (ties: lower i, then a)
+void make_guess(Ctx& c, const DevMol& m, Work& w, int nguess, long long ov) {
+  cudaStream_t s = c.stream;
+  std::vector<double> eps(m.n);
+  sync_copy(s, eps.data(), m.eps.get(), sizeof(double) * m.n);
+  std::vector<long long> order(ov);
+  std::iota(order.begin(), order.end(), 0LL);
+  auto de = [&](long long k) { return eps[m.o + k % m.v] - eps[k / m.v]; };
+  std::partial_sort(order.begin(), order.begin() + nguess, order.end(), [&](long long x, long long y) {
+    double dx = de(x), dy = de(y);
+    return dx < dy || (dx == dy && x < y);
+  });
+  XS_CUDA(cudaMemsetAsync(w.V.get(), 0, sizeof(double) * nguess * ov, s));
+  w.idx.ensure(nguess);
+  XS_CUDA(cudaMemcpyAsync(w.idx.get(), order.data(), sizeof(long long) * nguess, cudaMemcpyHostToDevice, s));
+  unit_vectors(s, nguess, ov, w.idx.get(), w.V.get());
+  XS_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+// f_n = 2/3 omega_n |d_n|^2 (atomic units), d_n = sqrt(2) sum_{mu nu} R^n_{mu nu} <mu|r|nu>,
+// R^n = C_occ U_n C_vir^T, <mu|r|nu> = R_A delta_{mu nu} + one-centre <s|r_i|p_i> = D1.
+__global__ void osc_kernel(int n, const int* __restrict__ ao_atom, const int* __restrict__ ao_local,
+                           const int* __restrict__ atom_elem, const double* __restrict__ xyz,
+                           const double* __restrict__ par, const double* __restrict__ R,
+                           const double* __restrict__ omega, double* __restrict__ f) {
+  const int k = blockIdx.x;
+  const double* Rk = R + (long long)k * n * n;
+  double d[3] = {0.0, 0.0, 0.0};
+  for (int mu = threadIdx.x; mu < n; mu += blockDim.x) {
+    int A = ao_atom[mu];
+    double r = Rk[(long long)mu * n + mu];
+    for (int x = 0; x < 3; ++x) d[x] += r * xyz[3 * A + x];
+    if (ao_local[mu] == 0 && mu + 3 < n && ao_atom[mu + 3] == A && ao_local[mu + 3] == 3) {
+      double D1 = par[atom_elem[A] * XS_NPARAM + 9];
+      for (int x = 0; x < 3; ++x) d[x] += D1 * (Rk[(long long)mu * n + mu + 1 + x] + Rk[(long long)(mu + 1 + x) * n + mu]);
+    }
+  }
+  __shared__ double sh[3][32];
+  for (int x = 0; x < 3; ++x) {
+    double v = d[x];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[x][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    for (int x = 0; x < 3; ++x) {
+      double v = 0.0;
+      for (int j = 0; j < (int)(blockDim.x >> 5); ++j) v += sh[x][j];
+      v *= 1.4142135623730951 / kBohrA;
+      s2 += v * v;
+    }
+    f[k] = (2.0 / 3.0) * (omega[k] / kHartreeEV) * s2;
+  }
+}
+
+void oscillator_strengths(Ctx& c, const DevMol& m, int kk, const double* U, const double* omega_dev, double* f_dev) {
+  cudaStream_t s = c.stream;
+  const int n = m.n, o = m.o, v = m.v;
+  const long long nn = (long long)n * n;
+  c.ws1.ensure((size_t)kk * nn);
+  c.ws4.ensure((size_t)kk * n * (o > v ? o : v));
+  // R_k = C_occ U_k C_vir^T
+  const double* CTocc = m.CT.get();
+  const double* CTvir = m.CT.get() + (size_t)o * n;
+  gemm<double>(s, true, false, n, v, o, 1.0, CTocc, n, 0, U, v, (long long)o * v, 0.0, c.ws4.get(), v,
+               (long long)n * v, kk);
+  gemm<double>(s, false, false, kk * n, n, v, 1.0, c.ws4.get(), v, 0, CTvir, n, 0, 0.0, c.ws1.get(), n, 0, 1);
+  osc_kernel<<<kk, 256, 0, s>>>(n, m.ao_atom.get(), m.ao_local.get(), m.atom_elem.get(), m.xyz.get(),
+                                c.d_par.get(), c.ws1.get(), omega_dev, f_dev);
+  XS_CHECK_LAUNCH();
+}
+
+int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
+  using clk = std::chrono::steady_clock;
+  cudaStream_t s = c.stream;
+  const int o = m.o, v = m.v;
+  const long long ov = (long long)o * v;
+  const bool rpa = opt.method == XS_TDHF;
+  const int kk = static_cast<int>(std::min<long long>(opt.nroots, ov));
+  int Smax = opt.max_subspace > 0 ? opt.max_subspace : std::max(48, (rpa ? 16 : 10) * kk);
+  Smax = static_cast<int>(std::min<long long>(Smax, ov));
+  Smax = std::min(Smax, 1000);
+  const int max_iter = opt.max_iter > 0 ? opt.max_iter : 200;
+  const int nguess = static_cast<int>(std::min<long long>(ov, std::max(2 * kk, kk + 2)));
+  if (Smax < nguess + (rpa ? 2 : 1) * kk) Smax = static_cast<int>(std::min<long long>(ov, nguess + 2 * kk));
+  const int maxnew = rpa ? 2 * kk : kk;
+
+  Work w;
+  w.V.alloc((size_t)Smax * ov);
+  w.S1.alloc((size_t)Smax * ov);
+  if (rpa) w.S2.alloc((size_t)Smax * ov);
+  w.a1.alloc((size_t)Smax * Smax);
+  if (rpa) w.a2.alloc((size_t)Smax * Smax);
+  const size_t SS = (size_t)Smax * Smax;
+  w.E.alloc(SS); w.Q.alloc(SS); w.w.alloc(Smax); w.Sh.alloc(SS); w.tS.alloc(SS);
+  w.E2.alloc(SS); w.Q2.alloc(SS); w.w2.alloc(Smax);
+  w.cu.alloc((size_t)Smax * 2 * kk); w.cw.alloc((size_t)Smax * kk);
+  w.X.alloc((size_t)kk * ov); w.AX.alloc((size_t)kk * ov); w.R1.alloc((size_t)kk * ov);
+  w.T.alloc((size_t)maxnew * ov);
+  if (rpa) { w.R2.alloc((size_t)kk * ov); w.MW.alloc((size_t)kk * ov); }
+  w.nrm.alloc(2 * kk + 2); w.nrm2.alloc(2 * kk + 2); w.omega.alloc(kk); w.Bm.alloc(4 * kk * kk + 4);
+  w.flag.alloc(4);
+  XS_CUDA(cudaMemsetAsync(w.flag.get(), 0, 4 * sizeof(int), s));
+
+  auto t_prod = clk::duration::zero();
+  auto apply = [&](int first, int count) {
+    auto t0 = clk::now();
+    products(c, m, opt.method, opt.precision, count, w.V.get() + first * ov, w.S1.get() + first * ov,
+             rpa ? w.S2.get() + first * ov : nullptr);
+    XS_CUDA(cudaStreamSynchronize(s));
+    t_prod += clk::now() - t0;
+    st.products += count;
+  };
+
+  make_guess(c, m, w, nguess, ov);
+  int S = nguess, Sold = 0;
+  apply(0, S);
+
+  std::vector<double> hw(kk), hn(2 * kk), hn2(kk);
+  std::vector<char> conv(kk, 0);
+  int it = 0;
+  bool converged = false;
+  int status = XS_OK;
+  for (it = 1; it <= max_iter; ++it) {
+    // projected matrices: new columns Sold..S-1 over all rows 0..S-1
+    gram<double>(s, S, S - Sold, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S1.get() + Sold * ov,
+                 static_cast<int>(ov), w.a1.get() + Sold, Smax, 1.0, 0.0, w.gws);
+    if (rpa)
+      gram<double>(s, S, S - Sold, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S2.get() + Sold * ov,
+                   static_cast<int>(ov), w.a2.get() + Sold, Smax, 1.0, 0.0, w.gws);
+    const int k = std::min(kk, S);
+    if (!rpa) {
+      sym_upper(s, S, w.a1.get(), Smax, w.E.get(), S);
+      jacobi_eig(s, S, w.E.get(), S, w.Q.get(), S, w.w.get(), w.flag.get());
+      XS_CUDA(cudaMemcpyAsync(w.omega.get(), w.w.get(), sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
+      // Ritz vectors and residuals
+      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.Q.get(), S, 0, w.V.get(), static_cast<int>(ov), 0,
+                   0.0, w.X.get(), static_cast<int>(ov), 0, 1);
+      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.Q.get(), S, 0, w.S1.get(), static_cast<int>(ov),
+                   0, 0.0, w.AX.get(), static_cast<int>(ov), 0, 1);
+      residual_norms(s, k, ov, w.AX.get(), w.X.get(), w.omega.get(), w.nrm.get(), w.R1.get());
+      sync_copy(s, hw.data(), w.omega.get(), sizeof(double) * k);
+      sync_copy(s, hn.data(), w.nrm.get(), sizeof(double) * k);
+    } else {
+      // a- = Q diag(lam) Q^T, Sh = a-^(1/2)
+      sym_upper(s, S, w.a2.get(), Smax, w.E2.get(), S);
+      jacobi_eig(s, S, w.E2.get(), S, w.Q2.get(), S, w.w2.get(), w.flag.get());
+      double lmin = 0.0;
+      sync_copy(s, &lmin, w.w2.get(), sizeof(double));
+      if (!(lmin > 0.0)) { status = XS_EUNSTABLE; break; }
+      XS_CUDA(cudaMemcpyAsync(w.tS.get(), w.Q2.get(), sizeof(double) * S * S, cudaMemcpyDeviceToDevice, s));
+      scale_cols(s, S, S, w.tS.get(), S, w.w2.get(), 0);
+      gemm<double>(s, false, true, S, S, S, 1.0, w.tS.get(), S, 0, w.Q2.get(), S, 0, 0.0, w.Sh.get(), S, 0, 1);
+      // M = Sh a+ Sh
+      sym_upper(s, S, w.a1.get(), Smax, w.E2.get(), S);   // E2 = a+
+      gemm<double>(s, false, false, S, S, S, 1.0, w.Sh.get(), S, 0, w.E2.get(), S, 0, 0.0, w.tS.get(), S, 0, 1);
+      gemm<double>(s, false, false, S, S, S, 1.0, w.tS.get(), S, 0, w.Sh.get(), S, 0, 0.0, w.E.get(), S, 0, 1);
+      jacobi_eig(s, S, w.E.get(), S, w.Q.get(), S, w.w.get(), w.flag.get());
+      XS_CUDA(cudaMemsetAsync(w.flag.get() + 3, 0, sizeof(int), s));
+      sqrt_roots(s, k, w.w.get(), w.omega.get(), w.flag.get() + 3);
+      // u~ = Sh z / sqrt(omega) (S x k), w~ = a+ u~ / omega
+      gemm<double>(s, false, false, S, k, S, 1.0, w.Sh.get(), S, 0, w.Q.get(), S, 0, 0.0, w.cu.get(), k, 0, 1);
+      scale_cols(s, S, k, w.cu.get(), k, w.omega.get(), 1);
+      gemm<double>(s, false, false, S, k, S, 1.0, w.E2.get(), S, 0, w.cu.get(), k, 0, 0.0, w.cw.get(), k, 0, 1);
+      scale_cols(s, S, k, w.cw.get(), k, w.omega.get(), 2);
+      // X+Y = V u~ (in X), X-Y = V w~ (in AX), (A+B)(X+Y) (R1 scratch -> PU), (A-B)(X-Y) (MW)
+      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cu.get(), k, 0, w.V.get(), static_cast<int>(ov),
+                   0, 0.0, w.X.get(), static_cast<int>(ov), 0, 1);
+      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cw.get(), k, 0, w.V.get(), static_cast<int>(ov),
+                   0, 0.0, w.AX.get(), static_cast<int>(ov), 0, 1);
+      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cu.get(), k, 0, w.S1.get(), static_cast<int>(ov),
+                   0, 0.0, w.R1.get(), static_cast<int>(ov), 0, 1);
+      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cw.get(), k, 0, w.S2.get(), static_cast<int>(ov),
+                   0, 0.0, w.MW.get(), static_cast<int>(ov), 0, 1);
+      // r1 = (A+B)(X+Y) - omega (X-Y), r2 = (A-B)(X-Y) - omega (X+Y)
+      residual_norms(s, k, ov, w.R1.get(), w.AX.get(), w.omega.get(), w.nrm.get(), w.R1.get());
+      residual_norms(s, k, ov, w.MW.get(), w.X.get(), w.omega.get(), w.nrm.get() + kk, w.R2.get());
+      int bad = 0;
+      sync_copy(s, &bad, w.flag.get() + 3, sizeof(int));
+      if (bad) { status = XS_EUNSTABLE; break; }
+      sync_copy(s, hw.data(), w.omega.get(), sizeof(double) * k);
+      sync_copy(s, hn.data(), w.nrm.get(), sizeof(double) * 2 * kk);
+      for (int j = 0; j < k; ++j) hn[j] = std::max(hn[j], hn[kk + j]);
+    }
+    bool all = true;
+    for (int j = 0; j < k; ++j) {
+      if (!std::isfinite(hn[j]) || !std::isfinite(hw[j])) throw Error(XS_ECUDA, "non-finite Davidson residual");
+      conv[j] = hn[j] <= opt.tol;
+      all = all && conv[j];
+    }
+    if (all && k == kk) { converged = true; break; }
+    if (it == max_iter) break;
+    // preconditioned residuals of the unconverged roots
+    if (!rpa) precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R1.get(), w.R1.get());
+    else {
+      precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R1.get(), w.R1.get());
+      precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R2.get(), w.R2.get());
+    }
+    int nnew = 0;
+    for (int j = 0; j < k; ++j) {
+      if (conv[j]) continue;
+      XS_CUDA(cudaMemcpyAsync(w.T.get() + nnew * ov, w.R1.get() + j * ov, sizeof(double) * ov,
+                              cudaMemcpyDeviceToDevice, s));
+      ++nnew;
+      if (rpa) {
+        XS_CUDA(cudaMemcpyAsync(w.T.get() + nnew * ov, w.R2.get() + j * ov, sizeof(double) * ov,
+                                cudaMemcpyDeviceToDevice, s));
+        ++nnew;
+      }
+    }
+    if (S + nnew > Smax) {
+      // collapse onto the current Ritz vectors
+      int nc;
+      if (!rpa) {
+        nc = std::min(S, 2 * kk);
+        w.C1.ensure((size_t)nc * ov);
+        w.C2.ensure((size_t)nc * ov);
+        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.Q.get(), S, 0, w.V.get(), static_cast<int>(ov),
+                     0, 0.0, w.C1.get(), static_cast<int>(ov), 0, 1);
+        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.Q.get(), S, 0, w.S1.get(),
+                     static_cast<int>(ov), 0, 0.0, w.C2.get(), static_cast<int>(ov), 0, 1);
+        XS_CUDA(cudaMemcpyAsync(w.V.get(), w.C1.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
+        XS_CUDA(cudaMemcpyAsync(w.S1.get(), w.C2.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
+        set_diag(s, nc, w.w.get(), w.a1.get(), Smax);
+      } else {
+        // orthonormal basis of span{u~, w~} in subspace coordinates
+        XS_CUDA(cudaMemcpy2DAsync(w.tS.get(), sizeof(double) * 2 * k, w.cu.get(), sizeof(double) * k,
+                                  sizeof(double) * k, S, cudaMemcpyDeviceToDevice, s));
+        XS_CUDA(cudaMemcpy2DAsync(w.tS.get() + k, sizeof(double) * 2 * k, w.cw.get(), sizeof(double) * k,
+                                  sizeof(double) * k, S, cudaMemcpyDeviceToDevice, s));
+        // Gram (2k x 2k) of the coefficient columns
+        gemm<double>(s, true, false, 2 * k, 2 * k, S, 1.0, w.tS.get(), 2 * k, 0, w.tS.get(), 2 * k, 0, 0.0,
+                     w.E2.get(), 2 * k, 0, 1);
+        jacobi_eig(s, 2 * k, w.E2.get(), 2 * k, w.Q2.get(), 2 * k, w.w2.get(), w.flag.get() + 1);
+        lowdin(s, 2 * k, w.w2.get(), w.Q2.get(), 2 * k, kLowdinThresh, w.Bm.get(), 2 * k, w.flag.get() + 2);
+        sync_copy(s, &nc, w.flag.get() + 2, sizeof(int));
+        // Cn = Ycoef Bm^T (S x nc)
+        gemm<double>(s, false, true, S, nc, 2 * k, 1.0, w.tS.get(), 2 * k, 0, w.Bm.get(), 2 * k, 0, 0.0, w.E.get(),
+                     nc, 0, 1);
+        w.C1.ensure((size_t)nc * ov);
+        w.C2.ensure((size_t)nc * ov);
+        w.C3.ensure((size_t)nc * ov);
+        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.E.get(), nc, 0, w.V.get(), static_cast<int>(ov),
+                     0, 0.0, w.C1.get(), static_cast<int>(ov), 0, 1);
+        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.E.get(), nc, 0, w.S1.get(),
+                     static_cast<int>(ov), 0, 0.0, w.C2.get(), static_cast<int>(ov), 0, 1);
+        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.E.get(), nc, 0, w.S2.get(),
+                     static_cast<int>(ov), 0, 0.0, w.C3.get(), static_cast<int>(ov), 0, 1);
+        XS_CUDA(cudaMemcpyAsync(w.V.get(), w.C1.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
+        XS_CUDA(cudaMemcpyAsync(w.S1.get(), w.C2.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
+        XS_CUDA(cudaMemcpyAsync(w.S2.get(), w.C3.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
+        gram<double>(s, nc, nc, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S1.get(),
+                     static_cast<int>(ov), w.a1.get(), Smax, 1.0, 0.0, w.gws);
+        gram<double>(s, nc, nc, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S2.get(),
+                     static_cast<int>(ov), w.a2.get(), Smax, 1.0, 0.0, w.gws);
+      }
+      S = nc;
+      st.collapses += 1;
+    }
+    nnew = std::min(nnew, Smax - S);
+    if (nnew <= 0) break;  // the subspace already spans everything it can hold
+    int nkeep = orthonormalise_append(c, w, S, nnew, ov, w.V.get() + (size_t)S * ov);
+    if (nkeep == 0) break;  // no new direction: stagnation
+    Sold = S;
+    S += nkeep;
+    apply(Sold, nkeep);
+    XS_CUDA(cudaStreamSynchronize(s));
+  }
+  st.iterations = std::min(it, max_iter);
+  st.seconds_products = std::chrono::duration<double>(t_prod).count();
+  if (status != XS_OK) return status;
+
+  // keep the roots: U = X+Y (CIS: X), W = X-Y (CIS: X)
+  m.nroots = kk;
+  m.method = opt.method;
+  m.U.alloc((size_t)kk * ov);
+  m.Wv.alloc((size_t)kk * ov);
+  XS_CUDA(cudaMemcpyAsync(m.U.get(), w.X.get(), sizeof(double) * kk * ov, cudaMemcpyDeviceToDevice, s));
+  XS_CUDA(cudaMemcpyAsync(m.Wv.get(), rpa ? w.AX.get() : w.X.get(), sizeof(double) * kk * ov,
+                          cudaMemcpyDeviceToDevice, s));
+  DevBuf<double> fdev(kk);
+  oscillator_strengths(c, m, kk, m.U.get(), w.omega.get(), fdev.get());
+  m.omega.assign(hw.begin(), hw.begin() + kk);
+  m.resid.assign(hn.begin(), hn.begin() + kk);
+  m.osc.resize(kk);
+  sync_copy(s, m.osc.data(), fdev.get(), sizeof(double) * kk);
+  m.iterations = st.iterations;
+  st.converged = converged;
+  return converged ? XS_OK : XS_ENOCONV;
+}
+
+}  // namespace xs

@@ -1,0 +1,23 @@
+// Davidson solver of libxs (davidson.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace xs {
+
+struct SolveStats {
+  int iterations = 0;
+  long long products = 0;
+  int collapses = 0;
+  bool converged = false;
+  double seconds_products = 0.0;
+};
+
+// Solves molecule m; stores roots, oscillator strengths, residuals and
+// amplitudes in m.  Returns XS_OK, XS_ENOCONV or XS_EUNSTABLE.
+int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st);
+
+// f (device, kk) from amplitudes U (kk x ov, X or X+Y) and omega (device, eV)
+void oscillator_strengths(Ctx& c, const DevMol& m, int kk, const double* U, const double* omega_dev, double* f_dev);
+
+}  // namespace xs

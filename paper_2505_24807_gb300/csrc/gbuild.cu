@@ -1,0 +1,204 @@
+// G(R) build of libxs: the NDDO two-electron contraction of the A*X product.
+//
+// Paper, Section "GPU Implementation", Eq. ftilde:
+//   Ft_{mu nu} = sum_{lam sig} [(mu nu|lam sig) - (mu lam|nu sig)] R_{lam sig},
+// with NDDO leaving Coulomb on the diagonal atom blocks (symmetrised R) and
+// exchange everywhere, contracted with the symmetric and antisymmetric parts
+// of R.  With J(R) = sum (mu nu|lam sig) R and K(R) = sum (mu lam|nu sig) R the
+// singlet products need (spin adaptation, see xs.h):
+//   CIS (and the Fock build at P = D/2):  G  = 2 J(R) - K(R)
+//   TDHF:                                 G+ = 4 J(Rs) - 2 K(Rs) = 4 J(R) - K(R) - K(R^T)
+//                                         G- = -2 K(Ra)          = -K(R) + K(R^T)
+//
+// Three steps per batch of nvec matrices:
+//   1. pack the diagonal atom blocks of R into product vectors r_B[q]
+//      (R_ls + R_sl for l < s, R_ll on the diagonal);
+//   2. two-centre Coulomb J2 = W r with the dense product supermatrix W
+//      (one GEMM over the batch: W is read once per batch);
+//   3. one thread per output element G_{mu lam}: diagonal atom blocks combine
+//      J2 with the closed-form one-centre Coulomb/exchange; off-diagonal blocks
+//      hold the two-centre exchange sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig}.
+#include "kernels.h"
+
+namespace xs {
+
+namespace {
+
+__device__ __forceinline__ int pidx(int a, int b) {
+  // product index of AOs a, b (0 = s, 1..3 = p) on a heavy atom
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  // rows: s: 0 1 2 3 | x: 4 5 6 | y: 7 8 | z: 9
+  const int base[4] = {0, 4, 7, 9};
+  return base[lo] + (hi - lo);
+}
+
+template <typename T>
+__global__ void pack_diag_kernel(int natoms, int n, int nvec, const int* __restrict__ atom_ao_off,
+                                 const int* __restrict__ atom_nao, const int* __restrict__ atom_prod_off,
+                                 const T* __restrict__ R, T* __restrict__ r) {
+  int A = blockIdx.x * blockDim.y + threadIdx.y;
+  int v = threadIdx.x;
+  if (A >= natoms) return;
+  for (; v < nvec; v += blockDim.x) {
+    const T* Rv = R + (long long)v * n * n;
+    int o = atom_ao_off[A], P = atom_prod_off[A];
+    if (atom_nao[A] == 1) {
+      r[(long long)P * nvec + v] = Rv[(long long)o * n + o];
+    } else {
+      for (int a = 0; a < 4; ++a)
+        for (int b = a; b < 4; ++b) {
+          T val = Rv[(long long)(o + a) * n + o + b];
+          if (b != a) val += Rv[(long long)(o + b) * n + o + a];
+          r[(long long)(P + pidx(a, b)) * nvec + v] = val;
+        }
+    }
+  }
+}
+
+// one-centre Coulomb J1 and exchange K1 of element e at AO pair (a, b) of a
+// heavy atom, from the 4x4 diagonal block Rd (row-major) -- closed forms of
+// the parameters gss, gsp, gpp, gp2, hsp and hpp = (gpp - gp2)/2.
+template <typename T>
+__device__ __forceinline__ void one_centre(const T* p, int a, int b, const T Rd[16], T& J1, T& K1ab, T& K1ba) {
+  const T gss = p[4], gsp = p[5], gpp = p[6], gp2 = p[7], hsp = p[8];
+  const T hpp = T(0.5) * (gpp - gp2);
+  auto R = [&](int i, int j) { return Rd[i * 4 + j]; };
+  auto K1 = [&](int x, int y) -> T {
+    if (x == 0 && y == 0) return gss * R(0, 0) + hsp * (R(1, 1) + R(2, 2) + R(3, 3));
+    if (x == 0) return gsp * R(0, y) + hsp * R(y, 0);
+    if (y == 0) return gsp * R(x, 0) + hsp * R(0, x);
+    if (x == y) {
+      T s = T(0);
+      for (int j = 1; j < 4; ++j) if (j != x) s += R(j, j);
+      return hsp * R(0, 0) + gpp * R(x, x) + hpp * s;
+    }
+    return gp2 * R(x, y) + hpp * R(y, x);
+  };
+  if (a == 0 && b == 0) {
+    J1 = gss * R(0, 0) + gsp * (R(1, 1) + R(2, 2) + R(3, 3));
+  } else if (a == 0 || b == 0) {
+    int i = a + b;
+    J1 = hsp * (R(0, i) + R(i, 0));
+  } else if (a == b) {
+    T s = T(0);
+    for (int j = 1; j < 4; ++j) if (j != a) s += R(j, j);
+    J1 = gsp * R(0, 0) + gpp * R(a, a) + gp2 * s;
+  } else {
+    J1 = hpp * (R(a, b) + R(b, a));
+  }
+  K1ab = K1(a, b);
+  K1ba = K1(b, a);
+}
+
+template <typename T, GMode MODE>
+__global__ void __launch_bounds__(256) assemble_kernel(int n, int np, int nvec, const int* __restrict__ ao_atom,
+                                                       const int* __restrict__ ao_local,
+                                                       const int* __restrict__ atom_ao_off,
+                                                       const int* __restrict__ atom_nao,
+                                                       const int* __restrict__ atom_prod_off,
+                                                       const int* __restrict__ atom_elem,
+                                                       const double* __restrict__ par, const T* __restrict__ W,
+                                                       const T* __restrict__ J2, const T* __restrict__ Rall,
+                                                       T* __restrict__ Gall, T* __restrict__ Gmall) {
+  const int lam = blockIdx.x * 32 + threadIdx.x;
+  const int mu = blockIdx.y * 8 + threadIdx.y;
+  const int v = blockIdx.z;
+  if (lam >= n || mu >= n) return;
+  const T* R = Rall + (long long)v * n * n;
+  const int A = ao_atom[mu], B = ao_atom[lam];
+  const int a = ao_local[mu], b = ao_local[lam];
+  const int oA = atom_ao_off[A], oB = atom_ao_off[B];
+  const int nA = atom_nao[A], nB = atom_nao[B];
+  const int PA = atom_prod_off[A], PB = atom_prod_off[B];
+  T g, gm = T(0);
+  if (A == B) {
+    const double* pd = par + atom_elem[A] * XS_NPARAM;
+    T p[XS_NPARAM];
+#pragma unroll
+    for (int i = 0; i < XS_NPARAM; ++i) p[i] = T(pd[i]);
+    T J1, K1ab, K1ba;
+    if (nA == 1) {
+      T r00 = R[(long long)oA * n + oA];
+      J1 = p[4] * r00;
+      K1ab = K1ba = p[4] * r00;
+    } else {
+      T Rd[16];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Rd[i * 4 + j] = R[(long long)(oA + i) * n + oA + j];
+      one_centre<T>(p, a, b, Rd, J1, K1ab, K1ba);
+    }
+    const int pab = (nA == 4) ? pidx(a, b) : 0;
+    const T J = J1 + J2[(long long)(PA + pab) * nvec + v];
+    if (MODE == G_CIS) {
+      g = T(2) * J - K1ab;
+    } else {
+      g = T(4) * J - (K1ab + K1ba);
+      gm = -(K1ab - K1ba);
+    }
+  } else {
+    // K(R)_{mu lam} = sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig}
+    // K(R^T)_{mu lam} = sum (mu nu|lam sig) R_{sig nu}
+    T kr = T(0), krt = T(0);
+    for (int nu = 0; nu < nA; ++nu) {
+      const int p = (nA == 4) ? pidx(a, nu) : 0;
+      const T* Wrow = W + (long long)(PA + p) * np + PB;
+      for (int sg = 0; sg < nB; ++sg) {
+        const int q = (nB == 4) ? pidx(b, sg) : 0;
+        const T w = Wrow[q];
+        kr = fma(w, R[(long long)(oA + nu) * n + oB + sg], kr);
+        if (MODE == G_RPA) krt = fma(w, R[(long long)(oB + sg) * n + oA + nu], krt);
+      }
+    }
+    if (MODE == G_CIS) {
+      g = -kr;
+    } else {
+      g = -(kr + krt);
+      gm = -(kr - krt);
+    }
+  }
+  Gall[(long long)v * n * n + (long long)mu * n + lam] = g;
+  if (MODE == G_RPA) Gmall[(long long)v * n * n + (long long)mu * n + lam] = gm;
+}
+
+}  // namespace
+
+template <typename T>
+void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* R, T* G, T* Gm,
+            DevBuf<T>& ws) {
+  if (nvec <= 0) return;
+  const int n = m.n, np = m.np;
+  ws.ensure((size_t)2 * np * nvec);
+  T* r = ws.get();
+  T* J2 = ws.get() + (size_t)np * nvec;
+  {
+    dim3 block(8, 32);
+    dim3 grid((m.L.natoms + 31) / 32);
+    pack_diag_kernel<T><<<grid, block, 0, s>>>(m.L.natoms, n, nvec, m.atom_ao_off.get(), m.atom_nao.get(),
+                                                m.atom_prod_off.get(), R, r);
+    XS_CHECK_LAUNCH();
+  }
+  const T* W = nullptr;
+  if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(m.W.get());
+  else W = reinterpret_cast<const T*>(m.Wf.get());
+  gemm<T>(s, false, false, np, nvec, np, T(1), W, np, 0, r, nvec, 0, T(0), J2, nvec, 0, 1);
+  dim3 block(32, 8);
+  dim3 grid((n + 31) / 32, (n + 7) / 8, nvec);
+  if (mode == G_CIS)
+    assemble_kernel<T, G_CIS><<<grid, block, 0, s>>>(n, np, nvec, m.ao_atom.get(), m.ao_local.get(),
+                                                     m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
+                                                     m.atom_elem.get(), d_par, W, J2, R, G, nullptr);
+  else
+    assemble_kernel<T, G_RPA><<<grid, block, 0, s>>>(n, np, nvec, m.ao_atom.get(), m.ao_local.get(),
+                                                     m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
+                                                     m.atom_elem.get(), d_par, W, J2, R, G, Gm);
+  XS_CHECK_LAUNCH();
+}
+
+template void gbuild<double>(cudaStream_t, const DevMol&, const double*, GMode, int, const double*, double*,
+                             double*, DevBuf<double>&);
+template void gbuild<float>(cudaStream_t, const DevMol&, const double*, GMode, int, const float*, float*, float*,
+                            DevBuf<float>&);
+
+}  // namespace xs

@@ -1,0 +1,56 @@
+// Host-side launchers of libxs's CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace xs {
+
+// ---- dense algebra (gemm.cu) ------------------------------------------------
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b], row-major storage; op(A) is M x K,
+// op(B) is K x N.  transA: A is stored K x M; transB: B is stored N x K.
+template <typename T>
+void gemm(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha, const T* A,
+          int lda, long long sA, const T* B, int ldb, long long sB, T beta, T* C, int ldc,
+          long long sC, int batch = 1);
+
+// C (M x N) = alpha A (M x L) B(N x L)^T + beta C for long L (split over L).
+template <typename T>
+void gram(cudaStream_t s, int M, int N, int L, const T* A, int lda, const T* B, int ldb, T* C,
+          int ldc, T alpha, T beta, DevBuf<T>& ws);
+
+// ---- G(R) build (gbuild.cu) -------------------------------------------------
+enum GMode { G_CIS = 0, G_RPA = 1 };
+// nvec AO matrices R (n x n each, row-major, consecutive) -> G (CIS/Fock:
+// 2J(R) - K(R)) or G+ = 4J(Rs) - 2K(Rs) and G- = -2K(Ra) (RPA).
+// Gm is unused for G_CIS.  ws: scratch of at least 2 * np * nvec.
+template <typename T>
+void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* R,
+            T* G, T* Gm, DevBuf<T>& ws);
+
+// ---- elementwise helpers (vec.cu) ---------------------------------------------
+template <typename T>
+void add_diag_term(cudaStream_t s, int nvec, int o, int v, const double* eps, const T* X, T* Y);
+void precondition(cudaStream_t s, int nvec, int o, int v, const double* eps, const double* omega,
+                  const double* R, double* T);
+void residual_norms(cudaStream_t s, int nvec, long long len, const double* A, const double* B,
+                    const double* omega, double* out_norm, double* R);
+void row_norms(cudaStream_t s, int nvec, long long len, const double* X, double* out_norm);
+void scale_rows(cudaStream_t s, int nvec, long long len, double* X, const double* scale);
+void convert_d2f(cudaStream_t s, long long n, const double* a, float* b);
+void convert_f2d(cudaStream_t s, long long n, const float* a, double* b);
+void split_d2f(cudaStream_t s, long long n, const double* a, float* hi, float* lo);
+void fill(cudaStream_t s, long long n, double* a, double v);
+void axpy(cudaStream_t s, long long n, double alpha, const double* x, double* y);
+void scal(cudaStream_t s, long long n, double alpha, double* x);
+void max_abs(cudaStream_t s, long long n, const double* a, double* out);   // out: one device double
+void transpose(cudaStream_t s, int rows, int cols, const double* a, double* b);
+
+// ---- small dense eigenproblems (small.cu) -----------------------------------
+// Symmetric eigen-decomposition of batch matrices (n <= 512) by cyclic Jacobi
+// in one CTA each: A (n x n, lda) is overwritten, V gets the eigenvectors in
+// columns (ldv), w the eigenvalues in ascending order.
+void jacobi_eig(cudaStream_t s, int n, double* A, int lda, double* V, int ldv, double* w, int* info);
+
+}  // namespace xs

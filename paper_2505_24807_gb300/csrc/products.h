@@ -1,0 +1,17 @@
+// A*X products of libxs (products.cu, tc.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace xs {
+
+// Y1 = A X (CIS) or Y1 = (A+B) X, Y2 = (A-B) X (TDHF) for nvec vectors
+// X (nvec x nocc x nvir, float64, device).  precision: XS_FP64 or XS_MIXED.
+void products(Ctx& c, DevMol& m, int method, int precision, int nvec, const double* X, double* Y1, double* Y2);
+void products_fp64(Ctx& c, const DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2);
+// G_CIS(R) of nvec AO matrices (float64 device arrays)
+void gmatrix(Ctx& c, const DevMol& m, int precision, int nvec, const double* R, double* G);
+// vectors per pass of the AO work arrays
+int product_batch(const DevMol& m);
+
+}  // namespace xs

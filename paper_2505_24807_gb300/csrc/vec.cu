@@ -1,0 +1,212 @@
+// Elementwise and reduction kernels of libxs (Davidson steps 4-6 of the
+// paper's Section "GPU Implementation": residuals, norms, diagonal
+// preconditioner; and the orbital-energy term of Eq. cis_matrix_vector).
+#include <cfloat>
+
+#include "kernels.h"
+
+namespace xs {
+
+namespace {
+
+template <typename T>
+__global__ void diag_term_kernel(int nvec, int o, int v, const double* __restrict__ eps, const T* __restrict__ X,
+                                 T* __restrict__ Y) {
+  long long ov = (long long)o * v;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ov * nvec) return;
+  long long e = idx % ov;
+  int i = static_cast<int>(e / v), a = static_cast<int>(e % v);
+  double de = eps[o + a] - eps[i];
+  Y[idx] = static_cast<T>(static_cast<double>(Y[idx]) + de * static_cast<double>(X[idx]));
+}
+
+// t = r / (omega - d eps), denominator magnitude clamped to >= 1e-4 eV
+__global__ void precond_kernel(int nvec, int o, int v, const double* __restrict__ eps,
+                               const double* __restrict__ omega, const double* __restrict__ R,
+                               double* __restrict__ Tt) {
+  long long ov = (long long)o * v;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ov * nvec) return;
+  int k = static_cast<int>(idx / ov);
+  long long e = idx % ov;
+  int i = static_cast<int>(e / v), a = static_cast<int>(e % v);
+  double d = omega[k] - (eps[o + a] - eps[i]);
+  if (fabs(d) < 1e-4) d = (d < 0.0) ? -1e-4 : 1e-4;
+  Tt[idx] = R[idx] / d;
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  return x;
+}
+
+// per row k: R = A - omega_k B (if R != nullptr), out = ||A - omega_k B||_2
+__global__ void resid_kernel(long long len, const double* __restrict__ A, const double* __restrict__ B,
+                             const double* __restrict__ omega, double* __restrict__ out, double* __restrict__ R) {
+  int k = blockIdx.y;
+  const double* a = A + (long long)k * len;
+  const double* b = B ? B + (long long)k * len : nullptr;
+  double w = omega ? omega[k] : 0.0;
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    double r = b ? (a[i] - w * b[i]) : a[i];
+    if (R) R[(long long)k * len + i] = r;
+    s += r * r;
+  }
+  __shared__ double sh[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) atomicAdd(out + k, t);
+  }
+}
+
+__global__ void sqrt_kernel(int n, double* x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = sqrt(x[i]);
+}
+
+__global__ void scale_rows_kernel(int nvec, long long len, double* X, const double* __restrict__ scale) {
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= len * nvec) return;
+  X[idx] *= scale[idx / len];
+}
+
+__global__ void d2f_kernel(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = static_cast<float>(a[i]);
+}
+__global__ void f2d_kernel(long long n, const float* __restrict__ a, double* __restrict__ b) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = static_cast<double>(a[i]);
+}
+__global__ void split_kernel(long long n, const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    float h = static_cast<float>(a[i]);
+    hi[i] = h;
+    lo[i] = static_cast<float>(a[i] - static_cast<double>(h));
+  }
+}
+__global__ void fill_kernel(long long n, double* a, double v) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+__global__ void scal_kernel(long long n, double alpha, double* __restrict__ x) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= alpha;
+}
+__global__ void axpy_kernel(long long n, double alpha, const double* __restrict__ x, double* __restrict__ y) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += alpha * x[i];
+}
+__global__ void maxabs_kernel(long long n, const double* __restrict__ a, unsigned long long* out) {
+  double m = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(a[i]));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  // non-negative doubles order like their bit patterns
+  if ((threadIdx.x & 31) == 0) atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(m)));
+}
+__global__ void transpose_kernel(int rows, int cols, const double* __restrict__ a, double* __restrict__ b) {
+  __shared__ double tile[32][33];
+  int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 32 + threadIdx.y;
+  for (int j = 0; j < 32; j += 8)
+    if (x < cols && y + j < rows) tile[threadIdx.y + j][threadIdx.x] = a[(long long)(y + j) * cols + x];
+  __syncthreads();
+  x = blockIdx.y * 32 + threadIdx.x;
+  y = blockIdx.x * 32 + threadIdx.y;
+  for (int j = 0; j < 32; j += 8)
+    if (x < rows && y + j < cols) b[(long long)(y + j) * rows + x] = tile[threadIdx.x][threadIdx.y + j];
+}
+
+}  // namespace
+
+template <typename T>
+void add_diag_term(cudaStream_t s, int nvec, int o, int v, const double* eps, const T* X, T* Y) {
+  long long n = (long long)nvec * o * v;
+  if (n == 0) return;
+  diag_term_kernel<T><<<grid1(n, 256), 256, 0, s>>>(nvec, o, v, eps, X, Y);
+  XS_CHECK_LAUNCH();
+}
+template void add_diag_term<double>(cudaStream_t, int, int, int, const double*, const double*, double*);
+template void add_diag_term<float>(cudaStream_t, int, int, int, const double*, const float*, float*);
+
+void precondition(cudaStream_t s, int nvec, int o, int v, const double* eps, const double* omega, const double* R,
+                  double* T) {
+  long long n = (long long)nvec * o * v;
+  if (n == 0) return;
+  precond_kernel<<<grid1(n, 256), 256, 0, s>>>(nvec, o, v, eps, omega, R, T);
+  XS_CHECK_LAUNCH();
+}
+
+void residual_norms(cudaStream_t s, int nvec, long long len, const double* A, const double* B, const double* omega,
+                    double* out_norm, double* R) {
+  if (nvec == 0) return;
+  XS_CUDA(cudaMemsetAsync(out_norm, 0, sizeof(double) * nvec, s));
+  int blocks = static_cast<int>(std::min<long long>(256, (len + 255) / 256));
+  resid_kernel<<<dim3(blocks, nvec), 256, 0, s>>>(len, A, B, omega, out_norm, R);
+  XS_CHECK_LAUNCH();
+  sqrt_kernel<<<grid1(nvec, 64), 64, 0, s>>>(nvec, out_norm);
+  XS_CHECK_LAUNCH();
+}
+
+void row_norms(cudaStream_t s, int nvec, long long len, const double* X, double* out_norm) {
+  residual_norms(s, nvec, len, X, nullptr, nullptr, out_norm, nullptr);
+}
+
+void scale_rows(cudaStream_t s, int nvec, long long len, double* X, const double* scale) {
+  long long n = (long long)nvec * len;
+  if (n == 0) return;
+  scale_rows_kernel<<<grid1(n, 256), 256, 0, s>>>(nvec, len, X, scale);
+  XS_CHECK_LAUNCH();
+}
+
+void convert_d2f(cudaStream_t s, long long n, const double* a, float* b) {
+  if (n == 0) return;
+  d2f_kernel<<<grid1(n, 256), 256, 0, s>>>(n, a, b);
+  XS_CHECK_LAUNCH();
+}
+void convert_f2d(cudaStream_t s, long long n, const float* a, double* b) {
+  if (n == 0) return;
+  f2d_kernel<<<grid1(n, 256), 256, 0, s>>>(n, a, b);
+  XS_CHECK_LAUNCH();
+}
+void split_d2f(cudaStream_t s, long long n, const double* a, float* hi, float* lo) {
+  if (n == 0) return;
+  split_kernel<<<grid1(n, 256), 256, 0, s>>>(n, a, hi, lo);
+  XS_CHECK_LAUNCH();
+}
+void fill(cudaStream_t s, long long n, double* a, double v) {
+  if (n == 0) return;
+  fill_kernel<<<grid1(n, 256), 256, 0, s>>>(n, a, v);
+  XS_CHECK_LAUNCH();
+}
+void axpy(cudaStream_t s, long long n, double alpha, const double* x, double* y) {
+  if (n == 0) return;
+  axpy_kernel<<<grid1(n, 256), 256, 0, s>>>(n, alpha, x, y);
+  XS_CHECK_LAUNCH();
+}
+void scal(cudaStream_t s, long long n, double alpha, double* x) {
+  if (n == 0) return;
+  scal_kernel<<<grid1(n, 256), 256, 0, s>>>(n, alpha, x);
+  XS_CHECK_LAUNCH();
+}
+void max_abs(cudaStream_t s, long long n, const double* a, double* out) {
+  XS_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
+  if (n == 0) return;
+  int blocks = static_cast<int>(std::min<long long>(1024, (n + 255) / 256));
+  maxabs_kernel<<<blocks, 256, 0, s>>>(n, a, reinterpret_cast<unsigned long long*>(out));
+  XS_CHECK_LAUNCH();
+}
+void transpose(cudaStream_t s, int rows, int cols, const double* a, double* b) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(rows, cols, a, b);
+  XS_CHECK_LAUNCH();
+}
+
+}  // namespace xs

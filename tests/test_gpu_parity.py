@@ -1,0 +1,151 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: float64 products agree to 1e-11 relative (rounding order only);
+mixed-precision products to 3e-5 relative; excitation energies to 1e-6 eV in
+float64 and 1e-5 eV in mixed precision (the stated target); oscillator
+strengths to 1e-4 absolute.
+"""
+import numpy as np
+import pytest
+
+import molgen
+from tests.gpu_common import context, oracle_ground_state, rel_err
+
+pytestmark = pytest.mark.gpu
+
+xs = pytest.importorskip("paper_2505_24807_gb300.xs")
+
+
+@pytest.fixture(scope="module")
+def small_case():
+    params = molgen.make_params(0)
+    Z, xyz = molgen.config_small(1)
+    mol, ints, res = oracle_ground_state(Z, xyz, params)
+    ctx = context(params)
+    xs.xs_ground_state(ctx.h, [(Z, xyz)])
+    yield dict(params=params, Z=Z, xyz=xyz, mol=mol, ints=ints, res=res, ctx=ctx)
+    ctx.close()
+
+
+def test_scf_matches_oracle(small_case):
+    c = small_case
+    Cg, eps = xs.xs_get_orbitals(c["ctx"].h, 0)
+    assert np.abs(eps - c["res"].eps).max() < 1e-7
+    o = c["mol"].nocc
+    D = 2 * Cg[:, :o] @ Cg[:, :o].T
+    assert np.abs(D - c["res"].D).max() < 1e-7
+
+
+def test_gbuild_matches_oracle(small_case):
+    from oracle import excited
+    c = small_case
+    n = c["mol"].nao
+    R = np.random.default_rng(5).uniform(-1, 1, size=(3, n, n))
+    G = xs.xs_apply(c["ctx"].h, 0, xs.XS_KIND_G, R)
+    ref = excited.apply_kind(c["mol"], c["ints"], None, None, None, R, "G")
+    assert rel_err(G, ref) < 1e-12
+
+
+@pytest.mark.parametrize("kind,okind", [(0, "A"), (1, "ApB"), (2, "AmB")])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_products_match_oracle(small_case, kind, okind, precision):
+    from oracle import excited
+    c = small_case
+    mol, res = c["mol"], c["res"]
+    # run on the oracle's own orbitals so elementwise comparison is meaningful
+    xs.xs_set_orbitals(c["ctx"].h, 0, res.C, res.eps)
+    X = molgen.trial_vectors(7, 4, mol.nocc, mol.nvir)
+    Y = xs.xs_apply(c["ctx"].h, 0, kind, X.reshape(4, -1), precision=precision).reshape(X.shape)
+    ref = excited.apply_kind(mol, c["ints"], res.C, res.eps, mol.nocc, X, okind)
+    tol = 1e-11 if precision == 0 else 3e-5
+    assert rel_err(Y, ref) < tol
+
+
+@pytest.mark.parametrize("method", ["CIS", "RPA"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_roots_match_bruteforce(small_case, method, precision):
+    from oracle import excited, nddo
+    c = small_case
+    mol, res = c["mol"], c["res"]
+    eri = nddo.full_eri(mol, c["ints"])
+    A, B = excited.explicit_AB(res.eps, res.C, mol.nocc, eri)
+    k = 5
+    if method == "CIS":
+        w, V = excited.cis_bruteforce(A, k)
+        f = excited.oscillator_strengths(mol, res.C, mol.nocc, w, V.T.reshape(k, mol.nocc, mol.nvir))
+    else:
+        w, U, W = excited.rpa_bruteforce(A, B, k)
+        f = excited.oscillator_strengths(mol, res.C, mol.nocc, w, U.T.reshape(k, mol.nocc, mol.nvir))
+    ctx = context(c["params"])
+    try:
+        xs.xs_ground_state(ctx.h, [(c["Z"], c["xyz"])])
+        out = xs.xs_excited(ctx.h, method=xs.XS_CIS if method == "CIS" else xs.XS_TDHF, nroots=k, tol=1e-6,
+                            precision=precision)
+    finally:
+        ctx.close()
+    tol = 1e-6 if precision == 0 else 1e-5
+    assert np.abs(out["omega"][0] - w).max() < tol
+    assert np.abs(out["osc"][0] - f).max() < 1e-4
+    assert out["info"]["converged"] == 1
+
+
+def test_amplitudes_normalised(small_case):
+    c = small_case
+    ctx = context(c["params"])
+    try:
+        xs.xs_ground_state(ctx.h, [(c["Z"], c["xyz"])])
+        xs.xs_excited(ctx.h, method=xs.XS_TDHF, nroots=3, tol=1e-7)
+        for r in range(3):
+            X, Y = xs.xs_get_amplitudes(ctx.h, 0, r)
+            assert abs(np.sum(X * X) - np.sum(Y * Y) - 1.0) < 1e-8
+    finally:
+        ctx.close()
+
+
+def test_h2_two_orbital_edge_case():
+    from oracle import excited, nddo, scf
+    params = molgen.make_params(0)
+    Z = np.array([1, 1])
+    xyz = np.array([[0.0, 0.0, 0.0], [0.9, 0.0, 0.0]])
+    mol = nddo.Molecule(Z, xyz, params)
+    ints = nddo.Integrals(mol)
+    res = scf.scf(mol, ints, min_gap=0.0)
+    ref = excited.solve(mol, ints, res, "RPA", 1, tol=1e-10)
+    ctx = context(params)
+    try:
+        xs.xs_ground_state(ctx.h, [(Z, xyz)])
+        out = xs.xs_excited(ctx.h, method=xs.XS_TDHF, nroots=3, tol=1e-9)
+    finally:
+        ctx.close()
+    assert abs(out["omega"][0, 0] - ref["omega"][0]) < 1e-9
+    assert np.all(out["omega"][0, 1:] == 0.0)   # only one root exists (ov = 1)
+
+
+def test_odd_electron_count_rejected():
+    params = molgen.make_params(0)
+    ctx = context(params)
+    try:
+        with pytest.raises(xs.XSError) as e:
+            xs.xs_ground_state(ctx.h, [(np.array([1, 1, 1]), np.array([[0, 0, 0], [1.0, 0, 0], [0, 1.2, 0]]))])
+        assert e.value.status == xs.XS_EINVAL
+    finally:
+        ctx.close()
+
+
+def test_unstable_reference_reported():
+    # seed 8 of the 12-heavy-atom chain has A - B with a negative eigenvalue
+    from oracle import excited, nddo
+    params = molgen.make_params(0)
+    Z, xyz = molgen.config_small(8)
+    mol, ints, res = oracle_ground_state(Z, xyz, params)
+    A, B = excited.explicit_AB(res.eps, res.C, mol.nocc, nddo.full_eri(mol, ints))
+    if np.linalg.eigvalsh(A - B)[0] > 0:
+        pytest.skip("reference is stable for this seed")
+    ctx = context(params)
+    try:
+        xs.xs_ground_state(ctx.h, [(Z, xyz)])
+        with pytest.raises(xs.XSError) as e:
+            xs.xs_excited(ctx.h, method=xs.XS_TDHF, nroots=5, tol=1e-6)
+        assert e.value.status == xs.XS_EUNSTABLE
+    finally:
+        ctx.close()
