@@ -161,6 +161,24 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
  * |X|^2 - |Y|^2 = 1.  `ov` must equal nocc*nvir.  Host or device pointers. */
 int xs_get_amplitudes(const xs_ctx* ctx, int mol, int root, double* X, double* Y, size_t ov);
 
+/* Per-kernel timing.  xs_profile(ctx, 1) clears and enables it: every
+ * instrumented kernel launch of later calls is bracketed by CUDA events on
+ * the launching stream; xs_profile(ctx, 0) disables it.  xs_profile_read
+ * synchronises the context's stream and copies up to max_entries entries
+ * (one per kernel name: launches, summed device milliseconds, summed
+ * algorithmic bytes and flops) and the number of entries into *count.  No
+ * counterpart in the paper (measurement plumbing). */
+typedef struct {
+  char name[32];
+  int launches;
+  double ms;
+  double bytes;
+  double flops;
+} xs_prof_entry;
+
+int xs_profile(xs_ctx* ctx, int enable);
+int xs_profile_read(xs_ctx* ctx, xs_prof_entry* out, int max_entries, int* count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,21 +68,52 @@ def _unit_sphere(rng):
             return p / np.sqrt(r2)
 
 
-def _balance_elements(z_heavy, target_valence, rng):
-    """Turn C<->N<->O one step at a time until the summed bonding valence
-    equals ``target_valence`` (or no further step is possible)."""
-    up = {O: N, N: C}      # one more bond
-    down = {C: N, N: O}    # one fewer bond
-    total = sum(BONDING_VALENCE[int(z)] for z in z_heavy)
-    while total != target_valence:
-        step = up if total < target_valence else down
-        cand = np.nonzero(np.isin(z_heavy, list(step.keys())))[0]
+def _assign_heteroatoms(n_heavy, n_h, rng):
+    """Element list of a saturated chain with n_h hydrogens.
+
+    Starting from all carbon, the bonding valence must drop by
+    delta = 4 n - (n_h + 2 (n - 1)).  Each O site lowers it by 2, each N site
+    by 1.  The number of sites m is drawn between ceil(delta/2) (all O) and
+    min(delta, ceil(n/2)), and the sites are an isolated set along the chain
+    (no two heteroatoms bonded), chosen by a left-to-right scan that skips
+    positions at random while there is room.  When delta exceeds what isolated
+    sites can absorb the remaining steps go to any site (C -> N -> O).
+    """
+    z = np.full(n_heavy, C, dtype=np.int32)
+    delta = 4 * n_heavy - (n_h + 2 * (n_heavy - 1))
+    if delta <= 0:
+        return z
+    cap = (n_heavy + 1) // 2
+    lo = (delta + 1) // 2
+    hi = min(delta, cap)
+    if lo <= hi:
+        m = int(rng.integers(lo, hi + 1))
+        n_o = delta - m
+        sites = []
+        k = 0
+        while len(sites) < m and k < n_heavy:
+            room = ((n_heavy - k) + 1) // 2 - (m - len(sites))   # spare isolated slots from k on
+            if room > 0 and rng.uniform() < 0.5:
+                k += 1
+                continue
+            sites.append(k)
+            k += 2
+        sites = np.array(sites, dtype=np.int64)
+        kinds = rng.permutation(len(sites))
+        for j, site in enumerate(sites):
+            z[site] = O if kinds[j] < n_o else N
+        return z
+    # too many heteroatoms to keep apart: one valence step at a time anywhere
+    total = 4 * n_heavy
+    target = total - delta
+    while total > target:
+        cand = np.nonzero(z != O)[0]
         if cand.size == 0:
             break
         k = int(cand[int(rng.integers(0, cand.size))])
-        z_heavy[k] = step[int(z_heavy[k])]
-        total += 1 if step is up else -1
-    return z_heavy
+        z[k] = N if z[k] == C else O
+        total -= 1
+    return z
 
 
 def _substituent_directions(bonds, count, rng):
@@ -126,7 +157,7 @@ def _substituent_directions(bonds, count, rng):
     return [ch * m + sh * nrm, ch * m - sh * nrm][:count]
 
 
-def make_chain(seed: int, n_heavy: int, n_h: int, *, heavy_weights=(0.6, 0.2, 0.2),
+def make_chain(seed: int, n_heavy: int, n_h: int, *,
                bond=(1.0, 1.5), h_bond=(1.0, 1.1), heavy_clash=2.5, h_clash=1.6,
                min_pair=0.9):
     """Seeded saturated heavy-atom chain with attached hydrogens.
@@ -134,10 +165,10 @@ def make_chain(seed: int, n_heavy: int, n_h: int, *, heavy_weights=(0.6, 0.2, 0.
     Heavy atoms follow a self-avoiding random walk: bond length U[bond],
     interior bond angle with cosine uniform between cos(125 deg) and
     cos(100 deg), dihedral uniform, non-neighbouring heavy atoms at least
-    ``heavy_clash`` apart.  Elements are drawn from C/N/O with
-    ``heavy_weights`` and then moved one step at a time (C<->N<->O) until the
-    free bonding valence (C 4, N 3, O 2, minus chain bonds) equals n_h, so
-    the molecule is saturated and closed shell.  Hydrogens sit at U[h_bond]
+    ``heavy_clash`` apart.  The elements make the chain saturated with
+    exactly n_h hydrogens (bonding valence C 4, N 3, O 2), heteroatoms kept
+    apart from each other (see _assign_heteroatoms), so the molecule is
+    closed shell.  Hydrogens sit at U[h_bond]
     Angstrom in tetrahedral directions around their parent (random phase for
     chain ends), nudged at random while closer than ``h_clash`` to any other
     atom.  Only when n_h exceeds what all-carbon saturation holds are the
@@ -151,15 +182,7 @@ def make_chain(seed: int, n_heavy: int, n_h: int, *, heavy_weights=(0.6, 0.2, 0.
     n_h = int(n_h)
     if n_heavy < 1:
         raise ValueError("need at least one heavy atom")
-    w = np.asarray(heavy_weights, dtype=np.float64)
-    cdf = np.cumsum(w) / np.sum(w)
-    z_heavy = np.empty(n_heavy, dtype=np.int32)
-    for k in range(n_heavy):
-        u = rng.uniform()
-        j = int(np.searchsorted(cdf, u, side="right"))
-        z_heavy[k] = HEAVY[min(j, 2)]
-    chain_bonds = 2 * (n_heavy - 1)
-    z_heavy = _balance_elements(z_heavy, n_h + chain_bonds, rng)
+    z_heavy = _assign_heteroatoms(n_heavy, n_h, rng)
 
     pos = np.zeros((n_heavy, 3))
     if n_heavy > 1:

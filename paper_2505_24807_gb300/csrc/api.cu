@@ -19,6 +19,10 @@ template <typename F>
 int guarded(xs_ctx* ctx, F&& f) {
   if (!ctx) return XS_EINVAL;
   ctx->c.err.clear();
+  struct Bind {
+    Bind(xs::Profiler* p) { xs::g_prof = p; }
+    ~Bind() { xs::g_prof = nullptr; }
+  } bind(&ctx->c.prof);
   try {
     XS_CUDA(cudaSetDevice(ctx->c.device));
     return f(ctx->c);
@@ -330,6 +334,44 @@ int xs_get_amplitudes(const xs_ctx* cctx, int mol, int root, double* X, double* 
       copy_any(s, Y, t.get(), sizeof(double) * n_ov);
       XS_CUDA(cudaStreamSynchronize(s));
     }
+    return XS_OK;
+  });
+}
+
+int xs_profile(xs_ctx* ctx, int enable) {
+  return guarded(ctx, [&](Ctx& c) {
+    c.prof.reset();
+    c.prof.on = enable != 0;
+    return XS_OK;
+  });
+}
+
+int xs_profile_read(xs_ctx* ctx, xs_prof_entry* out, int max_entries, int* count) {
+  return guarded(ctx, [&](Ctx& c) {
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    c.prof.flush();
+    int k = 0;
+    for (auto& kv : c.prof.e) {
+      if (out && k < max_entries) {
+        xs_prof_entry& e = out[k];
+        std::memset(&e, 0, sizeof(e));
+        std::strncpy(e.name, kv.first.c_str(), sizeof(e.name) - 1);
+        e.launches = kv.second.launches;
+        e.ms = kv.second.ms;
+        e.bytes = kv.second.bytes;
+        e.flops = kv.second.flops;
+      }
+      ++k;
+    }
+    // one more entry: every library kernel launch while profiling was on
+    if (out && k < max_entries) {
+      xs_prof_entry& e = out[k];
+      std::memset(&e, 0, sizeof(e));
+      std::strncpy(e.name, "all_launches", sizeof(e.name) - 1);
+      e.launches = static_cast<int>(c.prof.launches);
+    }
+    ++k;
+    if (count) *count = k;
     return XS_OK;
   });
 }

@@ -11,6 +11,7 @@
 
 #include "../../include/xs.h"
 #include "model.h"
+#include "prof.h"
 
 namespace xs {
 
@@ -29,7 +30,11 @@ struct Error : std::runtime_error {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                \
   } while (0)
 
-#define XS_CHECK_LAUNCH() XS_CUDA(cudaGetLastError())
+#define XS_CHECK_LAUNCH()                                   \
+  do {                                                      \
+    XS_CUDA(cudaGetLastError());                            \
+    if (::xs::g_prof && ::xs::g_prof->on) ++::xs::g_prof->launches; \
+  } while (0)
 
 // Owning device buffer.
 template <typename T>
@@ -91,6 +96,8 @@ struct Ctx {
   // scratch reused across calls
   DevBuf<double> ws0, ws1, ws2, ws3, ws4, ws5;
   DevBuf<float> fs0, fs1, fs2;
+  Profiler prof;
+  DevBuf<int> tc_err;   // error word of the tensor-core kernels' bounded waits
 };
 
 inline dim3 grid1(long long n, int block) { return dim3(static_cast<unsigned>((n + block - 1) / block)); }

@@ -19,6 +19,7 @@
 //      J2 with the closed-form one-centre Coulomb/exchange; off-diagonal blocks
 //      hold the two-centre exchange sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig}.
 #include "kernels.h"
+#include "prof.h"
 
 namespace xs {
 
@@ -185,6 +186,10 @@ void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, in
   gemm<T>(s, false, false, np, nvec, np, T(1), W, np, 0, r, nvec, 0, T(0), J2, nvec, 0, 1);
   dim3 block(32, 8);
   dim3 grid((n + 31) / 32, (n + 7) / 8, nvec);
+  // algorithmic traffic: read R, write G (and G-), read the pair integrals once
+  const double outs = (mode == G_CIS) ? 1.0 : 2.0;
+  ProfScope ps(s, sizeof(T) == 8 ? "gbuild_assemble_f64" : "gbuild_assemble_f32",
+               sizeof(T) * ((double)nvec * n * n * (1.0 + outs) + (double)np * np), 0.0);
   if (mode == G_CIS)
     assemble_kernel<T, G_CIS><<<grid, block, 0, s>>>(n, np, nvec, m.ao_atom.get(), m.ao_local.get(),
                                                      m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),

@@ -6,6 +6,7 @@
 // tile per 256-thread CTA, 4 x 4 outputs per thread strided by 16 so that
 // shared-memory reads are conflict free; K staged 16 at a time.
 #include "kernels.h"
+#include "prof.h"
 
 namespace xs {
 
@@ -117,6 +118,7 @@ void gemm(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha
     K = 0;
   }
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+  ProfScope ps(s, sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", 0.0, 2.0 * M * N * (double)K * batch);
   gemm_kernel<T><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, transA, B, ldb, sB, transB, beta, C, ldc,
                                       sC, 1, 0);
   XS_CHECK_LAUNCH();
@@ -133,6 +135,7 @@ void gram(cudaStream_t s, int M, int N, int L, const T* A, int lda, const T* B, 
   if (kSplit < 1) kSplit = 1;
   ws.ensure((size_t)kSplit * M * N);
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, kSplit);
+  ProfScope ps(s, sizeof(T) == 8 ? "gram_f64" : "gram_f32", sizeof(T) * (double)L * (M + N), 2.0 * M * N * (double)L);
   gemm_kernel<T><<<grid, 256, 0, s>>>(M, N, L, T(1), A, lda, 0, false, B, ldb, 0, true, T(0), ws.get(), N, 0,
                                       kSplit, (long long)M * N);
   XS_CHECK_LAUNCH();

@@ -1,0 +1,61 @@
+// Per-kernel CUDA-event timing of libxs (see prof.h).
+#include "prof.h"
+
+namespace xs {
+
+thread_local Profiler* g_prof = nullptr;
+
+cudaEvent_t Profiler::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t ev = nullptr;
+  cudaEventCreate(&ev);
+  return ev;
+}
+
+void Profiler::flush() {
+  for (auto& kv : e) {
+    for (auto& pr : kv.second.pending) {
+      cudaEventSynchronize(pr.second);
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) kv.second.ms += ms;
+      pool.push_back(pr.first);
+      pool.push_back(pr.second);
+    }
+    kv.second.pending.clear();
+  }
+}
+
+void Profiler::reset() {
+  flush();
+  e.clear();
+  launches = 0;
+}
+
+Profiler::~Profiler() {
+  flush();
+  for (auto ev : pool) cudaEventDestroy(ev);
+}
+
+ProfScope::ProfScope(cudaStream_t stream, const char* name, double bytes, double flops) {
+  if (!g_prof || !g_prof->on) return;
+  ent = &g_prof->e[name];
+  ent->launches += 1;
+  ent->bytes += bytes;
+  ent->flops += flops;
+  s = stream;
+  a = g_prof->get();
+  b = g_prof->get();
+  cudaEventRecord(a, s);
+}
+
+ProfScope::~ProfScope() {
+  if (!ent) return;
+  cudaEventRecord(b, s);
+  ent->pending.emplace_back(a, b);
+}
+
+}  // namespace xs

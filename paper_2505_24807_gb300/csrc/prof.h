@@ -1,0 +1,44 @@
+// Per-kernel CUDA-event timing of libxs (enabled through xs_profile).  Each
+// instrumented launch is bracketed by two events on the launching stream;
+// elapsed times are summed when the profile is read.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+namespace xs {
+
+struct ProfEntry {
+  int launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;   // algorithmic bytes, summed over launches
+  double flops = 0.0;   // algorithmic flops, summed over launches
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+struct Profiler {
+  bool on = false;
+  long long launches = 0;   // every kernel launch of the library while on
+  std::map<std::string, ProfEntry> e;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+  void flush();   // resolve pending event pairs (synchronises on them)
+  void reset();
+  ~Profiler();
+};
+
+// The profiler of the context whose API call is running on this thread.
+extern thread_local Profiler* g_prof;
+
+struct ProfScope {
+  ProfEntry* ent = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s = nullptr;
+  ProfScope(cudaStream_t stream, const char* name, double bytes, double flops);
+  ~ProfScope();
+};
+
+}  // namespace xs

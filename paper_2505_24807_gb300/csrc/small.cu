@@ -9,6 +9,7 @@
 
 #include "kernels.h"
 #include "small.h"
+#include "prof.h"
 
 namespace xs {
 
@@ -212,6 +213,7 @@ void jacobi_eig(cudaStream_t s, int n, double* A, int lda, double* V, int ldv, d
   size_t smem = sizeof(double) * (2 * (m / 2)) + sizeof(int) * 2 * (m / 2);
   size_t smem2 = sizeof(double) * n + sizeof(int) * n;
   if (smem2 > smem) smem = smem2;
+  ProfScope ps(s, "jacobi_f64", 0.0, 0.0);
   jacobi_kernel<<<1, 1024, smem, s>>>(n, A, lda, V, ldv, w, info, 60);
   XS_CHECK_LAUNCH();
 }

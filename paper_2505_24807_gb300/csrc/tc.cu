@@ -1,81 +1,126 @@
 // Mixed-precision A*X path of libxs (see tc.h).
+//
+// Per batch of k trial vectors (all tensor-core operands K-major TF32 pairs):
+//   1. X_k (o x v)                    -> TF32 pair, v padded to 32
+//   2. U_k^T (n x o) = C_vir X_k^T    (tc_gemm, epilogue writes a TF32 pair)
+//   3. R_k (n x n)   = C_occ U_k      (tc_gemm, float32 out)
+//   4. G_k = G(R_k)                   (float32 G build)  -> TF32 pair, n padded
+//   5. S_k^T (v x n) = C_vir^T G_k^T  (tc_gemm, TF32 pair out)
+//   6. Y_k (o x v)   = C_occ^T S_k + (eps_a - eps_i) X_k   (tc_gemm, float64 out)
+// For TDHF steps 5-6 run for G+ and G-.
 #include "kernels.h"
 #include "products.h"
 #include "tc.h"
+#include "tc_gemm.h"
 
 namespace xs {
-
-namespace {
-
-template <typename T>
-void pbuild_f(cudaStream_t s, int n, int o, int v, int nvec, const T* CT, const T* X, T* R, T* tmp) {
-  const T* CTocc = CT;
-  const T* CTvir = CT + (size_t)o * n;
-  if (v <= o) {
-    gemm<T>(s, true, false, n, v, o, T(1), CTocc, n, 0, X, v, (long long)o * v, T(0), tmp, v, (long long)n * v, nvec);
-    gemm<T>(s, false, false, nvec * n, n, v, T(1), tmp, v, 0, CTvir, n, 0, T(0), R, n, 0, 1);
-  } else {
-    gemm<T>(s, false, false, nvec * o, n, v, T(1), X, v, 0, CTvir, n, 0, T(0), tmp, n, 0, 1);
-    gemm<T>(s, true, false, n, n, o, T(1), CTocc, n, 0, tmp, n, (long long)o * n, T(0), R, n, (long long)n * n, nvec);
-  }
-}
-
-template <typename T>
-void backtransform_f(cudaStream_t s, int n, int o, int v, int nvec, const T* CT, const T* G, T* Y, T* tmp) {
-  const T* CTocc = CT;
-  const T* CTvir = CT + (size_t)o * n;
-  if (v <= o) {
-    gemm<T>(s, false, true, nvec * n, v, n, T(1), G, n, 0, CTvir, n, 0, T(0), tmp, v, 0, 1);
-    gemm<T>(s, false, false, o, v, n, T(1), CTocc, n, 0, tmp, v, (long long)n * v, T(0), Y, v, (long long)o * v, nvec);
-  } else {
-    gemm<T>(s, false, false, o, n, n, T(1), CTocc, n, 0, G, n, (long long)n * n, T(0), tmp, n, (long long)o * n, nvec);
-    gemm<T>(s, false, true, nvec * o, v, n, T(1), tmp, n, 0, CTvir, n, 0, T(0), Y, v, 0, 1);
-  }
-}
-
-}  // namespace
 
 void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2) {
   cudaStream_t s = c.stream;
   const int n = m.n, o = m.o, v = m.v;
+  const int np_ = pad32(n), op = pad32(o), vp = pad32(v);
   const long long ov = (long long)o * v, nn = (long long)n * n;
   if (!m.Wf.get()) {
     m.Wf.alloc((size_t)m.np * m.np);
     convert_d2f(s, (long long)m.np * m.np, m.W.get(), m.Wf.get());
   }
+  // orbital operands, cached until the orbitals change:
+  //   Cvir (n x vp) = C[mu][o + a], Cocc (n x op) = C[mu][i],
+  //   CTvir (v x np) = CT[o + a][mu], CTocc (o x np) = CT[i][mu]
+  const size_t orb = (size_t)n * vp + (size_t)n * op + (size_t)v * np_ + (size_t)o * np_;
   if (!m.CTf_hi.get()) {
-    m.CTf_hi.alloc(nn);
-    m.CTf_lo.alloc(nn);
-    split_d2f(s, nn, m.CT.get(), m.CTf_hi.get(), m.CTf_lo.get());
+    m.CTf_hi.alloc(orb);
+    m.CTf_lo.alloc(orb);
+    float* h = m.CTf_hi.get();
+    float* l = m.CTf_lo.get();
+    const double* CT = m.CT.get();
+    split_pad<double>(s, n, v, vp, CT + (size_t)o * n, n, 0, 0, 1, true, h, l);
+    h += (size_t)n * vp; l += (size_t)n * vp;
+    split_pad<double>(s, n, o, op, CT, n, 0, 0, 1, true, h, l);
+    h += (size_t)n * op; l += (size_t)n * op;
+    split_pad<double>(s, v, n, np_, CT + (size_t)o * n, n, 0, 0, 1, false, h, l);
+    h += (size_t)v * np_; l += (size_t)v * np_;
+    split_pad<double>(s, o, n, np_, CT, n, 0, 0, 1, false, h, l);
   }
+  const float* Cvir_h = m.CTf_hi.get();
+  const float* Cvir_l = m.CTf_lo.get();
+  const float* Cocc_h = Cvir_h + (size_t)n * vp;
+  const float* Cocc_l = Cvir_l + (size_t)n * vp;
+  const float* CTvir_h = Cocc_h + (size_t)n * op;
+  const float* CTvir_l = Cocc_l + (size_t)n * op;
+  const float* CTocc_h = CTvir_h + (size_t)v * np_;
+  const float* CTocc_l = CTvir_l + (size_t)v * np_;
+
   const int nb = product_batch(m);
   const int chunk = nvec < nb ? nvec : nb;
-  c.fs0.ensure((size_t)chunk * nn * 3 + (size_t)chunk * n * (o > v ? o : v) + (size_t)chunk * ov * 2);
-  float* R = c.fs0.get();
-  float* G = R + (size_t)chunk * nn;
-  float* Gm = G + (size_t)chunk * nn;
-  float* tmp = Gm + (size_t)chunk * nn;
-  float* Xf = tmp + (size_t)chunk * n * (o > v ? o : v);
-  float* Yf = Xf + (size_t)chunk * ov;
+  // per vector: X pair, U^T pair, R, G+, G-, G pair, S^T pair
+  const size_t per = 2 * (size_t)o * vp + 2 * (size_t)n * op + 3 * (size_t)nn + 2 * (size_t)n * np_ +
+                     2 * (size_t)v * np_;
+  c.fs0.ensure((size_t)chunk * per);
+  float* p = c.fs0.get();
+  float* Xh = p; p += (size_t)chunk * o * vp;
+  float* Xl = p; p += (size_t)chunk * o * vp;
+  float* Uh = p; p += (size_t)chunk * n * op;
+  float* Ul = p; p += (size_t)chunk * n * op;
+  float* R = p; p += (size_t)chunk * nn;
+  float* G = p; p += (size_t)chunk * nn;
+  float* Gm = p; p += (size_t)chunk * nn;
+  float* Gh = p; p += (size_t)chunk * n * np_;
+  float* Gl = p; p += (size_t)chunk * n * np_;
+  float* Sh = p; p += (size_t)chunk * v * np_;
+  float* Sl = p; p += (size_t)chunk * v * np_;
+  DevBuf<int>& err = c.tc_err;
+  if (!err.get()) {
+    err.alloc(1);
+    XS_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+  }
+
   for (int k0 = 0; k0 < nvec; k0 += chunk) {
     const int k = (nvec - k0) < chunk ? (nvec - k0) : chunk;
     const double* Xk = X + k0 * ov;
-    convert_d2f(s, k * ov, Xk, Xf);
-    pbuild_f<float>(s, n, o, v, k, m.CTf_hi.get(), Xf, R, tmp);
-    if (method == XS_CIS) {
-      gbuild<float>(s, m, c.d_par.get(), G_CIS, k, R, G, nullptr, c.fs1);
-      backtransform_f<float>(s, n, o, v, k, m.CTf_hi.get(), G, Yf, tmp);
-      convert_f2d(s, k * ov, Yf, Y1 + k0 * ov);
-      add_diag_term<double>(s, k, o, v, m.eps.get(), Xk, Y1 + k0 * ov);
-    } else {
-      gbuild<float>(s, m, c.d_par.get(), G_RPA, k, R, G, Gm, c.fs1);
-      backtransform_f<float>(s, n, o, v, k, m.CTf_hi.get(), G, Yf, tmp);
-      convert_f2d(s, k * ov, Yf, Y1 + k0 * ov);
-      add_diag_term<double>(s, k, o, v, m.eps.get(), Xk, Y1 + k0 * ov);
-      backtransform_f<float>(s, n, o, v, k, m.CTf_hi.get(), Gm, Yf, tmp);
-      convert_f2d(s, k * ov, Yf, Y2 + k0 * ov);
-      add_diag_term<double>(s, k, o, v, m.eps.get(), Xk, Y2 + k0 * ov);
+    split_pad<double>(s, o, v, vp, Xk, v, ov, (long long)o * vp, k, false, Xh, Xl);
+    {  // U^T = C_vir X^T : M = n, N = o, K = v
+      TcOperand A{Cvir_h, Cvir_l, vp, 0, false};
+      TcOperand B{Xh, Xl, vp, (long long)o * vp, true};
+      TcEpilogue e;
+      e.mode = 1; e.D = Uh; e.Dlo = Ul; e.ld = op; e.bstride = (long long)n * op;
+      tc_gemm(s, A, B, n, o, vp, k, e, err.get());
     }
+    {  // R = C_occ U : M = n, N = n, K = o
+      TcOperand A{Cocc_h, Cocc_l, op, 0, false};
+      TcOperand B{Uh, Ul, op, (long long)n * op, true};
+      TcEpilogue e;
+      e.mode = 0; e.D = R; e.ld = n; e.bstride = nn;
+      tc_gemm(s, A, B, n, n, op, k, e, err.get());
+    }
+    const bool rpa = method != XS_CIS;
+    gbuild<float>(s, m, c.d_par.get(), rpa ? G_RPA : G_CIS, k, R, G, rpa ? Gm : nullptr, c.fs1);
+    for (int pass = 0; pass < (rpa ? 2 : 1); ++pass) {
+      const float* Gs = pass == 0 ? G : Gm;
+      double* Yout = (pass == 0 ? Y1 : Y2) + k0 * ov;
+      split_pad<float>(s, n, n, np_, Gs, n, nn, (long long)n * np_, k, false, Gh, Gl);
+      {  // S^T = C_vir^T G^T : M = v, N = n, K = n
+        TcOperand A{CTvir_h, CTvir_l, np_, 0, false};
+        TcOperand B{Gh, Gl, np_, (long long)n * np_, true};
+        TcEpilogue e;
+        e.mode = 1; e.D = Sh; e.Dlo = Sl; e.ld = np_; e.bstride = (long long)v * np_;
+        tc_gemm(s, A, B, v, n, np_, k, e, err.get());
+      }
+      {  // Y = C_occ^T S + d eps X : M = o, N = v, K = n
+        TcOperand A{CTocc_h, CTocc_l, np_, 0, false};
+        TcOperand B{Sh, Sl, np_, (long long)v * np_, true};
+        TcEpilogue e;
+        e.mode = 2; e.Y = Yout; e.X = Xk; e.eps = m.eps.get(); e.ld = v; e.bstride = ov; e.o = o;
+        tc_gemm(s, A, B, o, v, np_, k, e, err.get());
+      }
+    }
+  }
+  int h_err = 0;
+  XS_CUDA(cudaMemcpyAsync(&h_err, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  XS_CUDA(cudaStreamSynchronize(s));
+  if (h_err) {
+    XS_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    throw Error(XS_ETIMEOUT, "tensor-core GEMM: a bounded device wait timed out (code " + std::to_string(h_err) + ")");
   }
 }
 

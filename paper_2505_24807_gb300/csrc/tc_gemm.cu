@@ -1,0 +1,388 @@
+// Split-precision tensor-core GEMM of libxs (sm_103a, tcgen05 + TMA).
+//
+// D = A B^T with A (M x K) and B (N x K) both K-major float32 matrices, each
+// given as a TF32 pair (hi, lo) with x ~= hi + lo (hi rounded to TF32, lo the
+// TF32 remainder).  The product is formed as hi*hi + hi*lo + lo*hi on the
+// 5th-generation tensor cores (kind::tf32) with float32 accumulation in TMEM,
+// which keeps about 21 significant bits -- the "split-precision (hi + lo)
+// products" that carry the dense C X C^T transforms of the A*X product.
+//
+// One CTA computes one 128 x BN tile (cta_group::1, M = 128):
+//   warp 0      TMA producer: four 128-byte-swizzled boxes per K block of 32
+//   warp 1      TMEM allocation and the single-thread MMA issue
+//   warps 2..5  epilogue: tcgen05.ld of the 128 accumulator lanes, stores
+// A 3-stage mbarrier ring couples producer and MMA; tcgen05.commit frees a
+// stage and finally signals the epilogue.  Every wait is bounded by the
+// global timer; a timeout sets the error word, the CTA skips the remaining
+// work, waits (bounded) for its issued copies and MMAs, frees TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "kernels.h"
+#include "prof.h"
+#include "tc_gemm.h"
+
+namespace xs {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 32;       // 32 tf32 = 128 bytes = one swizzle atom row
+constexpr int STAGES = 3;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+// Bounded wait; returns false (and raises the error word) on timeout or when
+// another thread already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  unsigned long long t0 = gtime();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*reinterpret_cast<volatile int*>(err)) return false;
+    if (gtime() - t0 > kWaitNs) {
+      atomicCAS(err, 0, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y, int z,
+                                         int rank3) {
+  if (rank3) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+  } else {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+  }
+}
+
+// K-major, 128-byte swizzle shared-memory matrix descriptor (8-row groups of
+// 1024 bytes, version 1 for sm_100-family).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// TF32 split of a float: hi keeps the 10 explicit mantissa bits (rounded to
+// nearest, ties away), lo = x - hi (exact in float32).
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  uint32_t b = __float_as_uint(x);
+  uint32_t h = (b + 0x1000u) & 0xFFFFE000u;
+  hi = __uint_as_float(h);
+  lo = x - hi;
+}
+
+struct EpiArgs {
+  int mode;             // 0: float D; 1: TF32 pair (Dhi, Dlo); 2: double Y + (eps_a - eps_i) X
+  float* D;
+  float* Dlo;
+  double* Y;
+  const double* X;
+  const double* eps;
+  int ld;               // leading dimension of the output rows
+  long long bstride;    // output stride between batch entries
+  int o;                // mode 2: number of occupied orbitals (eps offset of the virtuals)
+};
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                   const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int M, int N,
+                   int Kpad, int a3, int b3, EpiArgs ep, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte aligned stage buffers (the 128-byte swizzle repeats every 1024 bytes)
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int A_BYTES = BM * BK * 4;
+  constexpr int B_BYTES = BN * BK * 4;
+  constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  uint8_t* stage_base = base;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accfull = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, bz = blockIdx.z;
+  const int nk = Kpad / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accfull, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) + 1) & 1, err, 1)) break;
+      uint8_t* st = stage_base + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      const int k = kb * BK;
+      tma_load(st, &tmAh, &full[s], k, m0, bz, a3);
+      tma_load(st + A_BYTES, &tmAl, &full[s], k, m0, bz, a3);
+      tma_load(st + 2 * A_BYTES, &tmBh, &full[s], k, n0, bz, b3);
+      tma_load(st + 2 * A_BYTES + B_BYTES, &tmBl, &full[s], k, n0, bz, b3);
+      ++issued;
+    }
+    // wait for the copies still in flight before leaving (bounded)
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+      mbar_wait(&empty[kb % STAGES], ((kb / STAGES) + 0) & 1, err, 0) || true;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issue
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
+                           (static_cast<uint32_t>(BM >> 4) << 24);
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, err, 2)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint8_t* st = stage_base + s * STAGE_BYTES;
+      const uint32_t ah = smem_u32(st), al = smem_u32(st + A_BYTES);
+      const uint32_t bh = smem_u32(st + 2 * A_BYTES), bl = smem_u32(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 8; ++kk) {
+        const uint32_t off = kk * 32;  // 8 tf32 per MMA step
+        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(tmem, sdesc(ah + off), sdesc(bh + off), idesc, acc0);
+        mma_tf32(tmem, sdesc(ah + off), sdesc(bl + off), idesc, 1u);
+        mma_tf32(tmem, sdesc(al + off), sdesc(bh + off), idesc, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accfull);
+  } else if (warp >= 2) {
+    // epilogue: TMEM lanes 32*(warp % 4) .. +31 are this warp's rows
+    const int lane_base = 32 * (warp % 4);
+    const int row = m0 + lane_base + lane;
+    bool ok = mbar_wait(accfull, 0, err, 3);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && !*reinterpret_cast<volatile int*>(err)) {
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(lane_base) << 16) + c0, v);
+        if (row >= M) continue;
+        const long long rb = (long long)bz * ep.bstride + (long long)row * ep.ld;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col >= N) {
+            // a TF32-pair output feeds the next GEMM as a K-major operand:
+            // its padding columns up to the row stride must read as zero
+            if (ep.mode == 1 && col < ep.ld) {
+              ep.D[rb + col] = 0.0f;
+              ep.Dlo[rb + col] = 0.0f;
+            }
+            continue;
+          }
+          if (ep.mode == 0) {
+            ep.D[rb + col] = v[j];
+          } else if (ep.mode == 1) {
+            float h, l;
+            tf32_split(v[j], h, l);
+            ep.D[rb + col] = h;
+            ep.Dlo[rb + col] = l;
+          } else {
+            const double de = ep.eps[ep.o + col] - ep.eps[row];
+            ep.Y[rb + col] = static_cast<double>(v[j]) + de * ep.X[rb + col];
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+// zero-padded TF32 pair of a float64 or float32 matrix, optionally transposed:
+// dst[r][c] (ld_dst) = split(src[r][c]) or split(src[c][r]); pad columns are 0
+template <typename S>
+__global__ void split_pad_kernel(int rows, int cols, int ld_dst, const S* __restrict__ src, int ld_src,
+                                 long long sstride, long long dstride, int transpose, float* __restrict__ hi,
+                                 float* __restrict__ lo) {
+  const int b = blockIdx.z;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)rows * ld_dst) return;
+  const int r = static_cast<int>(idx / ld_dst), c = static_cast<int>(idx % ld_dst);
+  float h = 0.0f, l = 0.0f;
+  if (c < cols) {
+    const S* s = src + b * sstride;
+    const double x = transpose ? static_cast<double>(s[(long long)c * ld_src + r])
+                               : static_cast<double>(s[(long long)r * ld_src + c]);
+    const float xf = static_cast<float>(x);
+    uint32_t bits = __float_as_uint(xf);
+    h = __uint_as_float((bits + 0x1000u) & 0xFFFFE000u);
+    l = static_cast<float>(x - static_cast<double>(h));
+  }
+  hi[b * dstride + idx] = h;
+  lo[b * dstride + idx] = l;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  if (!fn) throw Error(XS_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  return fn;
+}
+
+// rows x kpad float32 matrix (row stride ld floats), batch entries bstride apart
+CUtensorMap make_map(const float* ptr, int rows, int kpad, int ld, int batch, long long bstride, int box_rows) {
+  CUtensorMap m;
+  const bool r3 = batch > 1;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(kpad), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(batch)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 4, static_cast<cuuint64_t>(bstride) * 4};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ld % 4) || (kpad % BK))
+    throw Error(XS_EINVAL, "tensor-core operand not 16-byte aligned or not padded");
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, r3 ? 3 : 2, const_cast<float*>(ptr), dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(XS_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+  return m;
+}
+
+template <int BN>
+size_t smem_bytes() {
+  return 1024 + STAGES * (2 * BM * BK * 4 + 2 * BN * BK * 4) + (2 * STAGES + 1) * 8 + 16;
+}
+
+}  // namespace
+
+int pad32(int k) { return (k + BK - 1) / BK * BK; }
+
+template <typename S>
+void split_pad(cudaStream_t s, int rows, int cols, int ld_dst, const S* src, int ld_src, long long sstride,
+               long long dstride, int batch, bool transpose, float* hi, float* lo) {
+  if (rows <= 0 || batch <= 0) return;
+  dim3 grid(static_cast<unsigned>(((long long)rows * ld_dst + 255) / 256), 1, batch);
+  split_pad_kernel<S><<<grid, 256, 0, s>>>(rows, cols, ld_dst, src, ld_src, sstride, dstride, transpose ? 1 : 0, hi,
+                                           lo);
+  XS_CHECK_LAUNCH();
+}
+template void split_pad<double>(cudaStream_t, int, int, int, const double*, int, long long, long long, int, bool,
+                                float*, float*);
+template void split_pad<float>(cudaStream_t, int, int, int, const float*, int, long long, long long, int, bool,
+                               float*, float*);
+
+void tc_gemm(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int N, int Kpad, int batch,
+             const TcEpilogue& e, int* d_err) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  constexpr int BNv = 128;
+  const CUtensorMap ah = make_map(A.hi, M, Kpad, A.ld, A.batched ? batch : 1, A.bstride, BM);
+  const CUtensorMap al = make_map(A.lo, M, Kpad, A.ld, A.batched ? batch : 1, A.bstride, BM);
+  const CUtensorMap bh = make_map(B.hi, N, Kpad, B.ld, B.batched ? batch : 1, B.bstride, BNv);
+  const CUtensorMap bl = make_map(B.lo, N, Kpad, B.ld, B.batched ? batch : 1, B.bstride, BNv);
+  EpiArgs ep{e.mode, e.D, e.Dlo, e.Y, e.X, e.eps, e.ld, e.bstride, e.o};
+  const size_t smem = smem_bytes<BNv>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    XS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BNv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem)));
+    attr_set = true;
+  }
+  dim3 grid((N + BNv - 1) / BNv, (M + BM - 1) / BM, batch);
+  ProfScope ps(s, "tc_gemm_tf32x3", 0.0, 2.0 * 3.0 * M * N * (double)Kpad * batch);
+  tc_gemm_kernel<BNv><<<grid, 192, smem, s>>>(ah, al, bh, bl, M, N, Kpad, A.batched && batch > 1 ? 1 : 0,
+                                              B.batched && batch > 1 ? 1 : 0, ep, d_err);
+  XS_CHECK_LAUNCH();
+}
+
+}  // namespace xs

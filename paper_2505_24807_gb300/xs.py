@@ -46,6 +46,11 @@ class xs_solve_info(C.Structure):
                 ("polished", C.c_int), ("seconds", C.c_double), ("seconds_products", C.c_double)]
 
 
+class xs_prof_entry(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
 _lib = None
 
 
@@ -70,6 +75,8 @@ def load():
         "xs_apply": (i, [vp, i, i, i, vp, vp, i]),
         "xs_excited": (i, [vp, C.POINTER(xs_ex_opts), vp, vp, vp, vp, C.POINTER(xs_solve_info)]),
         "xs_get_amplitudes": (i, [vp, i, i, vp, vp, sz]),
+        "xs_profile": (i, [vp, i]),
+        "xs_profile_read": (i, [vp, C.POINTER(xs_prof_entry), i, C.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -189,6 +196,20 @@ def xs_get_amplitudes(ctx, mol, root):
     Y = np.empty(ov)
     _check(ctx, load().xs_get_amplitudes(ctx, int(mol), int(root), _ptr(X), _ptr(Y), ov))
     return X.reshape(o, n - o), Y.reshape(o, n - o)
+
+
+def xs_profile(ctx, enable=True):
+    return _check(ctx, load().xs_profile(ctx, int(bool(enable))))
+
+
+def xs_profile_read(ctx):
+    """dict name -> dict(launches, ms, bytes, flops) of the instrumented kernels."""
+    n = C.c_int()
+    _check(ctx, load().xs_profile_read(ctx, None, 0, C.byref(n)))
+    arr = (xs_prof_entry * max(n.value, 1))()
+    _check(ctx, load().xs_profile_read(ctx, arr, n.value, C.byref(n)))
+    return {arr[k].name.decode(): dict(launches=arr[k].launches, ms=arr[k].ms, bytes=arr[k].bytes,
+                                       flops=arr[k].flops) for k in range(n.value)}
 
 
 class Context:

@@ -133,19 +133,29 @@ def test_odd_electron_count_rejected():
 
 
 def test_unstable_reference_reported():
-    # seed 8 of the 12-heavy-atom chain has A - B with a negative eigenvalue
+    # an all-oxygen chain with weakened resonance integrals has an A - B with a
+    # negative eigenvalue (checked here with the oracle): TDHF must refuse it
+    import copy
     from oracle import excited, nddo
-    params = molgen.make_params(0)
-    Z, xyz = molgen.config_small(8)
+    params = copy.deepcopy(molgen.make_params(0))
+    for z in params:
+        params[z]["beta_s"] *= 0.7
+        params[z]["beta_p"] *= 0.7
+    Z, xyz = molgen.config_small(3)
+    Z = Z.copy()
+    Z[Z > 1] = 8
     mol, ints, res = oracle_ground_state(Z, xyz, params)
     A, B = excited.explicit_AB(res.eps, res.C, mol.nocc, nddo.full_eri(mol, ints))
-    if np.linalg.eigvalsh(A - B)[0] > 0:
-        pytest.skip("reference is stable for this seed")
+    assert np.linalg.eigvalsh(A - B)[0] < -0.1
     ctx = context(params)
     try:
         xs.xs_ground_state(ctx.h, [(Z, xyz)])
         with pytest.raises(xs.XSError) as e:
             xs.xs_excited(ctx.h, method=xs.XS_TDHF, nroots=5, tol=1e-6)
         assert e.value.status == xs.XS_EUNSTABLE
+        # CIS (B = 0) is still defined for this reference
+        out = xs.xs_excited(ctx.h, method=xs.XS_CIS, nroots=3, tol=1e-6)
+        w, _ = excited.cis_bruteforce(A, 3)
+        assert np.abs(out["omega"][0] - w).max() < 1e-6
     finally:
         ctx.close()
