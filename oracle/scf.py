@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .nddo import Integrals, Molecule, core_hamiltonian, full_eri
+from .nddo import CORE_CHARGE, Integrals, Molecule, core_hamiltonian, full_eri
 
 
 def coulomb_exchange(mol: Molecule, ints: Integrals, R):
@@ -86,15 +86,16 @@ def scf(mol: Molecule, ints: Integrals | None = None, *, tol_density=1e-10, tol_
     Converged when max|D_new - D| < tol_density and max|F D - D F| <
     tol_commutator (eV).  The returned C, eps diagonalise F(D) of the
     converged D.  Raises if the HOMO-LUMO gap is below ``min_gap`` eV.
-    The start is the core-Hamiltonian density unless ``D0`` is given.
+    The start is ``D0`` if given, else the neutral-atom density: each atom's
+    core charge spread evenly over its valence AOs (diagonal).
     """
     if ints is None:
         ints = Integrals(mol)
     Hc = core_hamiltonian(mol, ints)
     o = mol.nocc
     if D0 is None:
-        eps, C = np.linalg.eigh(Hc)
-        D = 2.0 * C[:, :o] @ C[:, :o].T
+        occ = np.concatenate([np.full(na, CORE_CHARGE[int(z)] / na) for z, na in zip(mol.Z, mol.nao_atom)])
+        D = np.diag(occ)
     else:
         D = np.array(D0, dtype=np.float64)
     Fs, Es = [], []

@@ -1,5 +1,6 @@
 // Ground state of libxs: restricted closed-shell SCF, F C = C eps with S = I
-// (paper, Section "Ground-state wavefunction calculation", Eq. 1).
+// (paper, Section "Ground-state wavefunction calculation", Eq. 1), started
+// from the neutral-atom density (core charge spread over each atom's AOs).
 //
 // The two-electron Fock part reuses the excited-state G build: for the
 // closed-shell density D = 2 C_occ C_occ^T, J(D) - K(D)/2 = 2 J(P) - K(P) with
@@ -72,7 +73,7 @@ int run_scf(Ctx& c, DevMol& m, double tol, int max_iter) {
   const int n = m.n, o = m.o;
   const size_t nn = static_cast<size_t>(n) * n;
   cudaStream_t s = c.stream;
-  const int hist = 8;
+  const int hist = 10;
   DevBuf<double> F(nn), D(nn), P(nn), T1(nn), Err(nn), Fh(hist * nn), Eh(hist * nn), Fx(nn), Dn(nn);
   DevBuf<double> work, small(64 + hist * hist + 16), gws;
   DevBuf<int> dinfo;
@@ -82,10 +83,17 @@ int run_scf(Ctx& c, DevMol& m, double tol, int max_iter) {
   double* d_coef = small.get() + 16;       // DIIS coefficients
   double* d_B = small.get() + 16 + hist;   // DIIS matrix
 
-  // core-Hamiltonian start
-  XS_CUDA(cudaMemcpyAsync(m.CT.get(), m.H.get(), nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  sym_eig(c, n, m.CT.get(), m.eps.get(), work, dinfo);
-  density(s, n, o, m.CT.get(), D.get());
+  // neutral-atom start: each atom's core charge spread evenly over its AOs
+  {
+    std::vector<double> d0(nn, 0.0);
+    for (int a = 0; a < m.L.natoms; ++a)
+      for (int k = 0; k < m.L.nao_atom[a]; ++k) {
+        const int mu = m.L.ao_off[a] + k;
+        d0[(size_t)mu * n + mu] = core_charge(m.L.Z[a]) / m.L.nao_atom[a];
+      }
+    XS_CUDA(cudaMemcpyAsync(D.get(), d0.data(), nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    XS_CUDA(cudaStreamSynchronize(s));
+  }
 
   std::vector<int> slot_age;
   int count = 0, head = 0;
