@@ -161,6 +161,26 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
  * |X|^2 - |Y|^2 = 1.  `ov` must equal nocc*nvir.  Host or device pointers. */
 int xs_get_amplitudes(const xs_ctx* ctx, int mol, int root, double* X, double* Y, size_t ov);
 
+/* Allocation-free G(R) build: the same G = 2J(R) - K(R) as
+ * xs_apply(ctx, mol, XS_KIND_G, nvec, R, G, XS_FP64), for callers that must not
+ * allocate device memory during the call -- work recorded inside CUDA stream
+ * capture, or a process whose device memory belongs to another allocator's
+ * pool, where a cudaMalloc would fail or break the capture.  No counterpart in
+ * the paper.
+ *   R, G: DEVICE pointers to nvec n x n row-major float64 matrices, owned by
+ *   the caller (molecule `mol` must have its ground state already).
+ * Scratch comes from one fixed device array of 2^18 doubles (2 MiB) compiled
+ * into the library, held by every GPU that loads the library until the
+ * process exits.  A call needs 2 * nprod * nvec doubles of it (nprod = 10 per
+ * heavy atom + 1 per hydrogen); larger requests return XS_EINVAL.  The first
+ * call on a device looks the array's device address up once; make that first
+ * call before any stream capture.  The call is asynchronous on the context's
+ * stream.  Every call shares the one array: calls that overlap on the GPU
+ * (other streams or contexts on the same device) race.  Nothing in the array
+ * needs clearing -- each call writes every element it later reads.  The call
+ * makes no cudaMalloc, cudaFree or allocating library call. */
+int xs_gbuild_noalloc(xs_ctx* ctx, int mol, int nvec, const double* R, double* G);
+
 /* Per-kernel timing.  xs_profile(ctx, 1) clears and enables it: every
  * instrumented kernel launch of later calls is bracketed by CUDA events on
  * the launching stream; xs_profile(ctx, 0) disables it.  xs_profile_read

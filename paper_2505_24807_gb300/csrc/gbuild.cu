@@ -201,8 +201,39 @@ void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, in
   XS_CHECK_LAUNCH();
 }
 
+template <typename T>
+void gbuild_raw(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* R, T* G, T* Gm,
+                T* r, T* J2) {
+  if (nvec <= 0) return;
+  const int n = m.n, np = m.np;
+  {
+    dim3 block(8, 32);
+    dim3 grid((m.L.natoms + 31) / 32);
+    pack_diag_kernel<T><<<grid, block, 0, s>>>(m.L.natoms, n, nvec, m.atom_ao_off.get(), m.atom_nao.get(),
+                                                m.atom_prod_off.get(), R, r);
+    XS_CHECK_LAUNCH();
+  }
+  const T* W = nullptr;
+  if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(m.W.get());
+  else W = reinterpret_cast<const T*>(m.Wf.get());
+  gemm<T>(s, false, false, np, nvec, np, T(1), W, np, 0, r, nvec, 0, T(0), J2, nvec, 0, 1);
+  dim3 block(32, 8);
+  dim3 grid((n + 31) / 32, (n + 7) / 8, nvec);
+  if (mode == G_CIS)
+    assemble_kernel<T, G_CIS><<<grid, block, 0, s>>>(n, np, nvec, m.ao_atom.get(), m.ao_local.get(),
+                                                     m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
+                                                     m.atom_elem.get(), d_par, W, J2, R, G, nullptr);
+  else
+    assemble_kernel<T, G_RPA><<<grid, block, 0, s>>>(n, np, nvec, m.ao_atom.get(), m.ao_local.get(),
+                                                     m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
+                                                     m.atom_elem.get(), d_par, W, J2, R, G, Gm);
+  XS_CHECK_LAUNCH();
+}
+
 template void gbuild<double>(cudaStream_t, const DevMol&, const double*, GMode, int, const double*, double*,
                              double*, DevBuf<double>&);
+template void gbuild_raw<double>(cudaStream_t, const DevMol&, const double*, GMode, int, const double*, double*,
+                                 double*, double*, double*);
 template void gbuild<float>(cudaStream_t, const DevMol&, const double*, GMode, int, const float*, float*, float*,
                             DevBuf<float>&);
 

@@ -28,6 +28,10 @@ enum GMode { G_CIS = 0, G_RPA = 1 };
 template <typename T>
 void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* R,
             T* G, T* Gm, DevBuf<T>& ws);
+// The same with caller-provided scratch: r and J2 of np * nvec elements each.
+template <typename T>
+void gbuild_raw(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* R, T* G,
+                T* Gm, T* r, T* J2);
 
 // ---- elementwise helpers (vec.cu) ---------------------------------------------
 template <typename T>

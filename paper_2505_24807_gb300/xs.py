@@ -76,6 +76,7 @@ def load():
         "xs_excited": (i, [vp, C.POINTER(xs_ex_opts), vp, vp, vp, vp, C.POINTER(xs_solve_info)]),
         "xs_get_amplitudes": (i, [vp, i, i, vp, vp, sz]),
         "xs_profile": (i, [vp, i]),
+        "xs_gbuild_noalloc": (i, [vp, i, i, vp, vp]),
         "xs_profile_read": (i, [vp, C.POINTER(xs_prof_entry), i, C.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
@@ -196,6 +197,12 @@ def xs_get_amplitudes(ctx, mol, root):
     Y = np.empty(ov)
     _check(ctx, load().xs_get_amplitudes(ctx, int(mol), int(root), _ptr(X), _ptr(Y), ov))
     return X.reshape(o, n - o), Y.reshape(o, n - o)
+
+
+def xs_gbuild_noalloc(ctx, mol, R, G):
+    """G(R) into caller-owned device arrays, no device allocation (see xs.h).
+    Asynchronous on the context's stream."""
+    return _check(ctx, load().xs_gbuild_noalloc(ctx, int(mol), int(R.shape[0]), _ptr(R), _ptr(G)))
 
 
 def xs_profile(ctx, enable=True):
