@@ -60,6 +60,7 @@ void copy_any(cudaStream_t s, void* dst, const void* src, size_t bytes) {
 void invalidate_mixed(DevMol& m) {
   m.CTf_hi.release();
   m.CTf_lo.release();
+  m.CTf.release();
 }
 
 }  // namespace
@@ -280,6 +281,7 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
       inf.iterations = st.iterations > inf.iterations ? st.iterations : inf.iterations;
       inf.products += st.products;
       inf.converged = inf.converged && st.converged;
+      inf.polished = inf.polished || st.polished;
       tprod += st.seconds_products;
       const int kk = m.nroots;
       std::vector<double> pad(K, 0.0);

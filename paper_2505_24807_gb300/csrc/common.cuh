@@ -73,7 +73,8 @@ struct DevMol {
   DevBuf<double> H;       // core Hamiltonian n x n
   DevBuf<double> CT;      // MO coefficients, MO-major: CT[p * n + mu] = C[mu][p]
   DevBuf<double> eps;     // n orbital energies
-  DevBuf<float> CTf_hi, CTf_lo;  // split float copies of CT for the tensor-core path
+  DevBuf<float> CTf_hi, CTf_lo;  // TF32-pair operand copies of CT for the tensor-core path
+  DevBuf<float> CTf;             // float32 copy of CT for the float32 SIMT products
   bool ready = false;
   int scf_iterations = 0;
   // last excited-state solution

@@ -53,8 +53,8 @@ void sync_copy(cudaStream_t s, void* dst, const void* src, size_t bytes) {
   XS_CUDA(cudaStreamSynchronize(s));
 }
 
-// Orthonormalise the nnew rows of T against V[0:S] (classical Gram-Schmidt
-// twice) and among themselves (Loewdin, dropping directions whose Gram
+// Orthonormalise the nnew rows of T against V[0:S] (classical Gram-Schmidt,
+// repeated when the first pass cancels much of a row) and among themselves (Loewdin, dropping directions whose Gram
 // eigenvalue is below kLowdinThresh); writes the kept rows to V[S:].
 int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double* Vout) {
   cudaStream_t s = c.stream;
@@ -70,6 +70,13 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
                  w.tS.get(), nnew, 1.0, 0.0, w.gws);
     gemm<double>(s, true, false, nnew, static_cast<int>(ov), S, -1.0, w.tS.get(), nnew, 0, w.V.get(),
                  static_cast<int>(ov), 0, 1.0, w.T.get(), static_cast<int>(ov), 0, 1);
+    if (pass == 0) {
+      // a second pass only when the first removed a large part of some row
+      // (norm below 0.7 of the unit input): "twice is enough" criterion
+      row_norms(s, nnew, ov, w.T.get(), w.nrm.get());
+      sync_copy(s, h.data(), w.nrm.get(), sizeof(double) * nnew);
+      if (*std::min_element(h.begin(), h.end()) >= 0.7) break;
+    }
   }
   gram<double>(s, nnew, nnew, static_cast<int>(ov), w.T.get(), static_cast<int>(ov), w.T.get(), static_cast<int>(ov),
                w.E2.get(), nnew, 1.0, 0.0, w.gws);
@@ -195,9 +202,10 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   XS_CUDA(cudaMemsetAsync(w.flag.get(), 0, 4 * sizeof(int), s));
 
   auto t_prod = clk::duration::zero();
+  int prod_prec = opt.precision;
   auto apply = [&](int first, int count) {
     auto t0 = clk::now();
-    products(c, m, opt.method, opt.precision, count, w.V.get() + first * ov, w.S1.get() + first * ov,
+    products(c, m, opt.method, prod_prec, count, w.V.get() + first * ov, w.S1.get() + first * ov,
              rpa ? w.S2.get() + first * ov : nullptr);
     XS_CUDA(cudaStreamSynchronize(s));
     t_prod += clk::now() - t0;
@@ -211,9 +219,9 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   std::vector<double> hw(kk), hn(2 * kk), hn2(kk);
   std::vector<char> conv(kk, 0);
   int it = 0, kq = 1;
-  bool converged = false;
+  bool converged = false, polishing = false;
   int status = XS_OK;
-  for (it = 1; it <= max_iter; ++it) {
+  for (it = 1; it <= max_iter + 1; ++it) {
     // projected matrices: new columns Sold..S-1 over all rows 0..S-1
     gram<double>(s, S, S - Sold, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S1.get() + Sold * ov,
                  static_cast<int>(ov), w.a1.get() + Sold, Smax, 1.0, 0.0, w.gws);
@@ -277,8 +285,32 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       conv[j] = hn[j] <= tol_eff;
       all = all && conv[j];
     }
-    if (all && k == kk) { converged = true; break; }
-    if (it == max_iter) break;
+    if (polishing) { converged = true; st.polished = true; break; }
+    if (all && k == kk) {
+      if (opt.precision == XS_MIXED) {
+        // Rayleigh-Ritz once more in the span of the converged Ritz vectors
+        // with float32 SIMT products: the tensor cores' float32 accumulation
+        // truncates, which biases their products by ~1e-5 relative; the
+        // round-to-nearest SIMT products remove that bias from the energies.
+        const int nrows = rpa ? 2 * k : k;
+        XS_CUDA(cudaMemcpyAsync(w.T.get(), w.X.get(), sizeof(double) * k * ov, cudaMemcpyDeviceToDevice, s));
+        if (rpa)
+          XS_CUDA(cudaMemcpyAsync(w.T.get() + (size_t)k * ov, w.AX.get(), sizeof(double) * k * ov,
+                                  cudaMemcpyDeviceToDevice, s));
+        const int nb = orthonormalise_append(c, w, 0, nrows, ov, w.V.get());
+        if (nb >= k) {
+          prod_prec = kPrecF32;
+          apply(0, nb);
+          S = nb;
+          Sold = 0;
+          polishing = true;
+          continue;
+        }
+      }
+      converged = true;
+      break;
+    }
+    if (it >= max_iter) break;
     // preconditioned residuals of the unconverged roots
     if (!rpa) precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R1.get(), w.R1.get());
     else {

@@ -10,6 +10,7 @@ struct SolveStats {
   long long products = 0;
   int collapses = 0;
   bool converged = false;
+  bool polished = false;
   double seconds_products = 0.0;
 };
 

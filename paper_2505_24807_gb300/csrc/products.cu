@@ -86,10 +86,55 @@ void products_fp64(Ctx& c, const DevMol& m, int method, int nvec, const double* 
   }
 }
 
+// float32 SIMT products: float32 coefficients, R, G and integrals, float32
+// accumulation with round-to-nearest (no tensor cores); the accurate
+// reference for the final Rayleigh-Ritz step of a mixed-precision solve.
+void products_f32(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2) {
+  cudaStream_t s = c.stream;
+  const int n = m.n, o = m.o, v = m.v;
+  const long long ov = (long long)o * v, nn = (long long)n * n;
+  if (!m.Wf.get()) {
+    m.Wf.alloc((size_t)m.np * m.np);
+    convert_d2f(s, (long long)m.np * m.np, m.W.get(), m.Wf.get());
+  }
+  if (!m.CTf.get()) {
+    m.CTf.alloc(nn);
+    convert_d2f(s, nn, m.CT.get(), m.CTf.get());
+  }
+  const int nb = product_batch(m);
+  const int chunk = nvec < nb ? nvec : nb;
+  const size_t tmpn = (size_t)chunk * n * (o > v ? o : v);
+  c.fs2.ensure((size_t)chunk * nn * 3 + tmpn + (size_t)chunk * ov * 2);
+  float* R = c.fs2.get();
+  float* G = R + (size_t)chunk * nn;
+  float* Gm = G + (size_t)chunk * nn;
+  float* tmp = Gm + (size_t)chunk * nn;
+  float* Xf = tmp + tmpn;
+  float* Yf = Xf + (size_t)chunk * ov;
+  for (int k0 = 0; k0 < nvec; k0 += chunk) {
+    const int k = (nvec - k0) < chunk ? (nvec - k0) : chunk;
+    const double* Xk = X + k0 * ov;
+    convert_d2f(s, k * ov, Xk, Xf);
+    pbuild<float>(s, n, o, v, k, m.CTf.get(), Xf, R, tmp);
+    const bool rpa = method != XS_CIS;
+    gbuild<float>(s, m, c.d_par.get(), rpa ? G_RPA : G_CIS, k, R, G, rpa ? Gm : nullptr, c.fs1);
+    for (int pass = 0; pass < (rpa ? 2 : 1); ++pass) {
+      double* Y = (pass == 0 ? Y1 : Y2) + k0 * ov;
+      backtransform<float>(s, n, o, v, k, m.CTf.get(), pass == 0 ? G : Gm, Yf, tmp);
+      convert_f2d(s, k * ov, Yf, Y);
+      add_diag_term<double>(s, k, o, v, m.eps.get(), Xk, Y);
+    }
+  }
+}
+
 void products(Ctx& c, DevMol& m, int method, int precision, int nvec, const double* X, double* Y1, double* Y2) {
   if (nvec <= 0) return;
   if (precision == XS_MIXED) {
     products_mixed(c, m, method, nvec, X, Y1, Y2);
+    return;
+  }
+  if (precision == kPrecF32) {
+    products_f32(c, m, method, nvec, X, Y1, Y2);
     return;
   }
   products_fp64(c, m, method, nvec, X, Y1, Y2);

@@ -5,6 +5,9 @@
 
 namespace xs {
 
+// internal precision code: float32 SIMT products (polish step of mixed solves)
+constexpr int kPrecF32 = 2;
+
 // Y1 = A X (CIS) or Y1 = (A+B) X, Y2 = (A-B) X (TDHF) for nvec vectors
 // X (nvec x nocc x nvir, float64, device).  precision: XS_FP64 or XS_MIXED.
 void products(Ctx& c, DevMol& m, int method, int precision, int nvec, const double* X, double* Y1, double* Y2);

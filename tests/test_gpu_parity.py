@@ -139,9 +139,9 @@ def test_unstable_reference_reported():
     from oracle import excited, nddo
     params = copy.deepcopy(molgen.make_params(0))
     for z in params:
-        params[z]["beta_s"] *= 0.7
-        params[z]["beta_p"] *= 0.7
-    Z, xyz = molgen.config_small(3)
+        params[z]["beta_s"] *= 0.6
+        params[z]["beta_p"] *= 0.6
+    Z, xyz = molgen.config_small(0)
     Z = Z.copy()
     Z[Z > 1] = 8
     mol, ints, res = oracle_ground_state(Z, xyz, params)
