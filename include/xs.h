@@ -99,7 +99,9 @@ typedef struct {
   int iterations;       /* Davidson iterations of the slowest molecule */
   long long products;   /* trial vectors multiplied (sum over molecules) */
   int converged;        /* 1 if every root of every molecule converged */
-  int polished;         /* 1 if a float64 Rayleigh-Ritz polish followed a mixed solve */
+  int polished;         /* 1 if a float32-SIMT Rayleigh-Ritz step followed a mixed solve */
+  int learned;          /* 1 if the learned guess and diagonal shift were used */
+  int fallback;         /* 1 if the learned shift was dropped because a residual stalled */
   double seconds;       /* wall time of the call */
   double seconds_products;  /* of which in A*X products */
 } xs_solve_info;
@@ -160,6 +162,44 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
  * X (and Y for TDHF; Y may be NULL) of nocc*nvir float64 each, normalised
  * |X|^2 - |Y|^2 = 1.  `ov` must equal nocc*nvir.  Host or device pointers. */
 int xs_get_amplitudes(const xs_ctx* ctx, int mol, int root, double* X, double* Y, size_t ov);
+
+/* ---- learned Davidson guess and preconditioner ----------------------------
+ * Not in the paper: a small MLP (XS_MLP_FEATURES -> 256 -> 256 -> 256 -> 2,
+ * gelu, weights rounded to bfloat16, float32 accumulation) maps per-pair
+ * features of the lowest orbital-energy gaps to (0) the diagonal shift
+ * A_ia,ia - (eps_a - eps_i) = 2(ia|ia) - (ij|ab)|_{j=i,b=a}, used as the
+ * preconditioner r / (omega - d eps - shift), and (1) log10 of the pair's
+ * weight sum_n X_n,ia^2 in the lowest roots, used to pick the start vectors.
+ * xs_excited uses it when opts->guess == XS_GUESS_LEARNED and a network is
+ * loaded; the plain Davidson still decides convergence and the shift is
+ * dropped when a residual stalls, so converged roots do not change. */
+#define XS_MLP_FEATURES 10
+
+/* number of float32 parameters of the network (weights and biases, layer by
+ * layer: W (out x in) row-major, then b) */
+int xs_mlp_nparams(void);
+/* initialise the context's network (uniform +-1/sqrt(fan_in) weights, zero biases) */
+int xs_mlp_init(xs_ctx* ctx, unsigned long long seed);
+/* copy the parameters out / in (host or device, xs_mlp_nparams() floats) */
+int xs_mlp_get_weights(xs_ctx* ctx, float* w);
+int xs_mlp_set_weights(xs_ctx* ctx, const float* w);
+/* features of the npairs lowest-gap pairs of molecule `mol`: features
+ * (npairs x XS_MLP_FEATURES float32) and the pairs (flattened i * nvir + a);
+ * returns the number of pairs written in *count (<= npairs) */
+int xs_mlp_features(xs_ctx* ctx, int mol, int npairs, float* features, long long* pairs, int* count);
+/* training targets of the given pairs (npairs x 2 float32): exact diagonal
+ * shift (eV) and log10(max(sum over the last solve's roots of (X+Y)_ia^2, 1e-6)) */
+int xs_mlp_targets(xs_ctx* ctx, int mol, int npairs, const long long* pairs, float* targets);
+/* network outputs (rows x 2) for the given features */
+int xs_mlp_forward(xs_ctx* ctx, int rows, const float* features, float* out);
+/* gradient of the weighted loss (see xs_mlp_train) with respect to every
+ * parameter (xs_mlp_nparams() floats, host or device), and the loss */
+int xs_mlp_grad(xs_ctx* ctx, int rows, const float* features, const float* targets, float* grad, float* loss);
+/* Adam training on the GPU: `epochs` passes over rows samples in minibatches
+ * of `batch` rows (in the given order), learning rate lr, loss weights 0.01
+ * (shift, eV^2) and 1 (log-weight); mean loss per epoch in loss (epochs). */
+int xs_mlp_train(xs_ctx* ctx, int rows, const float* features, const float* targets, int epochs, int batch,
+                 float lr, float* loss);
 
 /* Allocation-free G(R) build: the same G = 2J(R) - K(R) as
  * xs_apply(ctx, mol, XS_KIND_G, nvec, R, G, XS_FP64), for callers that must not

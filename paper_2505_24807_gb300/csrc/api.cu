@@ -1,9 +1,12 @@
 // C ABI of libxs (declared and documented in include/xs.h).
+#include <atomic>
 #include <chrono>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "davidson.h"
+#include "mlp.h"
 #include "kernels.h"
 #include "products.h"
 #include "scf.h"
@@ -55,6 +58,22 @@ void upload(cudaStream_t s, DevBuf<T>& d, const std::vector<T>& h) {
 void copy_any(cudaStream_t s, void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return;
   XS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+}
+
+// A worker context for batched solves: the parent's parameters, its own
+// non-blocking stream and scratch buffers.
+std::unique_ptr<Ctx> make_worker(const Ctx& parent) {
+  std::unique_ptr<Ctx> w(new Ctx());
+  w->device = parent.device;
+  for (int e = 0; e < XS_NELEM; ++e) w->par[e] = parent.par[e];
+  w->have_params = true;
+  XS_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+  w->own_stream = true;
+  w->d_par.alloc(parent.d_par.n);
+  XS_CUDA(cudaMemcpyAsync(w->d_par.get(), parent.d_par.get(), sizeof(double) * parent.d_par.n,
+                          cudaMemcpyDeviceToDevice, w->stream));
+  XS_CUDA(cudaStreamSynchronize(w->stream));
+  return w;
 }
 
 void invalidate_mixed(DevMol& m) {
@@ -271,10 +290,52 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
     xs_solve_info inf{};
     inf.converged = 1;
     double tprod = 0.0;
-    for (size_t i = 0; i < c.mols.size(); ++i) {
-      DevMol& m = molecule(c, static_cast<int>(i));
-      xs::SolveStats st;
-      int rc = xs::davidson(c, m, o, st);
+    const int nmol = static_cast<int>(c.mols.size());
+    std::vector<xs::SolveStats> stats(nmol);
+    std::vector<int> rcs(nmol, XS_OK);
+    if (o.batched && nmol > 1) {
+      // molecules advance concurrently: one host thread per worker context,
+      // each launching on its own stream; the GPU overlaps their kernels
+      unsigned hw = std::thread::hardware_concurrency();
+      const int nw = std::max(1, std::min<int>(nmol, std::min<int>(hw ? static_cast<int>(hw) : 8, 16)));
+      while (static_cast<int>(c.workers.size()) < nw) c.workers.push_back(make_worker(c));
+      for (auto& wk : c.workers) wk->mlp = c.mlp;
+      XS_CUDA(cudaStreamSynchronize(c.stream));
+      std::atomic<int> next{0};
+      std::vector<std::string> errs(nmol);
+      std::vector<std::thread> th;
+      for (int t = 0; t < nw; ++t) {
+        th.emplace_back([&, t]() {
+          cudaSetDevice(c.device);
+          Ctx& w = *c.workers[t];
+          for (int i = next++; i < nmol; i = next++) {
+            try {
+              rcs[i] = xs::davidson(w, c.mols[i], o, stats[i]);
+            } catch (const Error& e) {
+              rcs[i] = e.status;
+              errs[i] = e.what();
+            } catch (const std::exception& e) {
+              rcs[i] = XS_ECUDA;
+              errs[i] = e.what();
+            }
+          }
+          cudaStreamSynchronize(w.stream);
+        });
+      }
+      for (auto& x : th) x.join();
+      for (int i = 0; i < nmol; ++i)
+        if (!errs[i].empty()) throw Error(rcs[i], "molecule " + std::to_string(i) + ": " + errs[i]);
+    } else {
+      for (int i = 0; i < nmol; ++i) {
+        molecule(c, i);
+        rcs[i] = xs::davidson(c, c.mols[i], o, stats[i]);
+      }
+    }
+    for (int ii = 0; ii < nmol; ++ii) {
+      const size_t i = static_cast<size_t>(ii);
+      DevMol& m = molecule(c, ii);
+      xs::SolveStats& st = stats[ii];
+      int rc = rcs[ii];
       if (rc == XS_EUNSTABLE) throw Error(XS_EUNSTABLE, "A - B is not positive definite (molecule " +
                                                             std::to_string(i) + ")");
       if (rc != XS_OK) status = rc;
@@ -282,6 +343,8 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
       inf.products += st.products;
       inf.converged = inf.converged && st.converged;
       inf.polished = inf.polished || st.polished;
+      inf.learned = inf.learned || st.learned;
+      inf.fallback = inf.fallback || st.fallback;
       tprod += st.seconds_products;
       const int kk = m.nroots;
       std::vector<double> pad(K, 0.0);
@@ -335,6 +398,153 @@ int xs_get_amplitudes(const xs_ctx* cctx, int mol, int root, double* X, double* 
       xs::scal(s, n_ov, 0.5, t.get());
       copy_any(s, Y, t.get(), sizeof(double) * n_ov);
       XS_CUDA(cudaStreamSynchronize(s));
+    }
+    return XS_OK;
+  });
+}
+
+int xs_mlp_nparams(void) {
+  xs::Mlp m;
+  return m.nparams();
+}
+
+int xs_mlp_init(xs_ctx* ctx, unsigned long long seed) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (!c.mlp) c.mlp = std::make_shared<xs::Mlp>();
+    c.mlp->init(c.stream, seed);
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    return XS_OK;
+  });
+}
+
+int xs_mlp_get_weights(xs_ctx* ctx, float* w) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (!c.mlp || !c.mlp->ready) throw Error(XS_ESTATE, "no network");
+    if (!w) throw Error(XS_EINVAL, "null buffer");
+    std::vector<float> h(c.mlp->nparams());
+    c.mlp->get(c.stream, h.data());
+    copy_any(c.stream, w, h.data(), sizeof(float) * h.size());
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    return XS_OK;
+  });
+}
+
+int xs_mlp_set_weights(xs_ctx* ctx, const float* w) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (!w) throw Error(XS_EINVAL, "null buffer");
+    if (!c.mlp) c.mlp = std::make_shared<xs::Mlp>();
+    std::vector<float> h(c.mlp->nparams());
+    copy_any(c.stream, h.data(), w, sizeof(float) * h.size());
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    c.mlp->set(c.stream, h.data());
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    return XS_OK;
+  });
+}
+
+int xs_mlp_features(xs_ctx* ctx, int mol, int npairs, float* features, long long* pairs, int* count) {
+  return guarded(ctx, [&](Ctx& c) {
+    DevMol& m = molecule(c, mol);
+    if (npairs <= 0 || !features) throw Error(XS_EINVAL, "bad request");
+    std::vector<long long> pr = xs::lowest_gap_pairs(c, m, npairs);
+    DevBuf<float> F(pr.size() * xs::kMlpFeatures);
+    DevBuf<long long> dp;
+    xs::pair_features(c, m, pr, F.get(), dp);
+    copy_any(c.stream, features, F.get(), sizeof(float) * F.n);
+    if (pairs) copy_any(c.stream, pairs, pr.data(), sizeof(long long) * pr.size());
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    if (count) *count = static_cast<int>(pr.size());
+    return XS_OK;
+  });
+}
+
+int xs_mlp_targets(xs_ctx* ctx, int mol, int npairs, const long long* pairs, float* targets) {
+  return guarded(ctx, [&](Ctx& c) {
+    DevMol& m = molecule(c, mol);
+    if (npairs <= 0 || !pairs || !targets) throw Error(XS_EINVAL, "bad request");
+    if (m.nroots == 0) throw Error(XS_ESTATE, "solve the molecule first (amplitudes give the weight targets)");
+    std::vector<long long> pr(npairs);
+    copy_any(c.stream, pr.data(), pairs, sizeof(long long) * npairs);
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    const long long ov = (long long)m.o * m.v;
+    for (long long p : pr)
+      if (p < 0 || p >= ov) throw Error(XS_EINVAL, "pair index out of range");
+    DevBuf<double> sh(npairs);
+    xs::diagonal_shift(c, m, pr, sh.get());
+    std::vector<double> shh(npairs);
+    XS_CUDA(cudaMemcpyAsync(shh.data(), sh.get(), sizeof(double) * npairs, cudaMemcpyDeviceToHost, c.stream));
+    // weight of each pair in the stored roots (X+Y for TDHF, X for CIS)
+    std::vector<double> U((size_t)m.nroots * ov);
+    XS_CUDA(cudaMemcpyAsync(U.data(), m.U.get(), sizeof(double) * U.size(), cudaMemcpyDeviceToHost, c.stream));
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    std::vector<float> t((size_t)npairs * 2);
+    for (int q = 0; q < npairs; ++q) {
+      double wgt = 0.0;
+      for (int r = 0; r < m.nroots; ++r) {
+        const double u = U[(size_t)r * ov + pr[q]];
+        wgt += u * u;
+      }
+      t[2 * q] = static_cast<float>(shh[q]);
+      t[2 * q + 1] = static_cast<float>(std::log10(std::max(wgt, 1e-6)));
+    }
+    copy_any(c.stream, targets, t.data(), sizeof(float) * t.size());
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    return XS_OK;
+  });
+}
+
+int xs_mlp_forward(xs_ctx* ctx, int rows, const float* features, float* out) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (!c.mlp || !c.mlp->ready) throw Error(XS_ESTATE, "no network");
+    if (rows <= 0 || !features || !out) throw Error(XS_EINVAL, "bad request");
+    DevBuf<float> F((size_t)rows * xs::kMlpFeatures);
+    copy_any(c.stream, F.get(), features, sizeof(float) * F.n);
+    std::vector<DevBuf<float>> Z, H;
+    c.mlp->forward(c.stream, rows, F.get(), Z, H);
+    copy_any(c.stream, out, H[xs::kMlpLayers - 1].get(), sizeof(float) * rows * xs::kMlpOutputs);
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    return XS_OK;
+  });
+}
+
+int xs_mlp_grad(xs_ctx* ctx, int rows, const float* features, const float* targets, float* grad, float* loss) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (!c.mlp || !c.mlp->ready) throw Error(XS_ESTATE, "initialise or load the network first");
+    if (rows <= 0 || !features || !targets || !grad) throw Error(XS_EINVAL, "bad request");
+    DevBuf<float> F((size_t)rows * xs::kMlpFeatures), T((size_t)rows * xs::kMlpOutputs), colw(2), scratch;
+    copy_any(c.stream, F.get(), features, sizeof(float) * F.n);
+    copy_any(c.stream, T.get(), targets, sizeof(float) * T.n);
+    const float cw[2] = {0.01f, 1.0f};
+    copy_any(c.stream, colw.get(), cw, sizeof(cw));
+    const float l = c.mlp->gradient(c.stream, rows, F.get(), T.get(), colw.get(), scratch);
+    copy_any(c.stream, grad, c.mlp->g.get(), sizeof(float) * c.mlp->nparams());
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    if (loss) *loss = l;
+    return XS_OK;
+  });
+}
+
+int xs_mlp_train(xs_ctx* ctx, int rows, const float* features, const float* targets, int epochs, int batch,
+                 float lr, float* loss) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (!c.mlp || !c.mlp->ready) throw Error(XS_ESTATE, "initialise or load the network first");
+    if (rows <= 0 || epochs <= 0 || batch <= 0 || !features || !targets) throw Error(XS_EINVAL, "bad request");
+    DevBuf<float> F((size_t)rows * xs::kMlpFeatures), T((size_t)rows * xs::kMlpOutputs), colw(2), scratch;
+    copy_any(c.stream, F.get(), features, sizeof(float) * F.n);
+    copy_any(c.stream, T.get(), targets, sizeof(float) * T.n);
+    const float cw[2] = {0.01f, 1.0f};
+    copy_any(c.stream, colw.get(), cw, sizeof(cw));
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    for (int e = 0; e < epochs; ++e) {
+      double sum = 0.0;
+      int nb = 0;
+      for (int r0 = 0; r0 < rows; r0 += batch) {
+        const int rb = std::min(batch, rows - r0);
+        sum += c.mlp->train_step(c.stream, rb, F.get() + (size_t)r0 * xs::kMlpFeatures,
+                                 T.get() + (size_t)r0 * xs::kMlpOutputs, colw.get(), lr, scratch);
+        ++nb;
+      }
+      if (loss) loss[e] = static_cast<float>(sum / nb);
     }
     return XS_OK;
   });

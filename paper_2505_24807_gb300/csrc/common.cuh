@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -12,6 +13,10 @@
 #include "../../include/xs.h"
 #include "model.h"
 #include "prof.h"
+
+namespace xs {
+struct Mlp;
+}
 
 namespace xs {
 
@@ -99,6 +104,10 @@ struct Ctx {
   DevBuf<float> fs0, fs1, fs2;
   Profiler prof;
   DevBuf<int> tc_err;   // error word of the tensor-core kernels' bounded waits
+  // batched solves: worker contexts (own stream and scratch), reused across calls
+  std::vector<std::unique_ptr<Ctx>> workers;
+  // learned guess / preconditioner network (shared by the workers)
+  std::shared_ptr<Mlp> mlp;
 };
 
 inline dim3 grid1(long long n, int block) { return dim3(static_cast<unsigned>((n + block - 1) / block)); }

@@ -27,6 +27,7 @@
 #include "products.h"
 #include "small.h"
 #include "syev.h"
+#include "mlp.h"
 
 namespace xs {
 
@@ -90,18 +91,24 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
   return nkeep;
 }
 
-// guess: unit vectors on the nguess lowest eps_a - eps_i (ties: lower i, then a)
-void make_guess(Ctx& c, const DevMol& m, Work& w, int nguess, long long ov) {
+// guess: unit vectors on the nguess lowest eps_a - eps_i (ties: lower i, then a),
+// or on the given pair list (learned guess)
+void make_guess(Ctx& c, const DevMol& m, Work& w, int nguess, long long ov, const std::vector<long long>* chosen) {
   cudaStream_t s = c.stream;
-  std::vector<double> eps(m.n);
-  sync_copy(s, eps.data(), m.eps.get(), sizeof(double) * m.n);
-  std::vector<long long> order(ov);
-  std::iota(order.begin(), order.end(), 0LL);
-  auto de = [&](long long k) { return eps[m.o + k % m.v] - eps[k / m.v]; };
-  std::partial_sort(order.begin(), order.begin() + nguess, order.end(), [&](long long x, long long y) {
-    double dx = de(x), dy = de(y);
-    return dx < dy || (dx == dy && x < y);
-  });
+  std::vector<long long> order;
+  if (chosen) {
+    order = *chosen;
+  } else {
+    std::vector<double> eps(m.n);
+    sync_copy(s, eps.data(), m.eps.get(), sizeof(double) * m.n);
+    order.resize(ov);
+    std::iota(order.begin(), order.end(), 0LL);
+    auto de = [&](long long k) { return eps[m.o + k % m.v] - eps[k / m.v]; };
+    std::partial_sort(order.begin(), order.begin() + nguess, order.end(), [&](long long x, long long y) {
+      double dx = de(x), dy = de(y);
+      return dx < dy || (dx == dy && x < y);
+    });
+  }
   XS_CUDA(cudaMemsetAsync(w.V.get(), 0, sizeof(double) * nguess * ov, s));
   w.idx.ensure(nguess);
   XS_CUDA(cudaMemcpyAsync(w.idx.get(), order.data(), sizeof(long long) * nguess, cudaMemcpyHostToDevice, s));
@@ -212,7 +219,41 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     st.products += count;
   };
 
-  make_guess(c, m, w, nguess, ov);
+  // learned guess and diagonal shift: MLP outputs on the lowest-gap pairs
+  DevBuf<double> lshift;
+  const double* shift = nullptr;
+  std::vector<long long> learned_pairs;
+  if (opt.guess == XS_GUESS_LEARNED && c.mlp && c.mlp->ready) {
+    const int npairs = static_cast<int>(std::min<long long>(ov, 65536));
+    std::vector<long long> pairs = lowest_gap_pairs(c, m, npairs);
+    DevBuf<float> F((size_t)pairs.size() * kMlpFeatures);
+    DevBuf<long long> dpairs;
+    pair_features(c, m, pairs, F.get(), dpairs);
+    std::vector<DevBuf<float>> Z, H;
+    c.mlp->forward(s, static_cast<int>(pairs.size()), F.get(), Z, H);
+    std::vector<float> out(pairs.size() * kMlpOutputs);
+    sync_copy(s, out.data(), H[kMlpLayers - 1].get(), sizeof(float) * out.size());
+    // preconditioner shift on the candidate pairs, zero elsewhere
+    std::vector<double> sh(pairs.size());
+    for (size_t q = 0; q < pairs.size(); ++q) sh[q] = out[q * kMlpOutputs];
+    lshift.alloc((size_t)ov);
+    XS_CUDA(cudaMemsetAsync(lshift.get(), 0, sizeof(double) * ov, s));
+    DevBuf<double> dsh(sh.size());
+    XS_CUDA(cudaMemcpyAsync(dsh.get(), sh.data(), sizeof(double) * sh.size(), cudaMemcpyHostToDevice, s));
+    scatter(s, static_cast<int>(pairs.size()), dpairs.get(), dsh.get(), lshift.get());
+    XS_CUDA(cudaStreamSynchronize(s));
+    shift = lshift.get();
+    // guess: the pairs with the highest predicted weight in the low roots
+    std::vector<size_t> idx(pairs.size());
+    std::iota(idx.begin(), idx.end(), size_t(0));
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+      return out[x * kMlpOutputs + 1] > out[y * kMlpOutputs + 1];
+    });
+    for (int q = 0; q < nguess; ++q) learned_pairs.push_back(pairs[idx[q]]);
+    st.learned = true;
+  }
+  make_guess(c, m, w, nguess, ov, learned_pairs.empty() ? nullptr : &learned_pairs);
+  std::vector<double> max_res_hist;
   int S = nguess, Sold = 0;
   apply(0, S);
 
@@ -312,10 +353,18 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     }
     if (it >= max_iter) break;
     // preconditioned residuals of the unconverged roots
-    if (!rpa) precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R1.get(), w.R1.get());
+    // fallback: drop the learned shift when the largest residual has not
+    // fallen by 10% over the last three iterations
+    max_res_hist.push_back(*std::max_element(hn.begin(), hn.begin() + k));
+    if (shift && max_res_hist.size() > 3 &&
+        max_res_hist.back() > 0.9 * max_res_hist[max_res_hist.size() - 4]) {
+      shift = nullptr;
+      st.fallback = true;
+    }
+    if (!rpa) precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R1.get(), w.R1.get(), shift);
     else {
-      precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R1.get(), w.R1.get());
-      precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R2.get(), w.R2.get());
+      precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R1.get(), w.R1.get(), shift);
+      precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R2.get(), w.R2.get(), shift);
     }
     int nnew = 0;
     for (int j = 0; j < k; ++j) {

@@ -11,6 +11,8 @@ struct SolveStats {
   int collapses = 0;
   bool converged = false;
   bool polished = false;
+  bool learned = false;    // learned guess and shift were used
+  bool fallback = false;   // the learned shift was dropped for a stalled residual
   double seconds_products = 0.0;
 };
 

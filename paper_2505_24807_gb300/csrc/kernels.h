@@ -37,7 +37,8 @@ void gbuild_raw(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode
 template <typename T>
 void add_diag_term(cudaStream_t s, int nvec, int o, int v, const double* eps, const T* X, T* Y);
 void precondition(cudaStream_t s, int nvec, int o, int v, const double* eps, const double* omega,
-                  const double* R, double* T);
+                  const double* R, double* T, const double* shift = nullptr);
+void scatter(cudaStream_t s, int n, const long long* idx, const double* val, double* out);  // out[idx[k]] = val[k]
 void residual_norms(cudaStream_t s, int nvec, long long len, const double* A, const double* B,
                     const double* omega, double* out_norm, double* R);
 void row_norms(cudaStream_t s, int nvec, long long len, const double* X, double* out_norm);

@@ -1,0 +1,42 @@
+// Learned Davidson guess and diagonal preconditioner of libxs (mlp.cu).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace xs {
+
+constexpr int kMlpFeatures = 10;
+constexpr int kMlpHidden = 256;
+constexpr int kMlpLayers = 4;
+constexpr int kMlpOutputs = 2;   // 0: diagonal shift (eV), 1: log10 pair weight
+
+struct Mlp {
+  int sizes[kMlpLayers + 1] = {kMlpFeatures, kMlpHidden, kMlpHidden, kMlpHidden, kMlpOutputs};
+  DevBuf<float> w, wq, m, v, g;   // master weights, bfloat16-rounded copy, Adam moments, gradient
+  int step = 0;
+  bool ready = false;
+  int nparams() const;
+  void init(cudaStream_t s, unsigned long long seed);
+  void set(cudaStream_t s, const float* host);
+  void get(cudaStream_t s, float* host) const;
+  void forward(cudaStream_t s, int rows, const float* X, std::vector<DevBuf<float>>& Z,
+               std::vector<DevBuf<float>>& H) const;
+  // gradient (into g) of the weighted mean-squared error with respect to the
+  // parameters, evaluated with the bfloat16-rounded weights; returns the loss
+  float gradient(cudaStream_t s, int rows, const float* X, const float* T, const float* colw, DevBuf<float>& scratch);
+  // one Adam step on the weighted mean-squared error; returns the loss
+  float train_step(cudaStream_t s, int rows, const float* X, const float* T, const float* colw, float lr,
+                   DevBuf<float>& scratch);
+};
+
+// the npairs lowest eps_a - eps_i pairs (flattened i * nvir + a), ties by index
+std::vector<long long> lowest_gap_pairs(Ctx& c, const DevMol& m, int npairs);
+// features (npairs x kMlpFeatures, device) of the given pairs
+void pair_features(Ctx& c, const DevMol& m, const std::vector<long long>& pairs, float* F_dev,
+                   DevBuf<long long>& dpairs);
+// exact diagonal shift 2 (ia|ia) - (ii|aa) of the given pairs (device, float64)
+void diagonal_shift(Ctx& c, const DevMol& m, const std::vector<long long>& pairs, double* shift_dev);
+
+}  // namespace xs

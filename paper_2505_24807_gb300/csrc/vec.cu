@@ -21,17 +21,17 @@ __global__ void diag_term_kernel(int nvec, int o, int v, const double* __restric
   Y[idx] = static_cast<T>(static_cast<double>(Y[idx]) + de * static_cast<double>(X[idx]));
 }
 
-// t = r / (omega - d eps), denominator magnitude clamped to >= 1e-4 eV
+// t = r / (omega - d eps - shift), denominator magnitude clamped to >= 1e-4 eV
 __global__ void precond_kernel(int nvec, int o, int v, const double* __restrict__ eps,
                                const double* __restrict__ omega, const double* __restrict__ R,
-                               double* __restrict__ Tt) {
+                               double* __restrict__ Tt, const double* __restrict__ shift) {
   long long ov = (long long)o * v;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= ov * nvec) return;
   int k = static_cast<int>(idx / ov);
   long long e = idx % ov;
   int i = static_cast<int>(e / v), a = static_cast<int>(e % v);
-  double d = omega[k] - (eps[o + a] - eps[i]);
+  double d = omega[k] - (eps[o + a] - eps[i]) - (shift ? shift[e] : 0.0);
   if (fabs(d) < 1e-4) d = (d < 0.0) ? -1e-4 : 1e-4;
   Tt[idx] = R[idx] / d;
 }
@@ -112,6 +112,11 @@ __global__ void maxabs_kernel(long long n, const double* __restrict__ a, unsigne
   // non-negative doubles order like their bit patterns
   if ((threadIdx.x & 31) == 0) atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(m)));
 }
+__global__ void scatter_kernel(int n, const long long* __restrict__ idx, const double* __restrict__ val,
+                               double* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[idx[k]] = val[k];
+}
 __global__ void transpose_kernel(int rows, int cols, const double* __restrict__ a, double* __restrict__ b) {
   __shared__ double tile[32][33];
   int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 32 + threadIdx.y;
@@ -137,10 +142,10 @@ template void add_diag_term<double>(cudaStream_t, int, int, int, const double*, 
 template void add_diag_term<float>(cudaStream_t, int, int, int, const double*, const float*, float*);
 
 void precondition(cudaStream_t s, int nvec, int o, int v, const double* eps, const double* omega, const double* R,
-                  double* T) {
+                  double* T, const double* shift) {
   long long n = (long long)nvec * o * v;
   if (n == 0) return;
-  precond_kernel<<<grid1(n, 256), 256, 0, s>>>(nvec, o, v, eps, omega, R, T);
+  precond_kernel<<<grid1(n, 256), 256, 0, s>>>(nvec, o, v, eps, omega, R, T, shift);
   XS_CHECK_LAUNCH();
 }
 
@@ -201,6 +206,11 @@ void max_abs(cudaStream_t s, long long n, const double* a, double* out) {
   if (n == 0) return;
   int blocks = static_cast<int>(std::min<long long>(1024, (n + 255) / 256));
   maxabs_kernel<<<blocks, 256, 0, s>>>(n, a, reinterpret_cast<unsigned long long*>(out));
+  XS_CHECK_LAUNCH();
+}
+void scatter(cudaStream_t s, int n, const long long* idx, const double* val, double* out) {
+  if (n == 0) return;
+  scatter_kernel<<<grid1(n, 256), 256, 0, s>>>(n, idx, val, out);
   XS_CHECK_LAUNCH();
 }
 void transpose(cudaStream_t s, int rows, int cols, const double* a, double* b) {

@@ -21,6 +21,7 @@ XS_FP64, XS_MIXED = 0, 1
 XS_KIND_A, XS_KIND_APB, XS_KIND_AMB, XS_KIND_G = 0, 1, 2, 3
 XS_GUESS_PLAIN, XS_GUESS_LEARNED = 0, 1
 XS_NPARAM, XS_NELEM = 13, 4
+XS_MLP_FEATURES = 10
 
 STATUS_NAMES = {0: "XS_OK", -1: "XS_EINVAL", -2: "XS_ENOMEM", -3: "XS_ESCF", -4: "XS_EUNSTABLE",
                 -5: "XS_ENOCONV", -6: "XS_ECUDA", -7: "XS_ETIMEOUT", -8: "XS_ESTATE"}
@@ -43,7 +44,8 @@ class xs_ex_opts(C.Structure):
 
 class xs_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("products", C.c_longlong), ("converged", C.c_int),
-                ("polished", C.c_int), ("seconds", C.c_double), ("seconds_products", C.c_double)]
+                ("polished", C.c_int), ("learned", C.c_int), ("fallback", C.c_int), ("seconds", C.c_double),
+                ("seconds_products", C.c_double)]
 
 
 class xs_prof_entry(C.Structure):
@@ -77,6 +79,15 @@ def load():
         "xs_get_amplitudes": (i, [vp, i, i, vp, vp, sz]),
         "xs_profile": (i, [vp, i]),
         "xs_gbuild_noalloc": (i, [vp, i, i, vp, vp]),
+        "xs_mlp_nparams": (i, []),
+        "xs_mlp_init": (i, [vp, C.c_ulonglong]),
+        "xs_mlp_get_weights": (i, [vp, vp]),
+        "xs_mlp_set_weights": (i, [vp, vp]),
+        "xs_mlp_features": (i, [vp, i, i, vp, vp, C.POINTER(i)]),
+        "xs_mlp_targets": (i, [vp, i, i, vp, vp]),
+        "xs_mlp_forward": (i, [vp, i, vp, vp]),
+        "xs_mlp_train": (i, [vp, i, vp, vp, i, i, C.c_float, vp]),
+        "xs_mlp_grad": (i, [vp, i, vp, vp, vp, C.POINTER(C.c_float)]),
         "xs_profile_read": (i, [vp, C.POINTER(xs_prof_entry), i, C.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
@@ -203,6 +214,65 @@ def xs_gbuild_noalloc(ctx, mol, R, G):
     """G(R) into caller-owned device arrays, no device allocation (see xs.h).
     Asynchronous on the context's stream."""
     return _check(ctx, load().xs_gbuild_noalloc(ctx, int(mol), int(R.shape[0]), _ptr(R), _ptr(G)))
+
+
+def xs_mlp_nparams():
+    return int(load().xs_mlp_nparams())
+
+
+def xs_mlp_init(ctx, seed=0):
+    return _check(ctx, load().xs_mlp_init(ctx, int(seed)))
+
+
+def xs_mlp_get_weights(ctx):
+    w = np.empty(xs_mlp_nparams(), dtype=np.float32)
+    _check(ctx, load().xs_mlp_get_weights(ctx, _ptr(w)))
+    return w
+
+
+def xs_mlp_set_weights(ctx, w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    return _check(ctx, load().xs_mlp_set_weights(ctx, _ptr(w)))
+
+
+def xs_mlp_features(ctx, mol, npairs):
+    F = np.empty((npairs, XS_MLP_FEATURES), dtype=np.float32)
+    P = np.empty(npairs, dtype=np.int64)
+    cnt = C.c_int()
+    _check(ctx, load().xs_mlp_features(ctx, int(mol), int(npairs), _ptr(F), _ptr(P), C.byref(cnt)))
+    return F[: cnt.value], P[: cnt.value]
+
+
+def xs_mlp_targets(ctx, mol, pairs):
+    pairs = np.ascontiguousarray(pairs, dtype=np.int64)
+    T = np.empty((pairs.size, 2), dtype=np.float32)
+    _check(ctx, load().xs_mlp_targets(ctx, int(mol), int(pairs.size), _ptr(pairs), _ptr(T)))
+    return T
+
+
+def xs_mlp_forward(ctx, features):
+    F = np.ascontiguousarray(features, dtype=np.float32)
+    out = np.empty((F.shape[0], 2), dtype=np.float32)
+    _check(ctx, load().xs_mlp_forward(ctx, int(F.shape[0]), _ptr(F), _ptr(out)))
+    return out
+
+
+def xs_mlp_grad(ctx, features, targets):
+    F = np.ascontiguousarray(features, dtype=np.float32)
+    T = np.ascontiguousarray(targets, dtype=np.float32)
+    g = np.empty(xs_mlp_nparams(), dtype=np.float32)
+    loss = C.c_float()
+    _check(ctx, load().xs_mlp_grad(ctx, int(F.shape[0]), _ptr(F), _ptr(T), _ptr(g), C.byref(loss)))
+    return g, loss.value
+
+
+def xs_mlp_train(ctx, features, targets, epochs=10, batch=4096, lr=1e-3):
+    F = np.ascontiguousarray(features, dtype=np.float32)
+    T = np.ascontiguousarray(targets, dtype=np.float32)
+    loss = np.zeros(int(epochs), dtype=np.float32)
+    _check(ctx, load().xs_mlp_train(ctx, int(F.shape[0]), _ptr(F), _ptr(T), int(epochs), int(batch), float(lr),
+                                    _ptr(loss)))
+    return loss
 
 
 def xs_profile(ctx, enable=True):

@@ -1,0 +1,109 @@
+"""Learned Davidson guess and preconditioner: the network kernels against the
+oracle MLP, the exact-diagonal training targets against the explicit A, and
+the effect of a trained network (roots unchanged, fewer iterations)."""
+import numpy as np
+import pytest
+
+import molgen
+from tests.gpu_common import context
+
+pytestmark = pytest.mark.gpu
+xs = pytest.importorskip("paper_2505_24807_gb300.xs")
+
+SIZES = [10, 256, 256, 256, 2]
+
+
+def unflatten(w):
+    params, off = [], 0
+    for fin, fout in zip(SIZES[:-1], SIZES[1:]):
+        W = w[off:off + fout * fin].reshape(fout, fin).astype(np.float64)
+        off += fout * fin
+        b = w[off:off + fout].astype(np.float64)
+        off += fout
+        params.append((W, b))
+    return params
+
+
+def bf16(x):
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def test_forward_and_gradient_match_oracle():
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    F = rng.normal(size=(300, 10)).astype(np.float32)
+    T = np.stack([rng.normal(scale=3.0, size=300), rng.normal(size=300)], axis=1).astype(np.float32)
+    ctx = context()
+    try:
+        xs.xs_mlp_init(ctx.h, seed=7)
+        w = xs.xs_mlp_get_weights(ctx.h)
+        params = unflatten(bf16(w))      # the forward pass uses bfloat16-rounded weights
+        out = xs.xs_mlp_forward(ctx.h, F)
+        g, loss = xs.xs_mlp_grad(ctx.h, F, T)
+    finally:
+        ctx.close()
+    Y, cache = mlp.forward(params, F.astype(np.float64))
+    assert np.abs(out - Y).max() <= 1e-4 * np.abs(Y).max()
+    cw = np.array([0.01, 1.0])
+    assert abs(loss - mlp.loss(Y, T, cw)) <= 1e-4 * mlp.loss(Y, T, cw)
+    grads = mlp.backward(params, cache, Y, T.astype(np.float64), cw)
+    ref = np.concatenate([np.concatenate([gW.reshape(-1), gb]) for gW, gb in grads])
+    assert np.abs(g - ref).max() <= 1e-3 * np.abs(ref).max()
+
+
+def test_diagonal_shift_targets_match_explicit_matrix():
+    from oracle import excited, nddo, scf
+    params = molgen.make_params(0)
+    Z, xyz = molgen.config_small(5)
+    mol = nddo.Molecule(Z, xyz, params)
+    ints = nddo.Integrals(mol)
+    res = scf.scf(mol, ints)
+    A, _ = excited.explicit_AB(res.eps, res.C, mol.nocc, nddo.full_eri(mol, ints))
+    de = excited.delta_eps(res.eps, mol.nocc).reshape(-1)
+    ctx = context(params)
+    try:
+        xs.xs_ground_state(ctx.h, [(Z, xyz)])
+        xs.xs_excited(ctx.h, method=xs.XS_CIS, nroots=3, tol=1e-7)
+        F, pairs = xs.xs_mlp_features(ctx.h, 0, 200)
+        T = xs.xs_mlp_targets(ctx.h, 0, pairs)
+    finally:
+        ctx.close()
+    ref = np.diag(A)[pairs] - de[pairs]
+    assert np.abs(T[:, 0] - ref).max() < 1e-5
+    assert np.all(np.isfinite(F))
+
+
+def _solve_set(ctx, mols, guess):
+    xs.xs_ground_state(ctx.h, mols)
+    return xs.xs_excited(ctx.h, method=xs.XS_TDHF, nroots=4, tol=1e-6, guess=guess, n_mol=len(mols), batched=1)
+
+
+def test_learned_guess_keeps_roots_and_cuts_iterations():
+    params = molgen.make_params(0)
+    train = [molgen.config_sized(2000 + s, 20 + 3 * (s % 10)) for s in range(16)]
+    test = [molgen.config_sized(9000 + s, 24 + 5 * s) for s in range(4)]
+    ctx = context(params)
+    try:
+        feats, targs = [], []
+        xs.xs_ground_state(ctx.h, train)
+        xs.xs_excited(ctx.h, method=xs.XS_TDHF, nroots=4, tol=1e-6, n_mol=len(train))
+        for i in range(len(train)):
+            F, pairs = xs.xs_mlp_features(ctx.h, i, 1024)
+            feats.append(F)
+            targs.append(xs.xs_mlp_targets(ctx.h, i, pairs))
+        F = np.concatenate(feats)
+        T = np.concatenate(targs)
+        perm = np.random.default_rng(0).permutation(len(F))
+        xs.xs_mlp_init(ctx.h, seed=1)
+        loss = xs.xs_mlp_train(ctx.h, F[perm], T[perm], epochs=150, batch=2048, lr=2e-3)
+        assert loss[-1] < 0.5 * loss[0]
+        plain = _solve_set(ctx, test, xs.XS_GUESS_PLAIN)
+        learned = _solve_set(ctx, test, xs.XS_GUESS_LEARNED)
+    finally:
+        ctx.close()
+    assert learned["info"]["learned"] == 1
+    assert np.abs(learned["omega"] - plain["omega"]).max() < 1e-6
+    print("iterations plain", plain["iters"], "learned", learned["iters"], "loss", loss[0], loss[-1])
+    assert learned["iters"].mean() <= plain["iters"].mean()
