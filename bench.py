@@ -34,6 +34,11 @@ WORKLOADS = {
                   desc="TDHF, seeded chain of 400 C/N/O + 600 H atoms, 2200 AOs, 10 roots"),
     "medium": dict(gen=molgen.config_medium, method="TDHF", nroots=10, tol=1e-5,
                    desc="TDHF, seeded chain of 100 C/N/O + 200 H atoms, 600 AOs, 10 roots"),
+    "batch": dict(method="CIS", nroots=6, tol=1e-5, n_mol=256,
+                  desc="CIS, 256 seeded molecules of 20-200 atoms (40% heavy), 6 roots each, batched"),
+    "learned": dict(method="TDHF", nroots=8, tol=1e-5, n_train=256, n_test=64,
+                    desc="TDHF, 8 roots; MLP guess trained on 256 seeded molecules of 20-120 atoms, "
+                         "evaluated on 64 held-out molecules of 20-300 atoms, batched"),
 }
 METRIC = "TDHF roots/s @1e-5 eV"
 
@@ -161,6 +166,94 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def timed(torch, stream, fn):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1e3
+
+
+def run_many(args, wl):
+    """Batched workloads: one step = one batched solve of every molecule."""
+    import torch
+    from paper_2505_24807_gb300 import xs
+    torch.cuda.set_device(0)
+    params = molgen.make_params(0)
+    stream = torch.cuda.Stream(device=0)
+    ctx = xs.xs_create(0, stream.cuda_stream)
+    xs.xs_set_params(ctx, molgen.params_table(params))
+    method = xs.XS_TDHF if wl["method"] == "TDHF" else xs.XS_CIS
+    K = wl["nroots"]
+    extra = {}
+    t0 = time.perf_counter()
+    if args.workload == "batch":
+        mols = [molgen.config_batch(s) for s in range(wl["n_mol"])]
+        guess = xs.XS_GUESS_PLAIN
+    else:
+        train = [molgen.config_sized(1000 + s, 20 + (s * 7919) % 101) for s in range(wl["n_train"])]
+        mols = [molgen.config_sized(9000 + s, 20 + (s * 4099) % 281) for s in range(wl["n_test"])]
+        xs.xs_ground_state(ctx, train)
+        xs.xs_excited(ctx, method=method, nroots=K, tol=1e-6, batched=1, n_mol=len(train))
+        feats, targs = [], []
+        for i in range(len(train)):
+            F, pairs = xs.xs_mlp_features(ctx, i, 2048)
+            feats.append(F)
+            targs.append(xs.xs_mlp_targets(ctx, i, pairs))
+        F = np.concatenate(feats)
+        T = np.concatenate(targs)
+        perm = np.random.default_rng(0).permutation(len(F))
+        xs.xs_mlp_init(ctx, seed=1)
+        tt = time.perf_counter()
+        loss = xs.xs_mlp_train(ctx, F[perm], T[perm], epochs=60, batch=4096, lr=2e-3)
+        extra["training"] = dict(molecules=len(train), samples=int(len(F)), epochs=60,
+                                 loss_first=float(loss[0]), loss_last=float(loss[-1]),
+                                 seconds=round(time.perf_counter() - tt, 3))
+        guess = xs.XS_GUESS_LEARNED
+    gs = xs.xs_ground_state(ctx, mols)
+    setup_s = time.perf_counter() - t0
+    nm = len(mols)
+
+    def solve(g=guess, batched=1, prec=xs.XS_MIXED):
+        return xs.xs_excited(ctx, method=method, nroots=K, tol=wl["tol"], precision=prec, guess=g, batched=batched,
+                             n_mol=nm)
+
+    for _ in range(args.warmup):
+        solve()
+    clocks = ClockSampler(0)
+    clocks.start()
+    res, sec = None, 0.0
+    for _ in range(args.steps):
+        res, dt = timed(torch, stream, solve)
+        sec += dt
+    clk = clocks.stop()
+    value = nm * K * args.steps / sec
+    seq, seq_s = timed(torch, stream, lambda: solve(batched=0))
+    extra["one_at_a_time"] = dict(value=nm * K / seq_s, unit="roots/s", seconds=seq_s)
+    if args.workload == "learned":
+        plain, plain_s = timed(torch, stream, lambda: solve(g=xs.XS_GUESS_PLAIN))
+        extra["plain_guess"] = dict(value=nm * K / plain_s, unit="roots/s", seconds=plain_s,
+                                    mean_iterations=float(np.mean(plain["iters"])),
+                                    max_abs_domega_vs_learned_eV=float(np.abs(plain["omega"] - res["omega"]).max()))
+        extra["learned_guess"] = dict(mean_iterations=float(np.mean(res["iters"])), fallback=res["info"]["fallback"])
+    r64, s64 = timed(torch, stream, lambda: solve(g=xs.XS_GUESS_PLAIN, prec=xs.XS_FP64))
+    extra["fp64_gpu"] = dict(value=nm * K / s64, unit="roots/s", seconds=s64,
+                             max_abs_domega_vs_chosen_eV=float(np.abs(r64["omega"] - res["omega"]).max()),
+                             speedup_of_chosen_form=value / (nm * K / s64))
+    line = dict(metric=METRIC.replace("TDHF", wl["method"]), value=value, unit="roots/s", n_gpus=1,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * sec / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32+f64", data="synthetic",
+                config=dict(workload=args.workload, desc=wl["desc"], molecules=nm, precision="mixed",
+                            setup_seconds=round(setup_s, 2), scf_iterations_max=gs["max_scf_iter_used"]),
+                iterations_mean=float(np.mean(res["iters"])), converged=int(res["info"]["converged"]),
+                clocks=clk, **extra)
+    print(json.dumps(line), flush=True)
+    xs.xs_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,6 +268,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.workload in ("batch", "learned"):
+        return run_many(args, wl)
 
     import torch
     world, rank, local = dist_env()

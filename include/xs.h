@@ -173,7 +173,7 @@ int xs_get_amplitudes(const xs_ctx* ctx, int mol, int root, double* X, double* Y
  * xs_excited uses it when opts->guess == XS_GUESS_LEARNED and a network is
  * loaded; the plain Davidson still decides convergence and the shift is
  * dropped when a residual stalls, so converged roots do not change. */
-#define XS_MLP_FEATURES 10
+#define XS_MLP_FEATURES 11
 
 /* number of float32 parameters of the network (weights and biases, layer by
  * layer: W (out x in) row-major, then b) */

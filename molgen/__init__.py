@@ -189,10 +189,16 @@ def make_chain(seed: int, n_heavy: int, n_h: int, *,
         pos[1] = [rng.uniform(*bond), 0.0, 0.0]
     k = 2
     attempts = 0
+    stuck = 0
     while k < n_heavy:
         attempts += 1
-        if attempts > 500 * n_heavy:
+        if attempts > 2000 * n_heavy:
             raise RuntimeError("chain walk failed to place atoms")
+        if stuck > 200 and k > 3:
+            # dead end of the self-avoiding walk: step back and regrow
+            k -= 2
+            stuck = 0
+            continue
         b = pos[k - 1] - pos[k - 2]
         b = b / _norm(b)
         ref = np.array([0.0, 0.0, 1.0]) if abs(b[2]) < 0.9 else np.array([1.0, 0.0, 0.0])
@@ -209,9 +215,11 @@ def make_chain(seed: int, n_heavy: int, n_h: int, *,
         if k >= 3:
             d2 = _dist2_to(pos[: k - 2], p)   # atom k-2 is the 1-3 neighbour
             if np.min(d2) < heavy_clash * heavy_clash:
+                stuck += 1
                 continue
         pos[k] = p
         k += 1
+        stuck = 0
 
     degree = np.zeros(n_heavy, dtype=np.int64)
     if n_heavy > 1:

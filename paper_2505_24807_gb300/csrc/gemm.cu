@@ -5,10 +5,10 @@
 // J = W r, the Davidson subspace projections and Ritz vectors, and the SCF.
 // A BM x BN output tile per 256-thread CTA, K staged 16 at a time through
 // shared memory; thread (tx, ty) owns rows ty + (BM/TM) i and columns
-// tx + (BN/TN) j so that shared-memory reads are conflict free.  Three
-// shapes: 64x64 (4x4 per thread) for square problems, 32x128 (2x8) when M
-// is small (Ritz vectors and Gram-Schmidt updates: M = roots), 128x32 (8x2)
-// when N is small (split-K Gram products of the subspace).
+// tx + (BN/TN) j so that shared-memory reads are conflict free.  Eleven tile
+// shapes, from 64x64 for square problems to 8x512 (Ritz vectors and
+// Gram-Schmidt updates: M = roots) and 256x8 (split-K Gram products: N = new
+// vectors); the one that pads the problem least is launched.
 #include "kernels.h"
 #include "prof.h"
 
@@ -48,8 +48,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, T alpha,
 
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
-    for (int r = 0; r < (BM * BK) / 256; ++r) {
+    for (int r = 0; r < (BM * BK + 255) / 256; ++r) {
       const int idx = tid + 256 * r;
+      if (idx >= BM * BK) break;
       int m, k;
       if (!transA) { m = idx / BK; k = idx % BK; } else { k = idx / BM; m = idx % BM; }
       const int gm = m0 + m, gk = k0 + k;
@@ -58,8 +59,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, T alpha,
       As[k][m] = val;
     }
 #pragma unroll
-    for (int r = 0; r < (BN * BK) / 256; ++r) {
+    for (int r = 0; r < (BN * BK + 255) / 256; ++r) {
       const int idx = tid + 256 * r;
+      if (idx >= BN * BK) break;
       int n, k;
       if (!transB) { k = idx / BN; n = idx % BN; } else { n = idx / BK; k = idx % BK; }
       const int gn = n0 + n, gk = k0 + k;
@@ -113,37 +115,70 @@ __global__ void reduce_split(int M, int N, int kSplit, const T* __restrict__ P, 
   *c = r;
 }
 
-enum class Shape { Square, SmallM, SmallN };
+// Tile shapes (BM, BN, TM, TN), all 256 threads.  The float64 pipe of this
+// part is narrow enough that the Davidson GEMMs run pipe-bound, so every
+// padded row or column of a tile is lost time: the shape that pads M x N
+// least is taken (ties: earlier entries, which block more registers).
+struct TileShape {
+  int bm, bn;
+};
+constexpr TileShape kShapes[] = {{64, 64}, {32, 128}, {16, 256}, {8, 512}, {128, 32}, {256, 16},
+                                 {256, 8}, {64, 32},  {32, 32},  {64, 16}, {32, 16}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-Shape pick_shape(int M, int N) {
-  if (M <= 32 && N > 64) return Shape::SmallM;
-  if (N <= 32 && M > 64) return Shape::SmallN;
-  return Shape::Square;
+int pick_shape(int M, int N) {
+  int best = 0;
+  long long best_area = -1;
+  for (int s = 0; s < kNumShapes; ++s) {
+    const int bm = kShapes[s].bm, bn = kShapes[s].bn;
+    const long long area = (long long)((M + bm - 1) / bm) * bm * (long long)((N + bn - 1) / bn) * bn;
+    if (best_area < 0 || area < best_area) {
+      best = s;
+      best_area = area;
+    }
+  }
+  return best;
 }
 
-int tiles_of(Shape sh, int M, int N) {
-  if (sh == Shape::SmallM) return ((N + 127) / 128) * ((M + 31) / 32);
-  if (sh == Shape::SmallN) return ((N + 31) / 32) * ((M + 127) / 128);
-  return ((N + 63) / 64) * ((M + 63) / 64);
+int tiles_of(int sh, int M, int N) {
+  const int bm = kShapes[sh].bm, bn = kShapes[sh].bn;
+  return ((N + bn - 1) / bn) * ((M + bm - 1) / bm);
+}
+
+template <typename T, int BM, int BN, int TM, int TN>
+void launch_one(cudaStream_t s, int M, int N, int K, T alpha, const T* A, int lda, long long sA, bool tA, const T* B,
+                int ldb, long long sB, bool tB, T beta, T* C, int ldc, long long sC, int zdim, int kSplit,
+                long long sSplit) {
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, zdim);
+  gemm_kernel<T, BM, BN, TM, TN><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, tA, B, ldb, sB, tB, beta, C, ldc,
+                                                      sC, kSplit, sSplit);
 }
 
 template <typename T>
-void launch_gemm(cudaStream_t s, Shape sh, int M, int N, int K, T alpha, const T* A, int lda, long long sA, bool tA,
+void launch_gemm(cudaStream_t s, int sh, int M, int N, int K, T alpha, const T* A, int lda, long long sA, bool tA,
                  const T* B, int ldb, long long sB, bool tB, T beta, T* C, int ldc, long long sC, int zdim, int kSplit,
                  long long sSplit) {
-  if (sh == Shape::SmallM) {
-    dim3 grid((N + 127) / 128, (M + 31) / 32, zdim);
-    gemm_kernel<T, 32, 128, 2, 8><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, tA, B, ldb, sB, tB, beta, C, ldc,
-                                                       sC, kSplit, sSplit);
-  } else if (sh == Shape::SmallN) {
-    dim3 grid((N + 31) / 32, (M + 127) / 128, zdim);
-    gemm_kernel<T, 128, 32, 8, 2><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, tA, B, ldb, sB, tB, beta, C, ldc,
-                                                       sC, kSplit, sSplit);
-  } else {
-    dim3 grid((N + 63) / 64, (M + 63) / 64, zdim);
-    gemm_kernel<T, 64, 64, 4, 4><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, tA, B, ldb, sB, tB, beta, C, ldc,
-                                                      sC, kSplit, sSplit);
+#define XS_GEMM_CASE(I, BM_, BN_, TM_, TN_)                                                                       \
+  case I:                                                                                                         \
+    launch_one<T, BM_, BN_, TM_, TN_>(s, M, N, K, alpha, A, lda, sA, tA, B, ldb, sB, tB, beta, C, ldc, sC, zdim, \
+                                      kSplit, sSplit);                                                            \
+    break;
+  switch (sh) {
+    XS_GEMM_CASE(1, 32, 128, 2, 8)
+    XS_GEMM_CASE(2, 16, 256, 2, 8)
+    XS_GEMM_CASE(3, 8, 512, 1, 16)
+    XS_GEMM_CASE(4, 128, 32, 8, 2)
+    XS_GEMM_CASE(5, 256, 16, 8, 2)
+    XS_GEMM_CASE(6, 256, 8, 8, 1)
+    XS_GEMM_CASE(7, 64, 32, 4, 2)
+    XS_GEMM_CASE(8, 32, 32, 2, 2)
+    XS_GEMM_CASE(9, 64, 16, 4, 1)
+    XS_GEMM_CASE(10, 32, 16, 2, 1)
+    default:
+      launch_one<T, 64, 64, 4, 4>(s, M, N, K, alpha, A, lda, sA, tA, B, ldb, sB, tB, beta, C, ldc, sC, zdim, kSplit,
+                                  sSplit);
   }
+#undef XS_GEMM_CASE
 }
 
 }  // namespace
@@ -163,7 +198,7 @@ template <typename T>
 void gram(cudaStream_t s, int M, int N, int L, const T* A, int lda, const T* B, int ldb, T* C, int ldc, T alpha,
           T beta, DevBuf<T>& ws) {
   if (M <= 0 || N <= 0) return;
-  const Shape sh = pick_shape(M, N);
+  const int sh = pick_shape(M, N);
   const int tiles = tiles_of(sh, M, N);
   int kSplit = (2 * 152 + tiles - 1) / tiles;
   const int maxSplit = (L + 4 * BK - 1) / (4 * BK);

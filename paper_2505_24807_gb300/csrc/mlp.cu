@@ -1,9 +1,11 @@
 // Learned Davidson guess and diagonal preconditioner of libxs.
 //
-// Per orbital pair (i, a) among the lowest orbital-energy gaps, ten features
+// Per orbital pair (i, a) among the lowest orbital-energy gaps, eleven features
 // (gap, orbital energies, centroid distance, spreads, s characters, the
-// one-centre self-overlap of the transition charge, the density overlap) feed
-// an MLP (10 -> 256 -> 256 -> 256 -> 2, gelu, weights rounded to bfloat16,
+// one-centre self-overlap of the transition charge, the density overlap, and
+// the Coulomb energy of the two orbital densities in the monopole picture,
+// sum_AB q_A(i) (s_A s_A|s_B s_B) q_B(a)) feed
+// an MLP (11 -> 256 -> 256 -> 256 -> 2, gelu, weights rounded to bfloat16,
 // float32 accumulation) whose two outputs are
 //   0: the diagonal shift d_ia = A_ia,ia - (eps_a - eps_i) = 2(ia|ia) - (ii|aa)
 //      (used as the preconditioner r / (omega - d eps - d));
@@ -162,6 +164,36 @@ __global__ void features_kernel(int npairs, int n, int o, int v, int natoms, con
   f[7] = static_cast<float>(sa[4]);
   f[8] = static_cast<float>(tq2);
   f[9] = static_cast<float>(ov);
+}
+
+// atomic populations q[A][p] = sum_{mu on A} C_mu,p^2 (natoms x n)
+__global__ void populations_kernel(int n, int natoms, const double* __restrict__ CT,
+                                   const int* __restrict__ atom_ao_off, const int* __restrict__ atom_nao, double* q) {
+  const int p = blockIdx.y;
+  const int A = blockIdx.x * blockDim.x + threadIdx.x;
+  if (A >= natoms) return;
+  double s = 0.0;
+  for (int u = 0; u < atom_nao[A]; ++u) {
+    const double c = CT[(long long)p * n + atom_ao_off[A] + u];
+    s += c * c;
+  }
+  q[(long long)A * n + p] = s;
+}
+
+// monopole Coulomb matrix gamma_AB = (s_A s_A | s_B s_B), gamma_AA = gss_A
+__global__ void gamma_kernel(int natoms, int np, const double* __restrict__ W, const int* __restrict__ atom_prod_off,
+                             const int* __restrict__ atom_elem, const double* __restrict__ par, double* g) {
+  const int A = blockIdx.y, B = blockIdx.x * blockDim.x + threadIdx.x;
+  if (B >= natoms) return;
+  g[(long long)A * natoms + B] = (A == B) ? par[atom_elem[A] * XS_NPARAM + 4]
+                                          : W[(long long)atom_prod_off[A] * np + atom_prod_off[B]];
+}
+
+__global__ void gather_pairs_kernel(int npairs, int o, int v, const long long* __restrict__ pairs,
+                                    const double* __restrict__ Jov, float* F) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npairs) return;
+  F[(long long)k * kMlpFeatures + 10] = static_cast<float>(Jov[pairs[k]] / 10.0);
 }
 
 __device__ __forceinline__ int pidx_m(int a, int b) {
@@ -416,6 +448,18 @@ void pair_features(Ctx& c, const DevMol& m, const std::vector<long long>& pairs,
   features_kernel<<<grid1(npairs, 128), 128, 0, s>>>(npairs, m.n, m.o, m.v, m.L.natoms, dpairs.get(), m.CT.get(),
                                                      m.eps.get(), stats.get(), m.atom_ao_off.get(), m.atom_nao.get(),
                                                      F_dev);
+  XS_CHECK_LAUNCH();
+  // monopole Coulomb energy of the orbital densities: J = Q_occ^T Gamma Q_vir (o x v)
+  const int N = m.L.natoms;
+  DevBuf<double> q((size_t)N * m.n), gam((size_t)N * N), t((size_t)N * m.v), J((size_t)m.o * m.v);
+  populations_kernel<<<dim3((N + 127) / 128, m.n), 128, 0, s>>>(m.n, N, m.CT.get(), m.atom_ao_off.get(),
+                                                               m.atom_nao.get(), q.get());
+  gamma_kernel<<<dim3((N + 127) / 128, N), 128, 0, s>>>(N, m.np, m.W.get(), m.atom_prod_off.get(), m.atom_elem.get(),
+                                                        c.d_par.get(), gam.get());
+  XS_CHECK_LAUNCH();
+  gemm<double>(s, false, false, N, m.v, N, 1.0, gam.get(), N, 0, q.get() + m.o, m.n, 0, 0.0, t.get(), m.v, 0, 1);
+  gemm<double>(s, true, false, m.o, m.v, N, 1.0, q.get(), m.n, 0, t.get(), m.v, 0, 0.0, J.get(), m.v, 0, 1);
+  gather_pairs_kernel<<<grid1(npairs, 128), 128, 0, s>>>(npairs, m.o, m.v, dpairs.get(), J.get(), F_dev);
   XS_CHECK_LAUNCH();
   XS_CUDA(cudaStreamSynchronize(s));
 }

@@ -7,7 +7,7 @@
 
 namespace xs {
 
-constexpr int kMlpFeatures = 10;
+constexpr int kMlpFeatures = 11;
 constexpr int kMlpHidden = 256;
 constexpr int kMlpLayers = 4;
 constexpr int kMlpOutputs = 2;   // 0: diagonal shift (eV), 1: log10 pair weight

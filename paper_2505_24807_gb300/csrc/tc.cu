@@ -54,21 +54,23 @@ void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, do
   const int nb = product_batch(m);
   const int chunk = nvec < nb ? nvec : nb;
   // per vector: X pair, U^T pair, R, G+, G-, G pair, S^T pair
-  const size_t per = 2 * (size_t)o * vp + 2 * (size_t)n * op + 3 * (size_t)nn + 2 * (size_t)n * np_ +
-                     2 * (size_t)v * np_;
-  c.fs0.ensure((size_t)chunk * per);
+  // sub-buffers start on 256-byte boundaries (tensor maps need 16-byte aligned bases)
+  auto up = [](size_t x) { return (x + 63) / 64 * 64; };
+  const size_t sX = up((size_t)chunk * o * vp), sU = up((size_t)chunk * n * op), sR = up((size_t)chunk * nn);
+  const size_t sG = up((size_t)chunk * n * np_), sS = up((size_t)chunk * v * np_);
+  c.fs0.ensure(2 * sX + 2 * sU + 3 * sR + 2 * sG + 2 * sS);
   float* p = c.fs0.get();
-  float* Xh = p; p += (size_t)chunk * o * vp;
-  float* Xl = p; p += (size_t)chunk * o * vp;
-  float* Uh = p; p += (size_t)chunk * n * op;
-  float* Ul = p; p += (size_t)chunk * n * op;
-  float* R = p; p += (size_t)chunk * nn;
-  float* G = p; p += (size_t)chunk * nn;
-  float* Gm = p; p += (size_t)chunk * nn;
-  float* Gh = p; p += (size_t)chunk * n * np_;
-  float* Gl = p; p += (size_t)chunk * n * np_;
-  float* Sh = p; p += (size_t)chunk * v * np_;
-  float* Sl = p; p += (size_t)chunk * v * np_;
+  float* Xh = p; p += sX;
+  float* Xl = p; p += sX;
+  float* Uh = p; p += sU;
+  float* Ul = p; p += sU;
+  float* R = p; p += sR;
+  float* G = p; p += sR;
+  float* Gm = p; p += sR;
+  float* Gh = p; p += sG;
+  float* Gl = p; p += sG;
+  float* Sh = p; p += sS;
+  float* Sl = p; p += sS;
   DevBuf<int>& err = c.tc_err;
   if (!err.get()) {
     err.alloc(1);

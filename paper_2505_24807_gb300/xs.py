@@ -21,7 +21,7 @@ XS_FP64, XS_MIXED = 0, 1
 XS_KIND_A, XS_KIND_APB, XS_KIND_AMB, XS_KIND_G = 0, 1, 2, 3
 XS_GUESS_PLAIN, XS_GUESS_LEARNED = 0, 1
 XS_NPARAM, XS_NELEM = 13, 4
-XS_MLP_FEATURES = 10
+XS_MLP_FEATURES = 11
 
 STATUS_NAMES = {0: "XS_OK", -1: "XS_EINVAL", -2: "XS_ENOMEM", -3: "XS_ESCF", -4: "XS_EUNSTABLE",
                 -5: "XS_ENOCONV", -6: "XS_ECUDA", -7: "XS_ETIMEOUT", -8: "XS_ESTATE"}

@@ -10,7 +10,7 @@ from tests.gpu_common import context
 pytestmark = pytest.mark.gpu
 xs = pytest.importorskip("paper_2505_24807_gb300.xs")
 
-SIZES = [10, 256, 256, 256, 2]
+SIZES = [11, 256, 256, 256, 2]
 
 
 def unflatten(w):
@@ -33,7 +33,7 @@ def bf16(x):
 def test_forward_and_gradient_match_oracle():
     from oracle import mlp
     rng = np.random.default_rng(4)
-    F = rng.normal(size=(300, 10)).astype(np.float32)
+    F = rng.normal(size=(300, 11)).astype(np.float32)
     T = np.stack([rng.normal(scale=3.0, size=300), rng.normal(size=300)], axis=1).astype(np.float32)
     ctx = context()
     try:
