@@ -262,6 +262,8 @@ def main():
     ap.add_argument("--impl", default="xs", choices=["xs", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--guess", default="auto", choices=["auto", "plain", "learned"],
+                    help="learned: the network in paper_2505_24807_gb300/guess_weights.f32 (auto: if present)")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -291,9 +293,15 @@ def main():
     method = xs.XS_TDHF if wl["method"] == "TDHF" else xs.XS_CIS
     prec = xs.XS_MIXED if args.precision == "mixed" else xs.XS_FP64
     K = wl["nroots"]
+    wpath = os.path.join(ROOT, "paper_2505_24807_gb300", "guess_weights.f32")
+    guess = xs.XS_GUESS_PLAIN
+    if args.guess == "learned" or (args.guess == "auto" and os.path.exists(wpath)):
+        xs.xs_mlp_set_weights(ctx, np.fromfile(wpath, dtype=np.float32))
+        guess = xs.XS_GUESS_LEARNED
 
-    def solve(p=prec):
-        return xs.xs_excited(ctx, method=method, nroots=K, tol=wl["tol"], precision=p)
+    def solve(p=prec, g=None):
+        return xs.xs_excited(ctx, method=method, nroots=K, tol=wl["tol"], precision=p,
+                             guess=guess if g is None else g)
 
     for _ in range(args.warmup):
         solve()
@@ -346,7 +354,7 @@ def main():
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        r64 = solve(xs.XS_FP64)
+        r64 = solve(xs.XS_FP64, xs.XS_GUESS_PLAIN)
         f1.record(stream)
         torch.cuda.synchronize()
         s64 = f0.elapsed_time(f1) / 1e3
@@ -408,6 +416,7 @@ def main():
                     dtype="f32+f64" if prec == xs.XS_MIXED else "f64",
                     data="synthetic",
                     config=dict(workload=args.workload, desc=wl["desc"], precision=args.precision,
+                                guess="learned" if guess == xs.XS_GUESS_LEARNED else "plain",
                                 nao=nao, nocc=nocc, tol_eV=wl["tol"], l2="working set > L2 (V, (A+B)V, (A-B)V)",
                                 setup_seconds=round(setup_s, 3), scf_iterations=gs["max_scf_iter_used"]),
                     iterations=int(last["info"]["iterations"]), products=int(last["info"]["products"]),

@@ -41,7 +41,8 @@ struct Work {
   DevBuf<double> a1, a2;           // Smax x Smax, upper part valid
   DevBuf<double> E, Q, w, E2, Q2, w2, Sh, tS;   // S x S work
   DevBuf<double> cu, cw;           // S x kk coefficient blocks
-  DevBuf<double> X, AX, U, Wv, PU, MW, R1, R2, T;  // kk x ov (T: 2kk x ov)
+  DevBuf<double> X, U, Wv, PU, MW, R1, R2, T;  // X: 2kk x ov (Ritz vectors, then X-Y or A X); T: 2kk x ov
+  double* AX = nullptr;                          // = X + kk * ov
   DevBuf<double> C1, C2, C3;       // collapse scratch (2kk x ov)
   DevBuf<double> nrm, nrm2, omega, Bm;
   DevBuf<int> flag;
@@ -197,11 +198,15 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   if (rpa) w.S2.alloc((size_t)Smax * ov);
   w.a1.alloc((size_t)Smax * Smax);
   if (rpa) w.a2.alloc((size_t)Smax * Smax);
-  const size_t SS = (size_t)Smax * Smax;
-  w.E.alloc(SS); w.Q.alloc(SS); w.w.alloc(Smax); w.Sh.alloc(SS); w.tS.alloc(SS);
-  w.E2.alloc(SS); w.Q2.alloc(SS); w.w2.alloc(Smax);
+  // small matrices: S x S subspace work and up to 2k x 2k blocks (tiny molecules can have Smax < 2k)
+  const size_t SB = (size_t)std::max(Smax, 2 * kk + 2);
+  const size_t SS = SB * SB;
+  w.E.alloc(SS); w.Q.alloc(SS); w.w.alloc(SB); w.Sh.alloc(SS);
+  w.tS.alloc(SS);
+  w.E2.alloc(SS); w.Q2.alloc(SS); w.w2.alloc(SB);
   w.cu.alloc((size_t)Smax * 2 * kk); w.cw.alloc((size_t)Smax * kk);
-  w.X.alloc((size_t)kk * ov); w.AX.alloc((size_t)kk * ov); w.R1.alloc((size_t)kk * ov);
+  w.X.alloc((size_t)2 * kk * ov); w.R1.alloc((size_t)kk * ov);
+  w.AX = w.X.get() + (size_t)kk * ov;
   w.T.alloc((size_t)maxnew * ov);
   if (rpa) { w.R2.alloc((size_t)kk * ov); w.MW.alloc((size_t)kk * ov); }
   w.nrm.alloc(2 * kk + 2); w.nrm2.alloc(2 * kk + 2); w.omega.alloc(kk); w.Bm.alloc(4 * kk * kk + 4);
@@ -279,8 +284,8 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.V.get(), static_cast<int>(ov), 0,
                    0.0, w.X.get(), static_cast<int>(ov), 0, 1);
       gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.S1.get(), static_cast<int>(ov),
-                   0, 0.0, w.AX.get(), static_cast<int>(ov), 0, 1);
-      residual_norms(s, k, ov, w.AX.get(), w.X.get(), w.omega.get(), w.nrm.get(), w.R1.get());
+                   0, 0.0, w.AX, static_cast<int>(ov), 0, 1);
+      residual_norms(s, k, ov, w.AX, w.X.get(), w.omega.get(), w.nrm.get(), w.R1.get());
       sync_copy(s, hw.data(), w.omega.get(), sizeof(double) * k);
       sync_copy(s, hn.data(), w.nrm.get(), sizeof(double) * k);
     } else {
@@ -301,17 +306,27 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       scale_cols(s, S, k, w.cu.get(), k, w.omega.get(), 1);
       gemm<double>(s, false, false, S, k, S, 1.0, w.E2.get(), S, 0, w.cu.get(), k, 0, 0.0, w.cw.get(), k, 0, 1);
       scale_cols(s, S, k, w.cw.get(), k, w.omega.get(), 2);
-      // X+Y = V u~ (in X), X-Y = V w~ (in AX), (A+B)(X+Y) (R1 scratch -> PU), (A-B)(X-Y) (MW)
-      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cu.get(), k, 0, w.V.get(), static_cast<int>(ov),
-                   0, 0.0, w.X.get(), static_cast<int>(ov), 0, 1);
-      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cw.get(), k, 0, w.V.get(), static_cast<int>(ov),
-                   0, 0.0, w.AX.get(), static_cast<int>(ov), 0, 1);
+      // [X+Y; X-Y] = [u~ w~]^T V in one product (X+Y in X, X-Y in AX = X + kk ov),
+      // then (A+B)(X+Y) (R1 scratch) and (A-B)(X-Y) (MW)
+      if (k == kk) {
+        XS_CUDA(cudaMemcpy2DAsync(w.tS.get(), sizeof(double) * 2 * k, w.cu.get(), sizeof(double) * k,
+                                  sizeof(double) * k, S, cudaMemcpyDeviceToDevice, s));
+        XS_CUDA(cudaMemcpy2DAsync(w.tS.get() + k, sizeof(double) * 2 * k, w.cw.get(), sizeof(double) * k,
+                                  sizeof(double) * k, S, cudaMemcpyDeviceToDevice, s));
+        gemm<double>(s, true, false, 2 * k, static_cast<int>(ov), S, 1.0, w.tS.get(), 2 * k, 0, w.V.get(),
+                     static_cast<int>(ov), 0, 0.0, w.X.get(), static_cast<int>(ov), 0, 1);
+      } else {
+        gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cu.get(), k, 0, w.V.get(),
+                     static_cast<int>(ov), 0, 0.0, w.X.get(), static_cast<int>(ov), 0, 1);
+        gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cw.get(), k, 0, w.V.get(),
+                     static_cast<int>(ov), 0, 0.0, w.AX, static_cast<int>(ov), 0, 1);
+      }
       gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cu.get(), k, 0, w.S1.get(), static_cast<int>(ov),
                    0, 0.0, w.R1.get(), static_cast<int>(ov), 0, 1);
       gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cw.get(), k, 0, w.S2.get(), static_cast<int>(ov),
                    0, 0.0, w.MW.get(), static_cast<int>(ov), 0, 1);
       // r1 = (A+B)(X+Y) - omega (X-Y), r2 = (A-B)(X-Y) - omega (X+Y)
-      residual_norms(s, k, ov, w.R1.get(), w.AX.get(), w.omega.get(), w.nrm.get(), w.R1.get());
+      residual_norms(s, k, ov, w.R1.get(), w.AX, w.omega.get(), w.nrm.get(), w.R1.get());
       residual_norms(s, k, ov, w.MW.get(), w.X.get(), w.omega.get(), w.nrm.get() + kk, w.R2.get());
       int bad = 0;
       sync_copy(s, &bad, w.flag.get() + 3, sizeof(int));
@@ -336,7 +351,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
         const int nrows = rpa ? 2 * k : k;
         XS_CUDA(cudaMemcpyAsync(w.T.get(), w.X.get(), sizeof(double) * k * ov, cudaMemcpyDeviceToDevice, s));
         if (rpa)
-          XS_CUDA(cudaMemcpyAsync(w.T.get() + (size_t)k * ov, w.AX.get(), sizeof(double) * k * ov,
+          XS_CUDA(cudaMemcpyAsync(w.T.get() + (size_t)k * ov, w.AX, sizeof(double) * k * ov,
                                   cudaMemcpyDeviceToDevice, s));
         const int nb = orthonormalise_append(c, w, 0, nrows, ov, w.V.get());
         if (nb >= k) {
@@ -354,10 +369,10 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     if (it >= max_iter) break;
     // preconditioned residuals of the unconverged roots
     // fallback: drop the learned shift when the largest residual has not
-    // fallen by 10% over the last three iterations
+    // fallen by 10% over the last five iterations
     max_res_hist.push_back(*std::max_element(hn.begin(), hn.begin() + k));
-    if (shift && max_res_hist.size() > 3 &&
-        max_res_hist.back() > 0.9 * max_res_hist[max_res_hist.size() - 4]) {
+    if (shift && max_res_hist.size() > 5 &&
+        max_res_hist.back() > 0.9 * max_res_hist[max_res_hist.size() - 6]) {
       shift = nullptr;
       st.fallback = true;
     }
@@ -446,7 +461,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   m.U.alloc((size_t)kk * ov);
   m.Wv.alloc((size_t)kk * ov);
   XS_CUDA(cudaMemcpyAsync(m.U.get(), w.X.get(), sizeof(double) * kk * ov, cudaMemcpyDeviceToDevice, s));
-  XS_CUDA(cudaMemcpyAsync(m.Wv.get(), rpa ? w.AX.get() : w.X.get(), sizeof(double) * kk * ov,
+  XS_CUDA(cudaMemcpyAsync(m.Wv.get(), rpa ? w.AX : w.X.get(), sizeof(double) * kk * ov,
                           cudaMemcpyDeviceToDevice, s));
   DevBuf<double> fdev(kk);
   oscillator_strengths(c, m, kk, m.U.get(), w.omega.get(), fdev.get());

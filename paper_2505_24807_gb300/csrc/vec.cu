@@ -41,9 +41,11 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-// per row k: R = A - omega_k B (if R != nullptr), out = ||A - omega_k B||_2
+// per row k: R = A - omega_k B (if R != nullptr); per-block partial sums of
+// |A - omega_k B|^2 into part[k * gridDim.x + block] (summed in a fixed order
+// afterwards, so the norms do not depend on scheduling)
 __global__ void resid_kernel(long long len, const double* __restrict__ A, const double* __restrict__ B,
-                             const double* __restrict__ omega, double* __restrict__ out, double* __restrict__ R) {
+                             const double* __restrict__ omega, double* __restrict__ part, double* __restrict__ R) {
   int k = blockIdx.y;
   const double* a = A + (long long)k * len;
   const double* b = B ? B + (long long)k * len : nullptr;
@@ -61,8 +63,16 @@ __global__ void resid_kernel(long long len, const double* __restrict__ A, const 
   if (threadIdx.x < 32) {
     double t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
     t = warp_sum(t);
-    if (threadIdx.x == 0) atomicAdd(out + k, t);
+    if (threadIdx.x == 0) part[(long long)k * gridDim.x + blockIdx.x] = t;
   }
+}
+
+__global__ void sum_sqrt_kernel(int nvec, int nblocks, const double* __restrict__ part, double* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nvec) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += part[(long long)k * nblocks + b];
+  out[k] = sqrt(s);
 }
 
 __global__ void sqrt_kernel(int n, double* x) {
@@ -152,11 +162,12 @@ void precondition(cudaStream_t s, int nvec, int o, int v, const double* eps, con
 void residual_norms(cudaStream_t s, int nvec, long long len, const double* A, const double* B, const double* omega,
                     double* out_norm, double* R) {
   if (nvec == 0) return;
-  XS_CUDA(cudaMemsetAsync(out_norm, 0, sizeof(double) * nvec, s));
-  int blocks = static_cast<int>(std::min<long long>(256, (len + 255) / 256));
-  resid_kernel<<<dim3(blocks, nvec), 256, 0, s>>>(len, A, B, omega, out_norm, R);
+  const int blocks = static_cast<int>(std::min<long long>(256, (len + 255) / 256));
+  static thread_local DevBuf<double> part;
+  part.ensure((size_t)nvec * blocks);
+  resid_kernel<<<dim3(blocks, nvec), 256, 0, s>>>(len, A, B, omega, part.get(), R);
   XS_CHECK_LAUNCH();
-  sqrt_kernel<<<grid1(nvec, 64), 64, 0, s>>>(nvec, out_norm);
+  sum_sqrt_kernel<<<grid1(nvec, 64), 64, 0, s>>>(nvec, blocks, part.get(), out_norm);
   XS_CHECK_LAUNCH();
 }
 
