@@ -68,6 +68,9 @@ extern "C" {
 
 #define XS_GUESS_PLAIN 0    /* unit vectors on the lowest orbital-energy gaps */
 #define XS_GUESS_LEARNED 1  /* MLP-predicted guess and diagonal shift (plain fallback) */
+#define XS_SUBSPACE_AUTO 0
+#define XS_SUBSPACE_FP64 1
+#define XS_SUBSPACE_EMULATED 2
 
 /* Number of per-element parameter fields, in this order:
  * Uss, Upp, beta_s, beta_p, gss, gsp, gpp, gp2, hsp, D1, D2, zeta_s, zeta_p
@@ -93,6 +96,10 @@ typedef struct {
   int max_subspace;  /* subspace cap per molecule (0: library default) */
   int max_iter;      /* Davidson iteration cap (0: library default) */
   int batched;       /* 1: all molecules advance together, one launch per step */
+  int subspace;      /* float64 subspace products: XS_SUBSPACE_AUTO (0), XS_SUBSPACE_FP64 (1, the
+                        float64 pipe) or XS_SUBSPACE_EMULATED (2, exact digit splitting on the tensor
+                        cores, see xs_subspace_gram); AUTO = EMULATED for XS_MIXED solves of
+                        molecules with nocc * nvir >= 32768, else FP64 */
 } xs_ex_opts;
 
 typedef struct {
@@ -220,6 +227,27 @@ int xs_mlp_train(xs_ctx* ctx, int rows, const float* features, const float* targ
  * needs clearing -- each call writes every element it later reads.  The call
  * makes no cudaMalloc, cudaFree or allocating library call. */
 int xs_gbuild_noalloc(xs_ctx* ctx, int mol, int nvec, const double* R, double* G);
+
+/* ---- float64 subspace products (the Davidson step, Section "GPU
+ * Implementation": projected matrices V^T A V, Gram-Schmidt against V, Ritz
+ * vectors and residuals V x) ----------------------------------------------
+ * The solver uses these internally; they are exported so that the products
+ * can be checked and timed on their own.  emulated != 0 runs them on the
+ * BF16 tensor cores by exact digit splitting (Ozaki et al., Numer. Algorithms
+ * 59 (2012) 95): every float64 row is cut into eight base-128 digits scaled
+ * by a per-row power of two, digit products are summed exactly in float32
+ * chunks of 4096 and assembled in float64 -- float64 accuracy (an error of
+ * the order of a float64 GEMM's) at tensor-core speed.  emulated == 0 runs
+ * the float64-pipe GEMM.  Pointers may be host or device memory, row-major,
+ * owned by the caller; the call is synchronous.  Errors: XS_EINVAL for bad
+ * sizes, XS_ECUDA for a non-finite input (emulated) or a CUDA failure,
+ * XS_ETIMEOUT when a bounded device wait gave up. */
+/* C (M x N) = A B^T, A: M x L, B: N x L */
+int xs_subspace_gram(xs_ctx* ctx, int M, int N, long long L, const double* A, const double* B, double* C,
+                     int emulated);
+/* Y (nout x L) = sum_{b<nb} coef_b^T X_b, X: nb x S x L, coef: nb x S x nout, 1 <= nb <= 3 */
+int xs_subspace_combine(xs_ctx* ctx, int nb, int S, int nout, long long L, const double* X, const double* coef,
+                        double* Y, int emulated);
 
 /* Per-kernel timing.  xs_profile(ctx, 1) clears and enables it: every
  * instrumented kernel launch of later calls is bracketed by CUDA events on

@@ -7,6 +7,7 @@
 
 #include "davidson.h"
 #include "mlp.h"
+#include "ozaki.h"
 #include "kernels.h"
 #include "products.h"
 #include "scf.h"
@@ -284,6 +285,8 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
     if (o.nroots < 1) throw Error(XS_EINVAL, "nroots must be >= 1");
     if (!(o.tol > 0.0)) throw Error(XS_EINVAL, "tol must be positive");
     if (o.precision != XS_FP64 && o.precision != XS_MIXED) throw Error(XS_EINVAL, "bad precision");
+    if (o.subspace < XS_SUBSPACE_AUTO || o.subspace > XS_SUBSPACE_EMULATED)
+      throw Error(XS_EINVAL, "bad subspace option");
     if (c.mols.empty()) throw Error(XS_ESTATE, "xs_ground_state must come first");
     const int K = o.nroots;
     int status = XS_OK;
@@ -584,6 +587,87 @@ int xs_profile_read(xs_ctx* ctx, xs_prof_entry* out, int max_entries, int* count
     }
     ++k;
     if (count) *count = k;
+    return XS_OK;
+  });
+}
+
+int xs_subspace_gram(xs_ctx* ctx, int M, int N, long long L, const double* A, const double* B, double* C,
+                     int emulated) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (M < 0 || N < 0 || L < 1 || (M > 0 && N > 0 && (!A || !B || !C)))
+      throw Error(XS_EINVAL, "bad gram arguments");
+    if (M == 0 || N == 0) return XS_OK;
+    if (L > (1LL << 31) - 1024) throw Error(XS_EINVAL, "vectors too long");
+    cudaStream_t s = c.stream;
+    DevBuf<double> dA((size_t)M * L), dB((size_t)N * L), dC((size_t)M * N);
+    copy_any(s, dA.get(), A, sizeof(double) * M * L);
+    copy_any(s, dB.get(), B, sizeof(double) * N * L);
+    if (emulated) {
+      if (!c.tc_err.get()) {
+        c.tc_err.alloc(1);
+        XS_CUDA(cudaMemsetAsync(c.tc_err.get(), 0, sizeof(int), s));
+      }
+      const long long Lp = xs::oz_lp(L);
+      DevBuf<xs::oz_t> ta((size_t)M * xs::kOzDigits * Lp), tb((size_t)N * xs::kOzDigits * Lp);
+      DevBuf<int> eA(M), eB(N);
+      xs::OzWork w;
+      xs::oz_exponents(s, M, L, dA.get(), L, eA.get(), w, c.tc_err.get());
+      xs::oz_exponents(s, N, L, dB.get(), L, eB.get(), w, c.tc_err.get());
+      xs::oz_slice(s, M, L, dA.get(), L, eA.get(), ta.get(), Lp, 0, nullptr, 0, 0);
+      xs::oz_slice(s, N, L, dB.get(), L, eB.get(), tb.get(), Lp, 0, nullptr, 0, 0);
+      xs::oz_gram(s, M, N, L, ta.get(), Lp, eA.get(), tb.get(), Lp, eB.get(), 1.0, 0.0, dC.get(), N, w,
+                  c.tc_err.get());
+      xs::check_device_error(c);
+    } else {
+      xs::gram<double>(s, M, N, static_cast<int>(L), dA.get(), static_cast<int>(L), dB.get(), static_cast<int>(L),
+                       dC.get(), N, 1.0, 0.0, c.ws0);
+    }
+    copy_any(s, C, dC.get(), sizeof(double) * M * N);
+    XS_CUDA(cudaStreamSynchronize(s));
+    return XS_OK;
+  });
+}
+
+int xs_subspace_combine(xs_ctx* ctx, int nb, int S, int nout, long long L, const double* X, const double* coef,
+                        double* Y, int emulated) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (nb < 1 || nb > 3 || S < 1 || nout < 0 || L < 1 || (nout > 0 && (!X || !coef || !Y)))
+      throw Error(XS_EINVAL, "bad combine arguments");
+    if (nout == 0) return XS_OK;
+    if (L > (1LL << 31) - 1024) throw Error(XS_EINVAL, "vectors too long");
+    cudaStream_t s = c.stream;
+    DevBuf<double> dX((size_t)nb * S * L), dc((size_t)nb * S * nout), dY((size_t)nout * L);
+    copy_any(s, dX.get(), X, sizeof(double) * nb * S * L);
+    copy_any(s, dc.get(), coef, sizeof(double) * nb * S * nout);
+    if (emulated) {
+      if (!c.tc_err.get()) {
+        c.tc_err.alloc(1);
+        XS_CUDA(cudaMemsetAsync(c.tc_err.get(), 0, sizeof(int), s));
+      }
+      const int ldk = xs::oz_ldk(S);
+      DevBuf<xs::oz_t> nn((size_t)nb * L * ldk);
+      // digit columns past S * 8 are read (times zero coefficients): clear them
+      XS_CUDA(cudaMemsetAsync(nn.get(), 0, sizeof(xs::oz_t) * nb * L * ldk, s));
+      DevBuf<int> e((size_t)nb * S);
+      xs::OzWork w;
+      xs::OzBlock blk[3];
+      for (int b = 0; b < nb; ++b) {
+        const double* Xb = dX.get() + (size_t)b * S * L;
+        xs::oz_exponents(s, S, L, Xb, L, e.get() + b * S, w, c.tc_err.get());
+        xs::oz_slice(s, S, L, Xb, L, e.get() + b * S, nullptr, 0, 0, nn.get() + (size_t)b * L * ldk, ldk, 0);
+        blk[b] = xs::OzBlock{nn.get() + (size_t)b * L * ldk, ldk, e.get() + b * S, dc.get() + (size_t)b * S * nout,
+                             nout};
+      }
+      xs::oz_combine(s, nb, blk, S, nout, L, 1.0, 0.0, dY.get(), L, w, c.tc_err.get());
+      xs::check_device_error(c);
+    } else {
+      for (int b = 0; b < nb; ++b)
+        xs::gemm<double>(s, true, false, nout, static_cast<int>(L), S, 1.0, dc.get() + (size_t)b * S * nout, nout, 0,
+                         dX.get() + (size_t)b * S * L, static_cast<int>(L), 0, b == 0 ? 0.0 : 1.0, dY.get(),
+                         static_cast<int>(L), 0, 1);
+    }
+    copy_any(s, Y, dY.get(), sizeof(double) * nout * L);
+    XS_CUDA(cudaStreamSynchronize(s));
     return XS_OK;
   });
 }

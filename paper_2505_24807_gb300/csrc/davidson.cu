@@ -28,6 +28,7 @@
 #include "small.h"
 #include "syev.h"
 #include "mlp.h"
+#include "ozaki.h"
 
 namespace xs {
 
@@ -35,20 +36,96 @@ namespace {
 
 constexpr double kLowdinThresh = 1e-14;
 constexpr double kMixedResidualFloor = 1e-4;
+// mixed solves of at least this many amplitudes run the float64 subspace
+// products on the tensor cores (exact digit splitting)
+constexpr long long kOzMinLength = 32768;
 
 struct Work {
   DevBuf<double> V, S1, S2;        // Smax x ov
   DevBuf<double> a1, a2;           // Smax x Smax, upper part valid
   DevBuf<double> E, Q, w, E2, Q2, w2, Sh, tS;   // S x S work
   DevBuf<double> cu, cw;           // S x kk coefficient blocks
-  DevBuf<double> X, U, Wv, PU, MW, R1, R2, T;  // X: 2kk x ov (Ritz vectors, then X-Y or A X); T: 2kk x ov
+  DevBuf<double> X, U, Wv, PU, MW, R1, T;  // X: 2kk x ov (Ritz vectors, then X-Y or A X); R1: residual rows
   double* AX = nullptr;                          // = X + kk * ov
   DevBuf<double> C1, C2, C3;       // collapse scratch (2kk x ov)
   DevBuf<double> nrm, nrm2, omega, Bm;
   DevBuf<int> flag;
   DevBuf<long long> idx;
   DevBuf<double> gws, eig_ws;
+  // float64-accurate tensor-core subspace products (exact digit splitting):
+  // V as Gram operand (tn) and as combination operand (nn), A V / (A+B) V and
+  // (A-B) V as combination operands, one scratch tn operand (new vectors)
+  bool oz = false;
+  long long Lp = 0;
+  int ldk = 0, bcap = 0;
+  DevBuf<oz_t> Vtn, Vnn, S1nn, S2nn, Btn;
+  DevBuf<int> eV, eS1, eS2, eB;
+  DevBuf<double> coef;
+  OzWork ozw;
 };
+
+// digits of V rows [first, first + count) in both layouts
+void slice_V(Ctx& c, Work& w, long long ov, int first, int count) {
+  if (!w.oz || count <= 0) return;
+  const double* X = w.V.get() + (size_t)first * ov;
+  oz_exponents(c.stream, count, ov, X, ov, w.eV.get() + first, w.ozw, c.tc_err.get());
+  oz_slice(c.stream, count, ov, X, ov, w.eV.get() + first, w.Vtn.get(), w.Lp, first, w.Vnn.get(), w.ldk, first);
+}
+
+// digits of product rows [first, first + count) (S1 or S2): nn layout, and the
+// tn layout into the scratch operand Btn when with_tn
+void slice_P(Ctx& c, Work& w, long long ov, const double* P, DevBuf<int>& e, DevBuf<oz_t>& nn, int first, int count,
+             bool with_tn) {
+  if (!w.oz || count <= 0) return;
+  if (with_tn && count > w.bcap) throw Error(XS_EINVAL, "subspace scratch operand too small");
+  const double* X = P + (size_t)first * ov;
+  oz_exponents(c.stream, count, ov, X, ov, e.get() + first, w.ozw, c.tc_err.get());
+  oz_slice(c.stream, count, ov, X, ov, e.get() + first, with_tn ? w.Btn.get() : nullptr, w.Lp, 0, nn.get(), w.ldk,
+           first);
+}
+
+// digits of count scratch rows T into Btn (exponents eB)
+void slice_T(Ctx& c, Work& w, long long ov, const double* T, int count) {
+  if (count > w.bcap) throw Error(XS_EINVAL, "subspace scratch operand too small");
+  oz_exponents(c.stream, count, ov, T, ov, w.eB.get(), w.ozw, c.tc_err.get());
+  oz_slice(c.stream, count, ov, T, ov, w.eB.get(), w.Btn.get(), w.Lp, 0, nullptr, 0, 0);
+}
+
+// Coefficients of the CIS step, outputs [X (kk) | R (kk)] with X_j = V q_j and
+// R_j = A V q_j - omega_j V q_j; blocks (A V, V), S x 2kk each.
+__global__ void cis_coef_kernel(int S, int k, int kk, const double* __restrict__ Q, int ldq,
+                                const double* __restrict__ omega, double* __restrict__ out) {
+  const int w2 = 2 * kk;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * w2) return;
+  const int m = idx / w2, j = idx % w2;
+  const int r = j < kk ? j : j - kk;
+  const double q = r < k ? Q[(size_t)m * ldq + r] : 0.0;
+  out[idx] = j < kk ? 0.0 : q;
+  out[(size_t)S * w2 + idx] = j < kk ? q : (r < k ? -omega[r] * q : 0.0);
+}
+
+// Coefficients of the TDHF step: residual outputs [r1 (kk) | r2 (kk)] over the
+// blocks ((A+B) V, V, (A-B) V) with r1_j = (A+B) V cu_j - omega_j V cw_j and
+// r2_j = (A-B) V cw_j - omega_j V cu_j, then a fourth block for the Ritz
+// vectors [V cu (kk) | V cw (kk)] over V; S x 2kk each.
+__global__ void rpa_coef_kernel(int S, int k, int kk, const double* __restrict__ cu, const double* __restrict__ cw,
+                                const double* __restrict__ omega, double* __restrict__ out) {
+  const int w2 = 2 * kk;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * w2) return;
+  const int m = idx / w2, j = idx % w2;
+  const int r = j < kk ? j : j - kk;
+  const bool ok = r < k;
+  const double u = ok ? cu[(size_t)m * k + r] : 0.0;
+  const double wv = ok ? cw[(size_t)m * k + r] : 0.0;
+  const double om = ok ? omega[r] : 0.0;
+  const size_t blk = (size_t)S * w2;
+  out[idx] = j < kk ? u : 0.0;
+  out[blk + idx] = j < kk ? -om * wv : -om * u;
+  out[2 * blk + idx] = j < kk ? 0.0 : wv;
+  out[3 * blk + idx] = j < kk ? u : wv;
+}
 
 void sync_copy(cudaStream_t s, void* dst, const void* src, size_t bytes) {
   XS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
@@ -68,10 +145,18 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
   XS_CUDA(cudaMemcpyAsync(w.nrm2.get(), h.data(), sizeof(double) * nnew, cudaMemcpyHostToDevice, s));
   scale_rows(s, nnew, ov, w.T.get(), w.nrm2.get());
   for (int pass = 0; pass < 2 && S > 0; ++pass) {
-    gram<double>(s, S, nnew, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.T.get(), static_cast<int>(ov),
-                 w.tS.get(), nnew, 1.0, 0.0, w.gws);
-    gemm<double>(s, true, false, nnew, static_cast<int>(ov), S, -1.0, w.tS.get(), nnew, 0, w.V.get(),
-                 static_cast<int>(ov), 0, 1.0, w.T.get(), static_cast<int>(ov), 0, 1);
+    if (w.oz) {
+      slice_T(c, w, ov, w.T.get(), nnew);
+      oz_gram(s, S, nnew, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eB.get(), 1.0, 0.0, w.tS.get(),
+              nnew, w.ozw, c.tc_err.get());
+      const OzBlock b{w.Vnn.get(), w.ldk, w.eV.get(), w.tS.get(), nnew};
+      oz_combine(s, 1, &b, S, nnew, ov, -1.0, 1.0, w.T.get(), ov, w.ozw, c.tc_err.get());
+    } else {
+      gram<double>(s, S, nnew, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.T.get(),
+                   static_cast<int>(ov), w.tS.get(), nnew, 1.0, 0.0, w.gws);
+      gemm<double>(s, true, false, nnew, static_cast<int>(ov), S, -1.0, w.tS.get(), nnew, 0, w.V.get(),
+                   static_cast<int>(ov), 0, 1.0, w.T.get(), static_cast<int>(ov), 0, 1);
+    }
     if (pass == 0) {
       // a second pass only when the first removed a large part of some row
       // (norm below 0.7 of the unit input): "twice is enough" criterion
@@ -80,8 +165,14 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
       if (*std::min_element(h.begin(), h.end()) >= 0.7) break;
     }
   }
-  gram<double>(s, nnew, nnew, static_cast<int>(ov), w.T.get(), static_cast<int>(ov), w.T.get(), static_cast<int>(ov),
-               w.E2.get(), nnew, 1.0, 0.0, w.gws);
+  if (w.oz) {
+    slice_T(c, w, ov, w.T.get(), nnew);
+    oz_gram(s, nnew, nnew, ov, w.Btn.get(), w.Lp, w.eB.get(), w.Btn.get(), w.Lp, w.eB.get(), 1.0, 0.0, w.E2.get(),
+            nnew, w.ozw, c.tc_err.get());
+  } else {
+    gram<double>(s, nnew, nnew, static_cast<int>(ov), w.T.get(), static_cast<int>(ov), w.T.get(),
+                 static_cast<int>(ov), w.E2.get(), nnew, 1.0, 0.0, w.gws);
+  }
   syevk(s, nnew, nnew, w.E2.get(), nnew, w.w2.get(), w.Q2.get(), nnew, w.eig_ws, w.flag.get() + 1);
   lowdin(s, nnew, w.w2.get(), w.Q2.get(), nnew, kLowdinThresh, w.Bm.get(), nnew, w.flag.get() + 2);
   int nkeep = 0;
@@ -205,10 +296,38 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   w.tS.alloc(SS);
   w.E2.alloc(SS); w.Q2.alloc(SS); w.w2.alloc(SB);
   w.cu.alloc((size_t)Smax * 2 * kk); w.cw.alloc((size_t)Smax * kk);
-  w.X.alloc((size_t)2 * kk * ov); w.R1.alloc((size_t)kk * ov);
+  w.X.alloc((size_t)2 * kk * ov); w.R1.alloc((size_t)(rpa ? 2 : 1) * kk * ov);
   w.AX = w.X.get() + (size_t)kk * ov;
   w.T.alloc((size_t)maxnew * ov);
-  if (rpa) { w.R2.alloc((size_t)kk * ov); w.MW.alloc((size_t)kk * ov); }
+  if (rpa) w.MW.alloc((size_t)kk * ov);
+  // residual rows: R1 (CIS: A X - omega X; TDHF: r1), R2 (TDHF: r2)
+  double* R1p = w.R1.get();
+  double* R2p = rpa ? w.R1.get() + (size_t)kk * ov : nullptr;
+  w.oz = opt.subspace == XS_SUBSPACE_EMULATED ||
+         (opt.subspace == XS_SUBSPACE_AUTO && opt.precision == XS_MIXED && ov >= kOzMinLength);
+  if (w.oz) {
+    if (!c.tc_err.get()) {
+      c.tc_err.alloc(1);
+      XS_CUDA(cudaMemsetAsync(c.tc_err.get(), 0, sizeof(int), s));
+    }
+    w.Lp = oz_lp(ov);
+    w.ldk = oz_ldk(Smax);
+    w.bcap = std::max(maxnew, std::max(nguess, 2 * kk));
+    w.Vtn.alloc((size_t)Smax * kOzDigits * w.Lp);
+    w.Btn.alloc((size_t)w.bcap * kOzDigits * w.Lp);
+    // combination operands: digit columns past S * 8 are read (times zero
+    // coefficients) and must hold finite values
+    w.Vnn.alloc((size_t)ov * w.ldk);
+    w.S1nn.alloc((size_t)ov * w.ldk);
+    XS_CUDA(cudaMemsetAsync(w.Vnn.get(), 0, sizeof(oz_t) * ov * w.ldk, s));
+    XS_CUDA(cudaMemsetAsync(w.S1nn.get(), 0, sizeof(oz_t) * ov * w.ldk, s));
+    if (rpa) {
+      w.S2nn.alloc((size_t)ov * w.ldk);
+      XS_CUDA(cudaMemsetAsync(w.S2nn.get(), 0, sizeof(oz_t) * ov * w.ldk, s));
+    }
+    w.eV.alloc(Smax); w.eS1.alloc(Smax); w.eS2.alloc(Smax); w.eB.alloc(w.bcap);
+    w.coef.alloc((size_t)4 * Smax * 2 * kk);
+  }
   w.nrm.alloc(2 * kk + 2); w.nrm2.alloc(2 * kk + 2); w.omega.alloc(kk); w.Bm.alloc(4 * kk * kk + 4);
   w.flag.alloc(4);
   XS_CUDA(cudaMemsetAsync(w.flag.get(), 0, 4 * sizeof(int), s));
@@ -260,6 +379,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   make_guess(c, m, w, nguess, ov, learned_pairs.empty() ? nullptr : &learned_pairs);
   std::vector<double> max_res_hist;
   int S = nguess, Sold = 0;
+  slice_V(c, w, ov, 0, S);
   apply(0, S);
 
   std::vector<double> hw(kk), hn(2 * kk), hn2(kk);
@@ -269,11 +389,22 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   int status = XS_OK;
   for (it = 1; it <= max_iter + 1; ++it) {
     // projected matrices: new columns Sold..S-1 over all rows 0..S-1
-    gram<double>(s, S, S - Sold, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S1.get() + Sold * ov,
-                 static_cast<int>(ov), w.a1.get() + Sold, Smax, 1.0, 0.0, w.gws);
-    if (rpa)
-      gram<double>(s, S, S - Sold, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S2.get() + Sold * ov,
-                   static_cast<int>(ov), w.a2.get() + Sold, Smax, 1.0, 0.0, w.gws);
+    if (w.oz) {
+      slice_P(c, w, ov, w.S1.get(), w.eS1, w.S1nn, Sold, S - Sold, true);
+      oz_gram(s, S, S - Sold, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS1.get() + Sold, 1.0, 0.0,
+              w.a1.get() + Sold, Smax, w.ozw, c.tc_err.get());
+      if (rpa) {
+        slice_P(c, w, ov, w.S2.get(), w.eS2, w.S2nn, Sold, S - Sold, true);
+        oz_gram(s, S, S - Sold, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS2.get() + Sold, 1.0, 0.0,
+                w.a2.get() + Sold, Smax, w.ozw, c.tc_err.get());
+      }
+    } else {
+      gram<double>(s, S, S - Sold, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S1.get() + Sold * ov,
+                   static_cast<int>(ov), w.a1.get() + Sold, Smax, 1.0, 0.0, w.gws);
+      if (rpa)
+        gram<double>(s, S, S - Sold, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S2.get() + Sold * ov,
+                     static_cast<int>(ov), w.a2.get() + Sold, Smax, 1.0, 0.0, w.gws);
+    }
     const int k = std::min(kk, S);
     if (!rpa) {
       sym_upper(s, S, w.a1.get(), Smax, w.E.get(), S);
@@ -281,11 +412,23 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       syevk(s, S, kq, w.E.get(), S, w.w.get(), w.Q.get(), kq, w.eig_ws, w.flag.get());
       XS_CUDA(cudaMemcpyAsync(w.omega.get(), w.w.get(), sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
       // Ritz vectors and residuals
-      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.V.get(), static_cast<int>(ov), 0,
-                   0.0, w.X.get(), static_cast<int>(ov), 0, 1);
-      gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.S1.get(), static_cast<int>(ov),
-                   0, 0.0, w.AX, static_cast<int>(ov), 0, 1);
-      residual_norms(s, k, ov, w.AX, w.X.get(), w.omega.get(), w.nrm.get(), w.R1.get());
+      if (w.oz) {
+        // X (rows 0..kk-1 of w.X) and R = A X - omega X (rows kk.., i.e. w.AX) in one pass
+        cis_coef_kernel<<<grid1((long long)S * 2 * kk, 256), 256, 0, s>>>(S, k, kk, w.Q.get(), kq, w.omega.get(),
+                                                                          w.coef.get());
+        XS_CHECK_LAUNCH();
+        const OzBlock blk[2] = {{w.S1nn.get(), w.ldk, w.eS1.get(), w.coef.get(), 2 * kk},
+                                {w.Vnn.get(), w.ldk, w.eV.get(), w.coef.get() + (size_t)S * 2 * kk, 2 * kk}};
+        oz_combine(s, 2, blk, S, 2 * kk, ov, 1.0, 0.0, w.X.get(), ov, w.ozw, c.tc_err.get());
+        R1p = w.AX;
+        row_norms(s, k, ov, R1p, w.nrm.get());
+      } else {
+        gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.V.get(),
+                     static_cast<int>(ov), 0, 0.0, w.X.get(), static_cast<int>(ov), 0, 1);
+        gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.S1.get(),
+                     static_cast<int>(ov), 0, 0.0, w.AX, static_cast<int>(ov), 0, 1);
+        residual_norms(s, k, ov, w.AX, w.X.get(), w.omega.get(), w.nrm.get(), R1p);
+      }
       sync_copy(s, hw.data(), w.omega.get(), sizeof(double) * k);
       sync_copy(s, hn.data(), w.nrm.get(), sizeof(double) * k);
     } else {
@@ -306,6 +449,22 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       scale_cols(s, S, k, w.cu.get(), k, w.omega.get(), 1);
       gemm<double>(s, false, false, S, k, S, 1.0, w.E2.get(), S, 0, w.cu.get(), k, 0, 0.0, w.cw.get(), k, 0, 1);
       scale_cols(s, S, k, w.cw.get(), k, w.omega.get(), 2);
+      if (w.oz) {
+        // residuals r1, r2 over ((A+B) V, V, (A-B) V) in one pass, then
+        // [X+Y; X-Y] = [u~ w~]^T V (X+Y in X, X-Y in AX = X + kk ov)
+        rpa_coef_kernel<<<grid1((long long)S * 2 * kk, 256), 256, 0, s>>>(S, k, kk, w.cu.get(), w.cw.get(),
+                                                                          w.omega.get(), w.coef.get());
+        XS_CHECK_LAUNCH();
+        const size_t cb = (size_t)S * 2 * kk;
+        const OzBlock blk[3] = {{w.S1nn.get(), w.ldk, w.eS1.get(), w.coef.get(), 2 * kk},
+                                {w.Vnn.get(), w.ldk, w.eV.get(), w.coef.get() + cb, 2 * kk},
+                                {w.S2nn.get(), w.ldk, w.eS2.get(), w.coef.get() + 2 * cb, 2 * kk}};
+        oz_combine(s, 3, blk, S, 2 * kk, ov, 1.0, 0.0, R1p, ov, w.ozw, c.tc_err.get());
+        const OzBlock rz{w.Vnn.get(), w.ldk, w.eV.get(), w.coef.get() + 3 * cb, 2 * kk};
+        oz_combine(s, 1, &rz, S, 2 * kk, ov, 1.0, 0.0, w.X.get(), ov, w.ozw, c.tc_err.get());
+        row_norms(s, k, ov, R1p, w.nrm.get());
+        row_norms(s, k, ov, R2p, w.nrm.get() + kk);
+      } else {
       // [X+Y; X-Y] = [u~ w~]^T V in one product (X+Y in X, X-Y in AX = X + kk ov),
       // then (A+B)(X+Y) (R1 scratch) and (A-B)(X-Y) (MW)
       if (k == kk) {
@@ -322,12 +481,13 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
                      static_cast<int>(ov), 0, 0.0, w.AX, static_cast<int>(ov), 0, 1);
       }
       gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cu.get(), k, 0, w.S1.get(), static_cast<int>(ov),
-                   0, 0.0, w.R1.get(), static_cast<int>(ov), 0, 1);
+                   0, 0.0, R1p, static_cast<int>(ov), 0, 1);
       gemm<double>(s, true, false, k, static_cast<int>(ov), S, 1.0, w.cw.get(), k, 0, w.S2.get(), static_cast<int>(ov),
                    0, 0.0, w.MW.get(), static_cast<int>(ov), 0, 1);
       // r1 = (A+B)(X+Y) - omega (X-Y), r2 = (A-B)(X-Y) - omega (X+Y)
-      residual_norms(s, k, ov, w.R1.get(), w.AX, w.omega.get(), w.nrm.get(), w.R1.get());
-      residual_norms(s, k, ov, w.MW.get(), w.X.get(), w.omega.get(), w.nrm.get() + kk, w.R2.get());
+      residual_norms(s, k, ov, R1p, w.AX, w.omega.get(), w.nrm.get(), R1p);
+      residual_norms(s, k, ov, w.MW.get(), w.X.get(), w.omega.get(), w.nrm.get() + kk, R2p);
+      }
       int bad = 0;
       sync_copy(s, &bad, w.flag.get() + 3, sizeof(int));
       if (bad) { status = XS_EUNSTABLE; break; }
@@ -355,6 +515,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
                                   cudaMemcpyDeviceToDevice, s));
         const int nb = orthonormalise_append(c, w, 0, nrows, ov, w.V.get());
         if (nb >= k) {
+          slice_V(c, w, ov, 0, nb);
           prod_prec = kPrecF32;
           apply(0, nb);
           S = nb;
@@ -376,19 +537,16 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       shift = nullptr;
       st.fallback = true;
     }
-    if (!rpa) precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R1.get(), w.R1.get(), shift);
-    else {
-      precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R1.get(), w.R1.get(), shift);
-      precondition(s, k, o, v, m.eps.get(), w.omega.get(), w.R2.get(), w.R2.get(), shift);
-    }
+    precondition(s, k, o, v, m.eps.get(), w.omega.get(), R1p, R1p, shift);
+    if (rpa) precondition(s, k, o, v, m.eps.get(), w.omega.get(), R2p, R2p, shift);
     int nnew = 0;
     for (int j = 0; j < k; ++j) {
       if (conv[j]) continue;
-      XS_CUDA(cudaMemcpyAsync(w.T.get() + nnew * ov, w.R1.get() + j * ov, sizeof(double) * ov,
+      XS_CUDA(cudaMemcpyAsync(w.T.get() + nnew * ov, R1p + j * ov, sizeof(double) * ov,
                               cudaMemcpyDeviceToDevice, s));
       ++nnew;
       if (rpa) {
-        XS_CUDA(cudaMemcpyAsync(w.T.get() + nnew * ov, w.R2.get() + j * ov, sizeof(double) * ov,
+        XS_CUDA(cudaMemcpyAsync(w.T.get() + nnew * ov, R2p + j * ov, sizeof(double) * ov,
                                 cudaMemcpyDeviceToDevice, s));
         ++nnew;
       }
@@ -400,13 +558,22 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
         nc = kq;
         w.C1.ensure((size_t)nc * ov);
         w.C2.ensure((size_t)nc * ov);
-        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.V.get(), static_cast<int>(ov),
-                     0, 0.0, w.C1.get(), static_cast<int>(ov), 0, 1);
-        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.S1.get(),
-                     static_cast<int>(ov), 0, 0.0, w.C2.get(), static_cast<int>(ov), 0, 1);
+        if (w.oz) {
+          const OzBlock bv{w.Vnn.get(), w.ldk, w.eV.get(), w.Q.get(), kq};
+          const OzBlock bs{w.S1nn.get(), w.ldk, w.eS1.get(), w.Q.get(), kq};
+          oz_combine(s, 1, &bv, S, nc, ov, 1.0, 0.0, w.C1.get(), ov, w.ozw, c.tc_err.get());
+          oz_combine(s, 1, &bs, S, nc, ov, 1.0, 0.0, w.C2.get(), ov, w.ozw, c.tc_err.get());
+        } else {
+          gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.V.get(),
+                       static_cast<int>(ov), 0, 0.0, w.C1.get(), static_cast<int>(ov), 0, 1);
+          gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.Q.get(), kq, 0, w.S1.get(),
+                       static_cast<int>(ov), 0, 0.0, w.C2.get(), static_cast<int>(ov), 0, 1);
+        }
         XS_CUDA(cudaMemcpyAsync(w.V.get(), w.C1.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
         XS_CUDA(cudaMemcpyAsync(w.S1.get(), w.C2.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
         set_diag(s, nc, w.w.get(), w.a1.get(), Smax);
+        slice_V(c, w, ov, 0, nc);
+        slice_P(c, w, ov, w.S1.get(), w.eS1, w.S1nn, 0, nc, false);
       } else {
         // orthonormal basis of span{u~, w~} in subspace coordinates
         XS_CUDA(cudaMemcpy2DAsync(w.tS.get(), sizeof(double) * 2 * k, w.cu.get(), sizeof(double) * k,
@@ -425,19 +592,38 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
         w.C1.ensure((size_t)nc * ov);
         w.C2.ensure((size_t)nc * ov);
         w.C3.ensure((size_t)nc * ov);
-        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.E.get(), nc, 0, w.V.get(), static_cast<int>(ov),
-                     0, 0.0, w.C1.get(), static_cast<int>(ov), 0, 1);
-        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.E.get(), nc, 0, w.S1.get(),
-                     static_cast<int>(ov), 0, 0.0, w.C2.get(), static_cast<int>(ov), 0, 1);
-        gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.E.get(), nc, 0, w.S2.get(),
-                     static_cast<int>(ov), 0, 0.0, w.C3.get(), static_cast<int>(ov), 0, 1);
+        if (w.oz) {
+          const OzBlock b1{w.Vnn.get(), w.ldk, w.eV.get(), w.E.get(), nc};
+          const OzBlock b2{w.S1nn.get(), w.ldk, w.eS1.get(), w.E.get(), nc};
+          const OzBlock b3{w.S2nn.get(), w.ldk, w.eS2.get(), w.E.get(), nc};
+          oz_combine(s, 1, &b1, S, nc, ov, 1.0, 0.0, w.C1.get(), ov, w.ozw, c.tc_err.get());
+          oz_combine(s, 1, &b2, S, nc, ov, 1.0, 0.0, w.C2.get(), ov, w.ozw, c.tc_err.get());
+          oz_combine(s, 1, &b3, S, nc, ov, 1.0, 0.0, w.C3.get(), ov, w.ozw, c.tc_err.get());
+        } else {
+          gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.E.get(), nc, 0, w.V.get(),
+                       static_cast<int>(ov), 0, 0.0, w.C1.get(), static_cast<int>(ov), 0, 1);
+          gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.E.get(), nc, 0, w.S1.get(),
+                       static_cast<int>(ov), 0, 0.0, w.C2.get(), static_cast<int>(ov), 0, 1);
+          gemm<double>(s, true, false, nc, static_cast<int>(ov), S, 1.0, w.E.get(), nc, 0, w.S2.get(),
+                       static_cast<int>(ov), 0, 0.0, w.C3.get(), static_cast<int>(ov), 0, 1);
+        }
         XS_CUDA(cudaMemcpyAsync(w.V.get(), w.C1.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
         XS_CUDA(cudaMemcpyAsync(w.S1.get(), w.C2.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
         XS_CUDA(cudaMemcpyAsync(w.S2.get(), w.C3.get(), sizeof(double) * nc * ov, cudaMemcpyDeviceToDevice, s));
-        gram<double>(s, nc, nc, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S1.get(),
-                     static_cast<int>(ov), w.a1.get(), Smax, 1.0, 0.0, w.gws);
-        gram<double>(s, nc, nc, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S2.get(),
-                     static_cast<int>(ov), w.a2.get(), Smax, 1.0, 0.0, w.gws);
+        if (w.oz) {
+          slice_V(c, w, ov, 0, nc);
+          slice_P(c, w, ov, w.S1.get(), w.eS1, w.S1nn, 0, nc, true);
+          oz_gram(s, nc, nc, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS1.get(), 1.0, 0.0,
+                  w.a1.get(), Smax, w.ozw, c.tc_err.get());
+          slice_P(c, w, ov, w.S2.get(), w.eS2, w.S2nn, 0, nc, true);
+          oz_gram(s, nc, nc, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS2.get(), 1.0, 0.0,
+                  w.a2.get(), Smax, w.ozw, c.tc_err.get());
+        } else {
+          gram<double>(s, nc, nc, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S1.get(),
+                       static_cast<int>(ov), w.a1.get(), Smax, 1.0, 0.0, w.gws);
+          gram<double>(s, nc, nc, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S2.get(),
+                       static_cast<int>(ov), w.a2.get(), Smax, 1.0, 0.0, w.gws);
+        }
       }
       S = nc;
       st.collapses += 1;
@@ -446,9 +632,11 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     if (nnew <= 0) break;  // the subspace already spans everything it can hold
     int nkeep = orthonormalise_append(c, w, S, nnew, ov, w.V.get() + (size_t)S * ov);
     if (nkeep == 0) break;  // no new direction: stagnation
+    slice_V(c, w, ov, S, nkeep);
     Sold = S;
     S += nkeep;
     apply(Sold, nkeep);
+    if (w.oz) check_device_error(c);
     XS_CUDA(cudaStreamSynchronize(s));
   }
   st.iterations = std::min(it, max_iter);

@@ -51,6 +51,10 @@ void axpy(cudaStream_t s, long long n, double alpha, const double* x, double* y)
 void scal(cudaStream_t s, long long n, double alpha, double* x);
 void max_abs(cudaStream_t s, long long n, const double* a, double* out);   // out: one device double
 void transpose(cudaStream_t s, int rows, int cols, const double* a, double* b);
+// Synchronise the context's stream and raise XS_ETIMEOUT (clearing the word)
+// when a tensor-core kernel's bounded wait gave up or a digit split met a
+// non-finite value (the error word c.tc_err).
+void check_device_error(Ctx& c);
 
 // ---- small dense eigenproblems (small.cu) -----------------------------------
 // Symmetric eigen-decomposition of batch matrices (n <= 512) by cyclic Jacobi

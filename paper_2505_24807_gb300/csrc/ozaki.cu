@@ -1,0 +1,502 @@
+// Float64-accurate Davidson subspace products on the BF16 tensor cores
+// (tcgen05 + TMA, sm_103a) by exact digit splitting (Ozaki, Ogita, Oishi and
+// Rump, Numer. Algorithms 59, 95-118 (2012)); the representation is described
+// in ozaki.h.
+//
+// One kernel, two shapes, both with K-major digit operands:
+//   gram  (mode 0)  C[m][n] = sum_l A[m][l] B[n][l]: rows of the MMA are the
+//                   digit planes (m, i) of A, columns the planes (n, j) of B,
+//                   K = l in exact chunks of 4096; the epilogue folds the 64
+//                   digit pairs with weights 2^(-7(i+j)) into a float64
+//                   partial per (chunk, m, n), summed in fixed order after.
+//   combine (mode 1) Y[k][l] = sum_m c[m][k] X[m][l]: rows are l, K = the
+//                   digit planes (block, m, i) of the stored vectors, columns
+//                   (k, t) hold the coefficient digits on the anti-diagonals
+//                   t = i + j of the digit pairs, so one float32 accumulator per
+//                   (l, k, t) sums exact integers; the epilogue weights t by
+//                   2^(-7t) (pairs with i + j > 9 fall below float64 rounding).
+// Warp 0 issues TMA loads through a STAGES-deep mbarrier ring, warp 1 owns
+// TMEM and issues the MMAs (M = 128, N = BN, K = 16 per instruction), warps
+// 2-5 drain the accumulators.  Every wait is bounded; a timeout raises the
+// error word and the CTA leaves after draining what it issued.
+#include <algorithm>
+
+#include "kernels.h"
+#include "ozaki.h"
+#include "prof.h"
+#include "tcgen05.cuh"
+
+namespace xs {
+
+namespace {
+
+using namespace tc5;
+
+constexpr int BM = 128;
+constexpr int BKE = 64;                     // bf16 per K block: one 128-byte swizzle row
+constexpr int KB_CHUNK = kOzChunk / BKE;    // K blocks per exact float32 chunk
+
+// Balanced base-128 digits of x 2^-e (|x| < 2^(e-1)): x 2^-e = sum_i d[i] 2^(-7(i+1))
+// up to a rounding of 2^-57; |d[i]| <= 64.  Integer arithmetic on the IEEE
+// fields: the magnitude is rounded to a 56-bit fixed-point integer q, then
+// peeled into digits from the least significant end.
+__device__ __forceinline__ void oz_digits(double x, int e, int* d) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int exf = static_cast<int>((bits >> 52) & 0x7FF);
+#pragma unroll
+  for (int i = 0; i < kOzDigits; ++i) d[i] = 0;
+  if (exf == 0 || exf == 0x7FF) return;   // zero / subnormal (below 2^-1022) / non-finite (flagged elsewhere)
+  const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  int sh = exf - 1019 - e;                 // q = mant 2^sh
+  unsigned long long q;
+  if (sh >= 0) {
+    q = mant << (sh > 2 ? 2 : sh);
+  } else {
+    const int rs = -sh;
+    q = rs >= 64 ? 0ull : (((mant >> (rs - 1)) + 1ull) >> 1);
+  }
+  long long r = (bits >> 63) ? -static_cast<long long>(q) : static_cast<long long>(q);
+#pragma unroll
+  for (int i = kOzDigits - 1; i >= 1; --i) {
+    const long long di = ((r + 64) & 127) - 64;
+    d[i] = static_cast<int>(di);
+    r = (r - di) >> 7;
+  }
+  d[0] = static_cast<int>(r);
+}
+
+__device__ __forceinline__ uint32_t digit_bits(int d) {
+  return __float_as_uint(static_cast<float>(d)) >> 16;   // exact: |d| <= 64
+}
+
+__device__ __forceinline__ uint4 pack8(const int* d) {
+  uint4 u;
+  u.x = digit_bits(d[0]) | (digit_bits(d[1]) << 16);
+  u.y = digit_bits(d[2]) | (digit_bits(d[3]) << 16);
+  u.z = digit_bits(d[4]) | (digit_bits(d[5]) << 16);
+  u.w = digit_bits(d[6]) | (digit_bits(d[7]) << 16);
+  return u;
+}
+
+struct OzArgs {
+  int mode;          // 0: gram partials, 1: combination
+  int kb_total;      // K blocks of the whole product (mode 0)
+  int kb_per_cta;    // mode 0: K blocks per chunk; mode 1: K blocks of this launch
+  int kb_begin;      // mode 1: first K block of this launch (concatenated over blocks)
+  int kb_per_blk;    // mode 1: K blocks per stored block
+  int ncols;         // mode 0: B vectors; mode 1: outputs
+  int Mvec;          // mode 0: A vectors
+  double* part;      // mode 0: [chunk][Mvec][ncols]
+  double* Y;         // mode 1
+  long long ldy;
+  long long L;
+  double alpha, beta;
+  const int* fexp;
+};
+
+template <int BN>
+struct OzCfg {
+  static constexpr int A_BYTES = BM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (200 * 1024) / STAGE > 8 ? 8 : (200 * 1024) / STAGE;
+  static constexpr int TCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  static constexpr size_t SMEM = 1024 + static_cast<size_t>(STAGES) * STAGE + (2 * STAGES + 1) * 8 + 16;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    oz_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+              const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB, OzArgs a,
+              int* err) {
+  using C = OzCfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accfull = empty + C::STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int m0 = blockIdx.x * BM;
+  int kb0, nk;
+  if (a.mode == 0) {
+    kb0 = blockIdx.y * a.kb_per_cta;
+    nk = min(a.kb_per_cta, a.kb_total - kb0);
+  } else {
+    kb0 = a.kb_begin;
+    nk = a.kb_per_cta;
+  }
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accfull, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, C::TCOLS);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % C::STAGES;
+      if (it >= C::STAGES && !mbar_wait(&empty[s], ((it / C::STAGES) + 1) & 1, err, 1)) break;
+      uint8_t* st = base + s * C::STAGE;
+      mbar_expect_tx(&full[s], C::STAGE);
+      const int kb = kb0 + it;
+      if (a.mode == 0) {
+        tma_load_2d(st, &tmA0, &full[s], kb * BKE, m0);
+      } else {
+        const int b = kb / a.kb_per_blk;
+        const CUtensorMap* ta = b == 0 ? &tmA0 : (b == 1 ? &tmA1 : &tmA2);
+        tma_load_2d(st, ta, &full[s], (kb - b * a.kb_per_blk) * BKE, m0);
+      }
+      tma_load_2d(st + C::A_BYTES, &tmB, &full[s], kb * BKE, 0);
+      ++issued;
+    }
+    for (int it = (issued > C::STAGES ? issued - C::STAGES : 0); it < issued; ++it)
+      mbar_wait(&empty[it % C::STAGES], (it / C::STAGES) & 1, err, 0) || true;
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_f32acc(1, BM, BN);
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % C::STAGES;
+      if (!mbar_wait(&full[s], (it / C::STAGES) & 1, err, 2)) break;
+      fence_after_sync();
+      uint8_t* st = base + s * C::STAGE;
+      const uint32_t aa = smem_u32(st), bb = smem_u32(st + C::A_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BKE / 16; ++kk) {
+        const uint32_t off = kk * 32;   // 16 bf16 per MMA step
+        mma_bf16(tmem, sdesc(aa + off), sdesc(bb + off), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accfull);
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    const uint32_t trow = tmem + (static_cast<uint32_t>(32 * q) << 16);
+    const bool ok = mbar_wait(accfull, 0, err, 3);
+    fence_after_sync();
+    if (ok && !*reinterpret_cast<volatile int*>(err)) {
+      if (a.mode == 0) {
+        const int i = r & 7;
+        const double wi = ldexp(1.0, -7 * (i + 1));
+        const int mv = (m0 + r) >> 3;
+        double* out = a.part + (static_cast<size_t>(blockIdx.y) * a.Mvec + mv) * a.ncols;
+        for (int n = 0; n < a.ncols; ++n) {
+          float v[8];
+          tmem_ld8(trow + n * 8, v);
+          double sum = 0.0, wj = 0.0078125;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            sum = fma(static_cast<double>(v[j]), wj, sum);
+            wj *= 0.0078125;
+          }
+          sum *= wi;
+          sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+          sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+          sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+          if ((lane & 7) == 0 && mv < a.Mvec) out[n] = sum;
+        }
+      } else {
+        const long long l = static_cast<long long>(m0) + r;
+        for (int k = 0; k < a.ncols; ++k) {
+          float v[8];
+          tmem_ld8(trow + k * 8, v);
+          double sum = 0.0, wt = 0.0078125 * 0.0078125;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            sum = fma(static_cast<double>(v[t]), wt, sum);
+            wt *= 0.0078125;
+          }
+          if (l < a.L) {
+            double y = a.alpha * ldexp(sum, a.fexp[k]);
+            double* p = a.Y + static_cast<size_t>(k) * a.ldy + l;
+            if (a.beta != 0.0) y = fma(a.beta, *p, y);
+            *p = y;
+          }
+        }
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after_sync();
+    tmem_dealloc(tmem, C::TCOLS);
+  }
+}
+
+__global__ void oz_absmax_kernel(long long L, const double* __restrict__ X, long long ldx,
+                                 unsigned long long* __restrict__ mx) {
+  const int r = blockIdx.y;
+  const double* x = X + static_cast<size_t>(r) * ldx;
+  unsigned long long m = 0;
+  for (long long l = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; l < L;
+       l += static_cast<long long>(gridDim.x) * blockDim.x)
+    m = max(m, static_cast<unsigned long long>(__double_as_longlong(fabs(x[l]))));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&mx[r], m);
+}
+
+__global__ void oz_exp_kernel(int nvec, const unsigned long long* __restrict__ mx, int* __restrict__ e, int* err) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nvec) return;
+  const unsigned long long b = mx[r];
+  const int ex = static_cast<int>((b >> 52) & 0x7FF);
+  if (ex == 0x7FF) atomicCAS(err, 0, 10);
+  e[r] = (b == 0) ? 0 : ex - 1021;
+}
+
+__global__ void oz_slice_kernel(int nvec, long long L, const double* __restrict__ X, long long ldx,
+                                const int* __restrict__ e, oz_t* __restrict__ tn, long long Lp, int tn_r0,
+                                oz_t* __restrict__ nn, int ldk, int nn_r0) {
+  const long long l = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (l >= (tn ? Lp : L)) return;
+  for (int r = 0; r < nvec; ++r) {
+    int d[kOzDigits];
+    if (l < L) {
+      oz_digits(X[static_cast<size_t>(r) * ldx + l], e[r], d);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kOzDigits; ++i) d[i] = 0;
+    }
+    if (tn) {
+#pragma unroll
+      for (int i = 0; i < kOzDigits; ++i)
+        tn[(static_cast<size_t>(tn_r0 + r) * kOzDigits + i) * Lp + l] = static_cast<oz_t>(digit_bits(d[i]));
+    }
+    if (nn && l < L)
+      *reinterpret_cast<uint4*>(nn + static_cast<size_t>(l) * ldk + static_cast<size_t>(nn_r0 + r) * kOzDigits) =
+          pack8(d);
+  }
+}
+
+// C[m][n] = alpha 2^(eA[m] + eB[n]) sum_chunk part[chunk][m][n] + beta C[m][n]
+__global__ void oz_reduce_kernel(int M, int N, int nchunk, const double* __restrict__ part, const int* __restrict__ eA,
+                                 const int* __restrict__ eB, double alpha, double beta, double* C, int ldc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  const int m = idx / N, n = idx % N;
+  double sum = 0.0;
+  for (int c = 0; c < nchunk; ++c) sum += part[(static_cast<size_t>(c) * M + m) * N + n];
+  double y = alpha * ldexp(sum, eA[m] + eB[n]);
+  double* p = C + static_cast<size_t>(m) * ldc + n;
+  if (beta != 0.0) y = fma(beta, *p, y);
+  *p = y;
+}
+
+struct CoefArgs {
+  const double* coef[3];
+  int ldc[3];
+  const int* e[3];
+};
+
+// Digit matrix of the combination coefficients, one CTA per output k:
+// column (k, t) of the product (row k * 8 + t here, K-major over the
+// concatenated blocks) holds at K index (b, m, i) the digit t - i of
+// c'[b][m] = coef_b[m][k] 2^(e_b[m]), split with the common exponent f[k].
+__global__ void oz_coef_kernel(int nb, int S, int Kp, int k0, CoefArgs ca, oz_t* __restrict__ bmat,
+                               int* __restrict__ fexp, int* err) {
+  const int k = blockIdx.x;
+  const int rowK = nb * Kp;
+  const int per = Kp / kOzDigits;
+  __shared__ unsigned long long smax;
+  if (threadIdx.x == 0) smax = 0;
+  __syncthreads();
+  unsigned long long mx = 0;
+  for (int idx = threadIdx.x; idx < nb * S; idx += blockDim.x) {
+    const int b = idx / S, m = idx % S;
+    const double c = ldexp(ca.coef[b][static_cast<size_t>(m) * ca.ldc[b] + k0 + k], ca.e[b][m]);
+    mx = max(mx, static_cast<unsigned long long>(__double_as_longlong(fabs(c))));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&smax, mx);
+  __syncthreads();
+  const unsigned long long M = smax;
+  const int ex = static_cast<int>((M >> 52) & 0x7FF);
+  if (threadIdx.x == 0 && ex == 0x7FF) atomicCAS(err, 0, 11);
+  const int f = (M == 0) ? 0 : ex - 1021;
+  if (threadIdx.x == 0) fexp[k] = f;
+  for (int idx = threadIdx.x; idx < nb * per; idx += blockDim.x) {
+    const int b = idx / per, m = idx % per;
+    int d[kOzDigits];
+    if (m < S) {
+      oz_digits(ldexp(ca.coef[b][static_cast<size_t>(m) * ca.ldc[b] + k0 + k], ca.e[b][m]), f, d);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kOzDigits; ++i) d[i] = 0;
+    }
+#pragma unroll
+    for (int t = 0; t < kOzDigits; ++t) {
+      int g[kOzDigits];
+#pragma unroll
+      for (int i = 0; i < kOzDigits; ++i) g[i] = (i <= t) ? d[t - i] : 0;
+      *reinterpret_cast<uint4*>(bmat + static_cast<size_t>(k * kOzDigits + t) * rowK + static_cast<size_t>(b) * Kp +
+                                static_cast<size_t>(m) * kOzDigits) = pack8(g);
+    }
+  }
+}
+
+// inner x rows bf16 matrix, row stride ld elements, boxes of 64 x box_rows
+CUtensorMap make_map_bf16(const oz_t* ptr, long long inner, long long rows, long long ld, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(BKE), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ld % 8) || inner <= 0 || rows <= 0)
+    throw Error(XS_EINVAL, "digit operand not 16-byte aligned or empty");
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<oz_t*>(ptr), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(XS_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+  return m;
+}
+
+template <int BN>
+void launch_oz(cudaStream_t s, dim3 grid, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
+               const CUtensorMap& b, const OzArgs& args, int* err) {
+  using C = OzCfg<BN>;
+  static bool attr = false;
+  if (!attr) {
+    XS_CUDA(cudaFuncSetAttribute(oz_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(C::SMEM)));
+    attr = true;
+  }
+  oz_kernel<BN><<<grid, 192, C::SMEM, s>>>(a0, a1, a2, b, args, err);
+  XS_CHECK_LAUNCH();
+}
+
+int pick_bn(int cols) { return cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 192 ? 192 : 256; }
+
+void dispatch(cudaStream_t s, int bn, dim3 grid, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
+              const CUtensorMap& b, const OzArgs& args, int* err) {
+  switch (bn) {
+    case 64: launch_oz<64>(s, grid, a0, a1, a2, b, args, err); break;
+    case 128: launch_oz<128>(s, grid, a0, a1, a2, b, args, err); break;
+    case 192: launch_oz<192>(s, grid, a0, a1, a2, b, args, err); break;
+    default: launch_oz<256>(s, grid, a0, a1, a2, b, args, err); break;
+  }
+}
+
+constexpr int kMaxCols = 256 / kOzDigits;   // vectors (gram) or outputs (combine) per launch
+
+}  // namespace
+
+void oz_exponents(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, int* e, OzWork& w,
+                  int* err) {
+  if (nvec <= 0) return;
+  w.mx.ensure(nvec);
+  XS_CUDA(cudaMemsetAsync(w.mx.get(), 0, sizeof(unsigned long long) * nvec, s));
+  if (L > 0) {
+    dim3 grid(static_cast<unsigned>(std::min<long long>(256, (L + 255) / 256)), nvec);
+    oz_absmax_kernel<<<grid, 256, 0, s>>>(L, X, ldx, w.mx.get());
+    XS_CHECK_LAUNCH();
+  }
+  oz_exp_kernel<<<(nvec + 127) / 128, 128, 0, s>>>(nvec, w.mx.get(), e, err);
+  XS_CHECK_LAUNCH();
+}
+
+void oz_slice(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, const int* e, oz_t* tn,
+              long long Lp, int tn_r0, oz_t* nn, int ldk, int nn_r0) {
+  if (nvec <= 0 || (!tn && !nn)) return;
+  if (tn && (Lp < L || Lp % 8)) throw Error(XS_EINVAL, "oz_slice: bad plane stride");
+  if (nn && ldk % 64) throw Error(XS_EINVAL, "oz_slice: bad nn stride");
+  const long long span = tn ? Lp : L;
+  ProfScope ps(s, "oz_slice", 8.0 * nvec * L + (tn ? 16.0 * nvec * Lp : 0.0) + (nn ? 16.0 * nvec * L : 0.0), 0.0);
+  oz_slice_kernel<<<grid1(span, 256), 256, 0, s>>>(nvec, L, X, ldx, e, tn, Lp, tn_r0, nn, ldk, nn_r0);
+  XS_CHECK_LAUNCH();
+}
+
+void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long long Alp, const int* eA,
+             const oz_t* Btn, long long Blp, const int* eB, double alpha, double beta, double* C, int ldc,
+             OzWork& w, int* err) {
+  if (M <= 0 || N <= 0) return;
+  if (L <= 0) throw Error(XS_EINVAL, "oz_gram: empty vectors");
+  const int kb_total = static_cast<int>((L + BKE - 1) / BKE);
+  const int nchunk = (kb_total + KB_CHUNK - 1) / KB_CHUNK;
+  const CUtensorMap ta = make_map_bf16(Atn, L, static_cast<long long>(M) * kOzDigits, Alp, BM);
+  for (int n0 = 0; n0 < N; n0 += kMaxCols) {
+    const int nn = std::min(kMaxCols, N - n0);
+    const int bn = pick_bn(nn * kOzDigits);
+    const CUtensorMap tb =
+        make_map_bf16(Btn + static_cast<size_t>(n0) * kOzDigits * Blp, L, static_cast<long long>(nn) * kOzDigits, Blp,
+                      bn);
+    w.part.ensure(static_cast<size_t>(nchunk) * M * nn);
+    OzArgs a{};
+    a.mode = 0;
+    a.kb_total = kb_total;
+    a.kb_per_cta = KB_CHUNK;
+    a.ncols = nn;
+    a.Mvec = M;
+    a.part = w.part.get();
+    dim3 grid((M * kOzDigits + BM - 1) / BM, nchunk);
+    {
+      ProfScope ps(s, "oz_gram", 2.0 * kOzDigits * static_cast<double>(L) * (M + nn), 2.0 * M * nn * (double)L);
+      dispatch(s, bn, grid, ta, ta, ta, tb, a, err);
+    }
+    oz_reduce_kernel<<<grid1(static_cast<long long>(M) * nn, 256), 256, 0, s>>>(M, nn, nchunk, w.part.get(), eA,
+                                                                               eB + n0, alpha, beta, C + n0, ldc);
+    XS_CHECK_LAUNCH();
+  }
+}
+
+void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, long long L, double alpha, double beta,
+                double* Y, long long ldy, OzWork& w, int* err) {
+  if (nout <= 0 || L <= 0) return;
+  if (nb < 1 || nb > 3) throw Error(XS_EINVAL, "oz_combine: 1 to 3 blocks");
+  if (S <= 0) throw Error(XS_EINVAL, "oz_combine: empty subspace");
+  const int Kp = oz_ldk(S);
+  const int kb_per_blk = Kp / BKE;
+  const int kb_total = nb * kb_per_blk;
+  CUtensorMap ta[3];
+  CoefArgs ca{};
+  for (int b = 0; b < nb; ++b) {
+    if (blk[b].ldk < Kp || blk[b].ldk % 64) throw Error(XS_EINVAL, "oz_combine: nn stride too small");
+    ta[b] = make_map_bf16(blk[b].nn, Kp, L, blk[b].ldk, BM);
+    ca.coef[b] = blk[b].coef;
+    ca.ldc[b] = blk[b].ldc;
+    ca.e[b] = blk[b].e;
+  }
+  for (int b = nb; b < 3; ++b) ta[b] = ta[0];
+  for (int k0 = 0; k0 < nout; k0 += kMaxCols) {
+    const int nk = std::min(kMaxCols, nout - k0);
+    const int bn = pick_bn(nk * kOzDigits);
+    w.bmat.ensure(static_cast<size_t>(nk) * kOzDigits * nb * Kp);
+    w.fexp.ensure(kMaxCols);
+    oz_coef_kernel<<<nk, 256, 0, s>>>(nb, S, Kp, k0, ca, w.bmat.get(), w.fexp.get(), err);
+    XS_CHECK_LAUNCH();
+    const CUtensorMap tb = make_map_bf16(w.bmat.get(), static_cast<long long>(nb) * Kp,
+                                         static_cast<long long>(nk) * kOzDigits, static_cast<long long>(nb) * Kp, bn);
+    for (int kb = 0; kb < kb_total; kb += KB_CHUNK) {
+      OzArgs a{};
+      a.mode = 1;
+      a.kb_begin = kb;
+      a.kb_per_cta = std::min(KB_CHUNK, kb_total - kb);
+      a.kb_per_blk = kb_per_blk;
+      a.ncols = nk;
+      a.Y = Y + static_cast<size_t>(k0) * ldy;
+      a.ldy = ldy;
+      a.L = L;
+      a.alpha = alpha;
+      a.beta = kb == 0 ? beta : 1.0;
+      a.fexp = w.fexp.get();
+      dim3 grid(static_cast<unsigned>((L + BM - 1) / BM), 1);
+      ProfScope ps(s, "oz_combine",
+                   2.0 * kOzDigits * static_cast<double>(L) * a.kb_per_cta * BKE / kOzDigits +
+                       8.0 * nk * (double)L * (a.beta != 0.0 ? 2 : 1),
+                   2.0 * nk * (double)L * a.kb_per_cta * BKE / kOzDigits);
+      dispatch(s, bn, grid, ta[0], ta[1], ta[2], tb, a, err);
+    }
+  }
+}
+
+}  // namespace xs

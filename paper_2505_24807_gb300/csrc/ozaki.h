@@ -1,0 +1,76 @@
+// Float64-accurate tall-skinny products of the Davidson subspace on the BF16
+// tensor cores (ozaki.cu).
+//
+// Every float64 vector x (one row of V, (A+B)V, (A-B)V, ...) is stored as
+// eight balanced base-128 digit planes: with a per-row exponent e,
+//   x[l] = 2^e * sum_{i=1..8} d_i[l] 2^(-7 i) + O(2^(e-57)),  |d_i| <= 64,
+// the error-free splitting of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms
+// 59, 95-118 (2012)).  The digits are small integers, exact in bfloat16; a
+// product of two digits is at most 2^12 in magnitude, so up to 4096 of them
+// sum exactly in the tensor cores' float32 accumulators.  Products of digit
+// planes are therefore exact, and the float64 result is assembled from them
+// with the digit weights -- the same accuracy as a float64 GEMM, at tensor-core
+// rather than float64-pipe speed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace xs {
+
+using oz_t = uint16_t;           // bfloat16 bit pattern of one digit
+constexpr int kOzDigits = 8;     // digit planes per float64 row
+constexpr int kOzChunk = 4096;   // digit products summed exactly per float32 accumulator
+
+struct OzWork {
+  DevBuf<double> part;              // split partial sums of oz_gram
+  DevBuf<oz_t> bmat;                // digit matrix of the oz_combine coefficients
+  DevBuf<int> fexp;                 // their per-output exponents
+  DevBuf<unsigned long long> mx;    // per-row max |x| bit patterns
+};
+
+// e[r] such that max_l |X[r][l]| < 2^(e[r]-1), rows r < nvec (row stride ldx).
+// A non-finite entry raises the error word (code 10).
+void oz_exponents(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, int* e, OzWork& w,
+                  int* err);
+
+// Digit planes of rows r < nvec of X (exponents e[r]), written as
+//   tn: planes [(tn_r0 + r) * 8 + i][l] (row stride Lp >= L, a multiple of 8;
+//       columns L..Lp-1 are set to 0), i = 0 the most significant digit;
+//   nn: [l][(nn_r0 + r) * 8 + i] (row stride ldk, a multiple of 64).
+// Either output may be null.
+void oz_slice(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, const int* e, oz_t* tn,
+              long long Lp, int tn_r0, oz_t* nn, int ldk, int nn_r0);
+
+// C (M x N, row stride ldc) = alpha * A B^T + beta * C, where A holds M rows and
+// B holds N rows of length L as tn digit planes (row strides Alp, Blp) with
+// exponents eA, eB.  Split over L into float32-exact chunks of 4096.
+void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long long Alp, const int* eA,
+             const oz_t* Btn, long long Blp, const int* eB, double alpha, double beta, double* C, int ldc,
+             OzWork& w, int* err);
+
+// One block of a combination: the first S rows of a stored set (nn digit
+// layout with row stride ldk, exponents e) and its coefficients coef[m][k]
+// (row stride ldc).
+struct OzBlock {
+  const oz_t* nn;
+  int ldk;
+  const int* e;
+  const double* coef;
+  int ldc;
+};
+
+// Y[k][l] (row stride ldy) = alpha * sum_b sum_{m<S} coef_b[m][k] X_b[m][l] + beta * Y[k][l]
+// for k < nout, l < L, over nb <= 3 blocks.
+void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, long long L, double alpha, double beta,
+                double* Y, long long ldy, OzWork& w, int* err);
+
+// Row stride of the nn layout for up to S rows.
+inline int oz_ldk(int S) { return ((S * kOzDigits + 63) / 64) * 64; }
+// Row stride of the tn layout for vectors of length L.
+inline long long oz_lp(long long L) { return ((L + 63) / 64) * 64; }
+
+}  // namespace xs

@@ -230,4 +230,17 @@ void transpose(cudaStream_t s, int rows, int cols, const double* a, double* b) {
   XS_CHECK_LAUNCH();
 }
 
+void check_device_error(Ctx& c) {
+  if (!c.tc_err.get()) return;
+  int h = 0;
+  XS_CUDA(cudaMemcpyAsync(&h, c.tc_err.get(), sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  XS_CUDA(cudaStreamSynchronize(c.stream));
+  if (h) {
+    XS_CUDA(cudaMemsetAsync(c.tc_err.get(), 0, sizeof(int), c.stream));
+    throw Error(h >= 10 ? XS_ECUDA : XS_ETIMEOUT,
+                h >= 10 ? "non-finite value in a float64 digit split (code " + std::to_string(h) + ")"
+                        : "tensor-core kernel: a bounded device wait timed out (code " + std::to_string(h) + ")");
+  }
+}
+
 }  // namespace xs

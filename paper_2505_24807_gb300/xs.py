@@ -20,6 +20,7 @@ XS_CIS, XS_TDHF = 0, 1
 XS_FP64, XS_MIXED = 0, 1
 XS_KIND_A, XS_KIND_APB, XS_KIND_AMB, XS_KIND_G = 0, 1, 2, 3
 XS_GUESS_PLAIN, XS_GUESS_LEARNED = 0, 1
+XS_SUBSPACE_AUTO, XS_SUBSPACE_FP64, XS_SUBSPACE_EMULATED = 0, 1, 2
 XS_NPARAM, XS_NELEM = 13, 4
 XS_MLP_FEATURES = 11
 
@@ -39,7 +40,8 @@ class xs_gs_info(C.Structure):
 
 class xs_ex_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("nroots", C.c_int), ("tol", C.c_double), ("precision", C.c_int),
-                ("guess", C.c_int), ("max_subspace", C.c_int), ("max_iter", C.c_int), ("batched", C.c_int)]
+                ("guess", C.c_int), ("max_subspace", C.c_int), ("max_iter", C.c_int), ("batched", C.c_int),
+                ("subspace", C.c_int)]
 
 
 class xs_solve_info(C.Structure):
@@ -79,6 +81,8 @@ def load():
         "xs_get_amplitudes": (i, [vp, i, i, vp, vp, sz]),
         "xs_profile": (i, [vp, i]),
         "xs_gbuild_noalloc": (i, [vp, i, i, vp, vp]),
+        "xs_subspace_gram": (i, [vp, i, i, C.c_longlong, vp, vp, vp, i]),
+        "xs_subspace_combine": (i, [vp, i, i, i, C.c_longlong, vp, vp, vp, i]),
         "xs_mlp_nparams": (i, []),
         "xs_mlp_init": (i, [vp, C.c_ulonglong]),
         "xs_mlp_get_weights": (i, [vp, vp]),
@@ -184,10 +188,10 @@ def xs_apply(ctx, mol, kind, x, precision=XS_FP64, out=None):
 
 
 def xs_excited(ctx, method=XS_CIS, nroots=5, tol=1e-6, precision=XS_FP64, guess=XS_GUESS_PLAIN, max_subspace=0,
-               max_iter=0, batched=0, n_mol=1, outputs=None, allow=()):
+               max_iter=0, batched=0, n_mol=1, outputs=None, allow=(), subspace=0):
     """Returns dict(omega, osc, iters, resid, info, status); arrays of shape (n_mol, nroots)."""
     o = xs_ex_opts(int(method), int(nroots), float(tol), int(precision), int(guess), int(max_subspace),
-                   int(max_iter), int(batched))
+                   int(max_iter), int(batched), int(subspace))
     if outputs is None:
         outputs = dict(omega=np.zeros((n_mol, nroots)), osc=np.zeros((n_mol, nroots)),
                        iters=np.zeros(n_mol, dtype=np.int32), resid=np.zeros((n_mol, nroots)))
@@ -214,6 +218,30 @@ def xs_gbuild_noalloc(ctx, mol, R, G):
     """G(R) into caller-owned device arrays, no device allocation (see xs.h).
     Asynchronous on the context's stream."""
     return _check(ctx, load().xs_gbuild_noalloc(ctx, int(mol), int(R.shape[0]), _ptr(R), _ptr(G)))
+
+
+def xs_subspace_gram(ctx, A, B, emulated=True):
+    """C = A B^T (float64) for A (M x L) and B (N x L): on the tensor cores by
+    exact digit splitting (emulated=True) or on the float64 pipe."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, L = A.shape
+    N = B.shape[0]
+    Cm = np.empty((M, N))
+    _check(ctx, load().xs_subspace_gram(ctx, M, N, L, _ptr(A), _ptr(B), _ptr(Cm), int(bool(emulated))))
+    return Cm
+
+
+def xs_subspace_combine(ctx, X, coef, emulated=True):
+    """Y[k] = sum_b sum_m coef[b][m][k] X[b][m] for X (nb x S x L) and coef
+    (nb x S x nout), nb <= 3."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    nb, S, L = X.shape
+    nout = coef.shape[2]
+    Y = np.empty((nout, L))
+    _check(ctx, load().xs_subspace_combine(ctx, nb, S, nout, L, _ptr(X), _ptr(coef), _ptr(Y), int(bool(emulated))))
+    return Y
 
 
 def xs_mlp_nparams():
