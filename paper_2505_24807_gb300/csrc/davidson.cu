@@ -173,7 +173,10 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
     gram<double>(s, nnew, nnew, static_cast<int>(ov), w.T.get(), static_cast<int>(ov), w.T.get(),
                  static_cast<int>(ov), w.E2.get(), nnew, 1.0, 0.0, w.gws);
   }
-  syevk(s, nnew, nnew, w.E2.get(), nnew, w.w2.get(), w.Q2.get(), nnew, w.eig_ws, w.flag.get() + 1);
+  // Gram matrices of nearly dependent directions have eigenvalues spread over
+  // many decades; two-sided Jacobi resolves the small ones to high relative
+  // accuracy, which the Loewdin factors 1/sqrt(lambda) need
+  jacobi_eig(s, nnew, w.E2.get(), nnew, w.Q2.get(), nnew, w.w2.get(), w.flag.get() + 1);
   lowdin(s, nnew, w.w2.get(), w.Q2.get(), nnew, kLowdinThresh, w.Bm.get(), nnew, w.flag.get() + 2);
   int nkeep = 0;
   sync_copy(s, &nkeep, w.flag.get() + 2, sizeof(int));
@@ -583,7 +586,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
         // Gram (2k x 2k) of the coefficient columns
         gemm<double>(s, true, false, 2 * k, 2 * k, S, 1.0, w.tS.get(), 2 * k, 0, w.tS.get(), 2 * k, 0, 0.0,
                      w.E2.get(), 2 * k, 0, 1);
-        syevk(s, 2 * k, 2 * k, w.E2.get(), 2 * k, w.w2.get(), w.Q2.get(), 2 * k, w.eig_ws, w.flag.get() + 1);
+        jacobi_eig(s, 2 * k, w.E2.get(), 2 * k, w.Q2.get(), 2 * k, w.w2.get(), w.flag.get() + 1);
         lowdin(s, 2 * k, w.w2.get(), w.Q2.get(), 2 * k, kLowdinThresh, w.Bm.get(), 2 * k, w.flag.get() + 2);
         sync_copy(s, &nc, w.flag.get() + 2, sizeof(int));
         // Cn = Ycoef Bm^T (S x nc)
