@@ -54,9 +54,32 @@ def peaks():
 
 
 # float64 and float32 SIMT FMA throughput of this GB300 measured by the
-# project's own probe (profiles/peaks_probe.md): 1.195 and 72.99 TFLOP/s.
+# project's own probe kernel (paper_2505_24807_gb300/probe_peaks.cu): 1.195
+# and 72.99 TFLOP/s.
 FP64_SIMT_TFLOPS = 1.195
 FP32_SIMT_TFLOPS = 72.99
+
+
+def kernel_roofline(name, t, pk):
+    """Achieved rate of one profiled kernel family against its bound: digit
+    products, digit splits and the G build stream HBM (algorithmic bytes);
+    tensor-core GEMMs against the TF32 peak; SIMT kernels against the float64
+    or float32 pipe."""
+    per_launch_s = t["ms"] / 1e3 / t["launches"]
+    if name.startswith(("oz_", "gbuild")) and t["bytes"] > 0:
+        ach = t["bytes"] / t["launches"] / per_launch_s / 1e9
+        return dict(kernel=name, bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
+                    frac=ach / pk["hbm_gbs"], traffic=None, peak_source=pk["source"] + " hbm_gbs",
+                    bytes_per_launch=t["bytes"] / t["launches"], ms_per_launch=per_launch_s * 1e3)
+    ach = t["flops"] / t["launches"] / per_launch_s / 1e12
+    if name.startswith("tc_"):
+        peak, src, bound = pk["bf16_sustained"] / 2.0, pk["source"] + " bf16 sustained x 1/2 (tf32)", "tensor"
+    elif "f64" in name:
+        peak, src, bound = FP64_SIMT_TFLOPS, "measured fp64 FMA probe", "alu"
+    else:
+        peak, src, bound = FP32_SIMT_TFLOPS, "measured fp32 FMA probe", "alu"
+    return dict(kernel=name, bound=bound, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None,
+                peak_source=src, flops_per_launch=t["flops"] / t["launches"], ms_per_launch=per_launch_s * 1e3)
 
 
 class ClockSampler:
@@ -378,24 +401,9 @@ def main():
     pk = peaks()
     kernels = {k: v for k, v in prof.items() if k != "all_launches" and v["launches"] > 0}
     top_name = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
-    roof = None
-    if top_name:
-        t = kernels[top_name]
-        per_launch_s = t["ms"] / 1e3 / t["launches"]
-        if t["bytes"] > 0 and t["flops"] == 0:
-            ach = t["bytes"] / t["launches"] / per_launch_s / 1e9
-            roof = dict(kernel=top_name, bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
-                        frac=ach / pk["hbm_gbs"], traffic=None, peak_source=pk["source"] + " hbm_gbs")
-        else:
-            ach = t["flops"] / t["launches"] / per_launch_s / 1e12
-            if "f64" in top_name:
-                peak, src, bound = FP64_SIMT_TFLOPS, "measured fp64 FMA probe", "alu"
-            elif "tc" in top_name:
-                peak, src, bound = pk["bf16_sustained"] / 2.0, pk["source"] + " bf16 sustained x 1/2 (tf32)", "tensor"
-            else:
-                peak, src, bound = FP32_SIMT_TFLOPS, "measured fp32 FMA probe", "alu"
-            roof = dict(kernel=top_name, bound=bound, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                        traffic=None, peak_source=src)
+    roof = kernel_roofline(top_name, kernels[top_name], pk) if top_name else None
+    # the A.X product itself: its transforms (tensor cores) and G build (HBM)
+    ax = {k: kernel_roofline(k, kernels[k], pk) for k in kernels if k.startswith(("tc_gemm", "gbuild"))}
     kernel_table = {k: dict(launches=v["launches"], ms=round(v["ms"], 3),
                             share=round(v["ms"] / max(sum(x["ms"] for x in kernels.values()), 1e-9), 4))
                     for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["ms"])}
@@ -422,7 +430,7 @@ def main():
                     iterations=int(last["info"]["iterations"]), products=int(last["info"]["products"]),
                     converged=int(last["info"]["converged"]),
                     max_abs_err_vs_oracle_eV=oracle_err,
-                    roofline=roof, kernels=kernel_table, cpu_baseline=cpu, e2e=e2e,
+                    roofline=roof, ax_product=ax, kernels=kernel_table, cpu_baseline=cpu, e2e=e2e,
                     gpu_launches=int(prof.get("all_launches", {}).get("launches", 0)),
                     clocks=clk, fp64_gpu=fp64)
         print(json.dumps(line), flush=True)

@@ -78,6 +78,7 @@ std::unique_ptr<Ctx> make_worker(const Ctx& parent) {
 }
 
 void invalidate_mixed(DevMol& m) {
+  m.dip.release();
   m.CTf_hi.release();
   m.CTf_lo.release();
   m.CTf.release();

@@ -80,6 +80,7 @@ struct DevMol {
   DevBuf<double> eps;     // n orbital energies
   DevBuf<float> CTf_hi, CTf_lo;  // TF32-pair operand copies of CT for the tensor-core path
   DevBuf<float> CTf;             // float32 copy of CT for the float32 SIMT products
+  DevBuf<double> dip;            // MO dipole integrals <i|r_x|a>, 3 x nocc x nvir (lazily)
   bool ready = false;
   int scf_iterations = 0;
   // last excited-state solution

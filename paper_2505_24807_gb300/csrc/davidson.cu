@@ -58,7 +58,8 @@ struct Work {
   bool oz = false;
   long long Lp = 0;
   int ldk = 0, bcap = 0;
-  DevBuf<oz_t> Vtn, Vnn, S1nn, S2nn, Btn;
+  DevBuf<oz_t> Vtn, Vnn, S1nn, S2nn, Btn, Tnn;
+  int ldkT = 0;
   DevBuf<int> eV, eS1, eS2, eB;
   DevBuf<double> coef;
   OzWork ozw;
@@ -84,11 +85,11 @@ void slice_P(Ctx& c, Work& w, long long ov, const double* P, DevBuf<int>& e, Dev
            first);
 }
 
-// digits of count scratch rows T into Btn (exponents eB)
-void slice_T(Ctx& c, Work& w, long long ov, const double* T, int count) {
+// digits of count scratch rows T into Btn (exponents eB), and into Tnn when with_nn
+void slice_T(Ctx& c, Work& w, long long ov, const double* T, int count, bool with_nn = false) {
   if (count > w.bcap) throw Error(XS_EINVAL, "subspace scratch operand too small");
   oz_exponents(c.stream, count, ov, T, ov, w.eB.get(), w.ozw, c.tc_err.get());
-  oz_slice(c.stream, count, ov, T, ov, w.eB.get(), w.Btn.get(), w.Lp, 0, nullptr, 0, 0);
+  oz_slice(c.stream, count, ov, T, ov, w.eB.get(), w.Btn.get(), w.Lp, 0, with_nn ? w.Tnn.get() : nullptr, w.ldkT, 0);
 }
 
 // Coefficients of the CIS step, outputs [X (kk) | R (kk)] with X_j = V q_j and
@@ -166,7 +167,7 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
     }
   }
   if (w.oz) {
-    slice_T(c, w, ov, w.T.get(), nnew);
+    slice_T(c, w, ov, w.T.get(), nnew, true);
     oz_gram(s, nnew, nnew, ov, w.Btn.get(), w.Lp, w.eB.get(), w.Btn.get(), w.Lp, w.eB.get(), 1.0, 0.0, w.E2.get(),
             nnew, w.ozw, c.tc_err.get());
   } else {
@@ -180,9 +181,17 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
   lowdin(s, nnew, w.w2.get(), w.Q2.get(), nnew, kLowdinThresh, w.Bm.get(), nnew, w.flag.get() + 2);
   int nkeep = 0;
   sync_copy(s, &nkeep, w.flag.get() + 2, sizeof(int));
-  if (nkeep > 0)
-    gemm<double>(s, false, false, nkeep, static_cast<int>(ov), nnew, 1.0, w.Bm.get(), nnew, 0, w.T.get(),
-                 static_cast<int>(ov), 0, 0.0, Vout, static_cast<int>(ov), 0, 1);
+  if (nkeep > 0) {
+    if (w.oz) {
+      // Vout = Bm T on the tensor cores: coefficients Bm^T (nnew x nkeep)
+      transpose(s, nkeep, nnew, w.Bm.get(), w.coef.get());
+      const OzBlock b{w.Tnn.get(), w.ldkT, w.eB.get(), w.coef.get(), nkeep};
+      oz_combine(s, 1, &b, nnew, nkeep, ov, 1.0, 0.0, Vout, ov, w.ozw, c.tc_err.get());
+    } else {
+      gemm<double>(s, false, false, nkeep, static_cast<int>(ov), nnew, 1.0, w.Bm.get(), nnew, 0, w.T.get(),
+                   static_cast<int>(ov), 0, 0.0, Vout, static_cast<int>(ov), 0, 1);
+    }
+  }
   return nkeep;
 }
 
@@ -211,59 +220,74 @@ void make_guess(Ctx& c, const DevMol& m, Work& w, int nguess, long long ov, cons
   XS_CUDA(cudaStreamSynchronize(s));
 }
 
+// Transition dipoles through the MO dipole integrals D^x_ia = <i|r_x|a>
+// (paper, Section "Results": oscillator strengths of the excited states):
+// the AO dipole operator is R_A on the diagonal plus the one-centre
+// <s|r_x|p_x> = D1 of each heavy atom, so D^x = C_occ^T (r_x C_vir) with
+// r_x C_vir formed elementwise; then d_n = sqrt(2) sum_ia U_n,ia D_ia and
+// f_n = 2/3 omega_n |d_n|^2 in atomic units.
+
+// Bt[a][mu] = (r_x C_vir)[mu][a], component x
+__global__ void dipole_rc_kernel(int n, int o, int v, int x, const int* __restrict__ ao_atom,
+                                 const int* __restrict__ ao_local, const int* __restrict__ atom_elem,
+                                 const double* __restrict__ xyz, const double* __restrict__ par,
+                                 const double* __restrict__ CT, double* __restrict__ Bt) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)v * n) return;
+  const int a = static_cast<int>(idx / n), mu = static_cast<int>(idx % n);
+  const int A = ao_atom[mu];
+  const double* c = CT + (size_t)(o + a) * n;
+  double r = xyz[3 * A + x] * c[mu];
+  const int loc = ao_local[mu];
+  const bool heavy = (loc == 0) ? (mu + 3 < n && ao_atom[mu + 3] == A && ao_local[mu + 3] == 3) : (loc > 0);
+  if (heavy) {
+    const double D1 = par[atom_elem[A] * XS_NPARAM + 9];
+    if (loc == 0) r = fma(D1, c[mu + 1 + x], r);
+    else if (loc == 1 + x) r = fma(D1, c[mu - 1 - x], r);
+  }
+  Bt[idx] = r;
+}
+
+__global__ void osc_from_dipoles_kernel(int k, const double* __restrict__ dm, const double* __restrict__ omega,
+                                        double* __restrict__ f) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s2 = 0.0;
+  for (int x = 0; x < 3; ++x) {
+    const double d = dm[j * 3 + x] * (1.4142135623730951 / kBohrA);
+    s2 += d * d;
+  }
+  f[j] = (2.0 / 3.0) * (omega[j] / kHartreeEV) * s2;
+}
+
 }  // namespace
 
-// f_n = 2/3 omega_n |d_n|^2 (atomic units), d_n = sqrt(2) sum_{mu nu} R^n_{mu nu} <mu|r|nu>,
-// R^n = C_occ U_n C_vir^T, <mu|r|nu> = R_A delta_{mu nu} + one-centre <s|r_i|p_i> = D1.
-__global__ void osc_kernel(int n, const int* __restrict__ ao_atom, const int* __restrict__ ao_local,
-                           const int* __restrict__ atom_elem, const double* __restrict__ xyz,
-                           const double* __restrict__ par, const double* __restrict__ R,
-                           const double* __restrict__ omega, double* __restrict__ f) {
-  const int k = blockIdx.x;
-  const double* Rk = R + (long long)k * n * n;
-  double d[3] = {0.0, 0.0, 0.0};
-  for (int mu = threadIdx.x; mu < n; mu += blockDim.x) {
-    int A = ao_atom[mu];
-    double r = Rk[(long long)mu * n + mu];
-    for (int x = 0; x < 3; ++x) d[x] += r * xyz[3 * A + x];
-    if (ao_local[mu] == 0 && mu + 3 < n && ao_atom[mu + 3] == A && ao_local[mu + 3] == 3) {
-      double D1 = par[atom_elem[A] * XS_NPARAM + 9];
-      for (int x = 0; x < 3; ++x) d[x] += D1 * (Rk[(long long)mu * n + mu + 1 + x] + Rk[(long long)(mu + 1 + x) * n + mu]);
-    }
-  }
-  __shared__ double sh[3][32];
+void mo_dipoles(Ctx& c, DevMol& m) {
+  if (m.dip.get()) return;
+  cudaStream_t s = c.stream;
+  const int n = m.n, o = m.o, v = m.v;
+  const long long ov = (long long)o * v;
+  m.dip.alloc((size_t)3 * ov);
+  c.ws4.ensure((size_t)v * n);
   for (int x = 0; x < 3; ++x) {
-    double v = d[x];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[x][threadIdx.x >> 5] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s2 = 0.0;
-    for (int x = 0; x < 3; ++x) {
-      double v = 0.0;
-      for (int j = 0; j < (int)(blockDim.x >> 5); ++j) v += sh[x][j];
-      v *= 1.4142135623730951 / kBohrA;
-      s2 += v * v;
-    }
-    f[k] = (2.0 / 3.0) * (omega[k] / kHartreeEV) * s2;
+    dipole_rc_kernel<<<grid1((long long)v * n, 256), 256, 0, s>>>(n, o, v, x, m.ao_atom.get(), m.ao_local.get(),
+                                                                m.atom_elem.get(), m.xyz.get(), c.d_par.get(),
+                                                                m.CT.get(), c.ws4.get());
+    XS_CHECK_LAUNCH();
+    gemm<double>(s, false, true, o, v, n, 1.0, m.CT.get(), n, 0, c.ws4.get(), n, 0, 0.0, m.dip.get() + (size_t)x * ov, v,
+                 0, 1);
   }
 }
 
-void oscillator_strengths(Ctx& c, const DevMol& m, int kk, const double* U, const double* omega_dev, double* f_dev) {
+void oscillator_strengths(Ctx& c, DevMol& m, int kk, const double* U, const double* omega_dev, double* f_dev) {
   cudaStream_t s = c.stream;
-  const int n = m.n, o = m.o, v = m.v;
-  const long long nn = (long long)n * n;
-  c.ws1.ensure((size_t)kk * nn);
-  c.ws4.ensure((size_t)kk * n * (o > v ? o : v));
-  // R_k = C_occ U_k C_vir^T
-  const double* CTocc = m.CT.get();
-  const double* CTvir = m.CT.get() + (size_t)o * n;
-  gemm<double>(s, true, false, n, v, o, 1.0, CTocc, n, 0, U, v, (long long)o * v, 0.0, c.ws4.get(), v,
-               (long long)n * v, kk);
-  gemm<double>(s, false, false, kk * n, n, v, 1.0, c.ws4.get(), v, 0, CTvir, n, 0, 0.0, c.ws1.get(), n, 0, 1);
-  osc_kernel<<<kk, 256, 0, s>>>(n, m.ao_atom.get(), m.ao_local.get(), m.atom_elem.get(), m.xyz.get(),
-                                c.d_par.get(), c.ws1.get(), omega_dev, f_dev);
+  const long long ov = (long long)m.o * m.v;
+  mo_dipoles(c, m);
+  c.ws5.ensure((size_t)3 * kk);
+  // dm[j][x] = sum_ia U_j,ia D^x_ia
+  gram<double>(s, kk, 3, static_cast<int>(ov), U, static_cast<int>(ov), m.dip.get(), static_cast<int>(ov), c.ws5.get(),
+               3, 1.0, 0.0, c.ws0);
+  osc_from_dipoles_kernel<<<grid1(kk, 64), 64, 0, s>>>(kk, c.ws5.get(), omega_dev, f_dev);
   XS_CHECK_LAUNCH();
 }
 
@@ -318,6 +342,9 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     w.bcap = std::max(maxnew, std::max(nguess, 2 * kk));
     w.Vtn.alloc((size_t)Smax * kOzDigits * w.Lp);
     w.Btn.alloc((size_t)w.bcap * kOzDigits * w.Lp);
+    w.ldkT = oz_ldk(w.bcap);
+    w.Tnn.alloc((size_t)ov * w.ldkT);
+    XS_CUDA(cudaMemsetAsync(w.Tnn.get(), 0, sizeof(oz_t) * ov * w.ldkT, s));
     // combination operands: digit columns past S * 8 are read (times zero
     // coefficients) and must hold finite values
     w.Vnn.alloc((size_t)ov * w.ldk);

@@ -21,6 +21,9 @@ struct SolveStats {
 int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st);
 
 // f (device, kk) from amplitudes U (kk x ov, X or X+Y) and omega (device, eV)
-void oscillator_strengths(Ctx& c, const DevMol& m, int kk, const double* U, const double* omega_dev, double* f_dev);
+// MO dipole integrals D^x_ia (3 x nocc x nvir) of the molecule, computed once
+// and kept in m.dip until the orbitals change.
+void mo_dipoles(Ctx& c, DevMol& m);
+void oscillator_strengths(Ctx& c, DevMol& m, int kk, const double* U, const double* omega_dev, double* f_dev);
 
 }  // namespace xs

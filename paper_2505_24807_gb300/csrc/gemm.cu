@@ -115,6 +115,156 @@ __global__ void reduce_split(int M, int N, int kSplit, const T* __restrict__ P, 
   *c = r;
 }
 
+// float32 C = alpha op(A) op(B) + beta C for large M and N: 128 x 128 tiles,
+// 8 x 8 outputs per thread (as 2 x 2 blocks of 4 x 4 for conflict-free
+// float4 shared-memory reads), K staged 8 at a time through a double-buffered
+// shared-memory ring with the next tile prefetched into registers.  vecA /
+// vecB: the operand allows aligned float4 global loads along its contiguous
+// dimension.
+constexpr int FB = 128, FK = 8;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) sgemm_big_kernel(int M, int N, int K, float alpha, const float* __restrict__ A,
+                                                        int lda, long long sA, const float* __restrict__ B, int ldb,
+                                                        long long sB, float beta, float* __restrict__ C, int ldc,
+                                                        long long sC, int vecA, int vecB) {
+  __shared__ __align__(16) float As[2][FK][FB + 4];
+  __shared__ __align__(16) float Bs[2][FK][FB + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * FB, n0 = blockIdx.x * FB;
+  A += blockIdx.z * sA;
+  B += blockIdx.z * sB;
+  C += blockIdx.z * sC;
+
+  float ra[4], rb[4];
+  // global -> registers for the K tile starting at k0
+  auto load_tiles = [&](int k0) {
+    if (!TA) {
+      const int m = tid / 2, kk = (tid % 2) * 4;
+      const int gm = m0 + m, gk = k0 + kk;
+      if (vecA && gm < M && gk + 3 < K) {
+        const float4 t = *reinterpret_cast<const float4*>(A + (long long)gm * lda + gk);
+        ra[0] = t.x; ra[1] = t.y; ra[2] = t.z; ra[3] = t.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ra[q] = (gm < M && gk + q < K) ? A[(long long)gm * lda + gk + q] : 0.0f;
+      }
+    } else {
+      const int kk = tid / 32, m = (tid % 32) * 4;
+      const int gk = k0 + kk, gm = m0 + m;
+      if (vecA && gk < K && gm + 3 < M) {
+        const float4 t = *reinterpret_cast<const float4*>(A + (long long)gk * lda + gm);
+        ra[0] = t.x; ra[1] = t.y; ra[2] = t.z; ra[3] = t.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ra[q] = (gk < K && gm + q < M) ? A[(long long)gk * lda + gm + q] : 0.0f;
+      }
+    }
+    if (!TB) {
+      const int kk = tid / 32, n = (tid % 32) * 4;
+      const int gk = k0 + kk, gn = n0 + n;
+      if (vecB && gk < K && gn + 3 < N) {
+        const float4 t = *reinterpret_cast<const float4*>(B + (long long)gk * ldb + gn);
+        rb[0] = t.x; rb[1] = t.y; rb[2] = t.z; rb[3] = t.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rb[q] = (gk < K && gn + q < N) ? B[(long long)gk * ldb + gn + q] : 0.0f;
+      }
+    } else {
+      const int n = tid / 2, kk = (tid % 2) * 4;
+      const int gn = n0 + n, gk = k0 + kk;
+      if (vecB && gn < N && gk + 3 < K) {
+        const float4 t = *reinterpret_cast<const float4*>(B + (long long)gn * ldb + gk);
+        rb[0] = t.x; rb[1] = t.y; rb[2] = t.z; rb[3] = t.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rb[q] = (gn < N && gk + q < K) ? B[(long long)gn * ldb + gk + q] : 0.0f;
+      }
+    }
+  };
+  auto store_tiles = [&](int buf) {
+    if (!TA) {
+      const int m = tid / 2, kk = (tid % 2) * 4;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) As[buf][kk + q][m] = ra[q];
+    } else {
+      const int kk = tid / 32, m = (tid % 32) * 4;
+      *reinterpret_cast<float4*>(&As[buf][kk][m]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+    }
+    if (!TB) {
+      const int kk = tid / 32, n = (tid % 32) * 4;
+      *reinterpret_cast<float4*>(&Bs[buf][kk][n]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    } else {
+      const int n = tid / 2, kk = (tid % 2) * 4;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Bs[buf][kk + q][n] = rb[q];
+    }
+  };
+
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+  load_tiles(0);
+  store_tiles(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += FK) {
+    const bool more = k0 + FK < K;
+    if (more) load_tiles(k0 + FK);
+#pragma unroll
+    for (int kk = 0; kk < FK; ++kk) {
+      float a[8], b[8];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      store_tiles(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+      if (gn >= N) continue;
+      float* c = C + (long long)gm * ldc + gn;
+      float r = alpha * acc[i][j];
+      if (beta != 0.0f) r = fmaf(beta, *c, r);
+      *c = r;
+    }
+  }
+}
+
+void sgemm_big(cudaStream_t s, bool tA, bool tB, int M, int N, int K, float alpha, const float* A, int lda,
+               long long sA, const float* B, int ldb, long long sB, float beta, float* C, int ldc, long long sC,
+               int batch) {
+  auto al = [](const float* p, int ld, long long st) {
+    return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && (ld % 4 == 0) && (st % 4 == 0) ? 1 : 0;
+  };
+  const int vA = al(A, lda, sA), vB = al(B, ldb, sB);
+  dim3 grid((N + FB - 1) / FB, (M + FB - 1) / FB, batch);
+  if (!tA && !tB) sgemm_big_kernel<false, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, vA, vB);
+  else if (!tA && tB) sgemm_big_kernel<false, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, vA, vB);
+  else if (tA && !tB) sgemm_big_kernel<true, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, vA, vB);
+  else sgemm_big_kernel<true, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, vA, vB);
+}
+
 // Tile shapes (BM, BN, TM, TN), all 256 threads.  The float64 pipe of this
 // part is narrow enough that the Davidson GEMMs run pipe-bound, so every
 // padded row or column of a tile is lost time: the shape that pads M x N
@@ -189,6 +339,13 @@ void gemm(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K < 0) K = 0;
   ProfScope ps(s, sizeof(T) == 8 ? "gemm_f64" : "gemm_f32", 0.0, 2.0 * M * N * (double)K * batch);
+  if (sizeof(T) == 4 && M >= 64 && N >= 64 && K >= 32) {
+    sgemm_big(s, transA, transB, M, N, K, static_cast<float>(alpha), reinterpret_cast<const float*>(A), lda, sA,
+              reinterpret_cast<const float*>(B), ldb, sB, static_cast<float>(beta), reinterpret_cast<float*>(C), ldc,
+              sC, batch);
+    XS_CHECK_LAUNCH();
+    return;
+  }
   launch_gemm<T>(s, pick_shape(M, N), M, N, K, alpha, A, lda, sA, transA, B, ldb, sB, transB, beta, C, ldc, sC, batch,
                  1, 0);
   XS_CHECK_LAUNCH();
