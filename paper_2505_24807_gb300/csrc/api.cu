@@ -187,7 +187,7 @@ int xs_ground_state(xs_ctx* ctx, int n_mol, const int* natoms, const int* Z, con
       upload(s, m.atom_prod_off, m.L.prod_off);
       upload(s, m.atom_elem, m.L.elem);
       upload(s, m.xyz, m.L.xyz);
-      XS_CUDA(cudaStreamSynchronize(s));
+      xs::build_gtiles(s, m);
       int it = xs::run_scf(c, m, scf_tol, max_iter);
       maxit = it > maxit ? it : maxit;
       m.ready = true;

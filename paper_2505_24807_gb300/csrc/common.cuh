@@ -81,6 +81,8 @@ struct DevMol {
   DevBuf<float> CTf_hi, CTf_lo;  // TF32-pair operand copies of CT for the tensor-core path
   DevBuf<float> CTf;             // float32 copy of CT for the float32 SIMT products
   DevBuf<double> dip;            // MO dipole integrals <i|r_x|a>, 3 x nocc x nvir (lazily)
+  DevBuf<int> gb_rows, gb_cols;  // atom-aligned G tiles (first AO, count, first atom, end atom)
+  int gb_nrows = 0, gb_ncols = 0;
   bool ready = false;
   int scf_iterations = 0;
   // last excited-state solution

@@ -15,10 +15,15 @@
 //      (R_ls + R_sl for l < s, R_ll on the diagonal);
 //   2. two-centre Coulomb J2 = W r with the dense product supermatrix W
 //      (one GEMM over the batch: W is read once per batch);
-//   3. one thread per output element G_{mu lam}: diagonal atom blocks combine
-//      J2 with the closed-form one-centre Coulomb/exchange; off-diagonal blocks
-//      hold the two-centre exchange sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig}.
+//   3. atom-aligned tiles of G (one row group x one column tile per CTA, the
+//      tile's pair-integral block staged once in shared memory, the nvec
+//      matrices streamed through it): diagonal atom blocks combine J2 with the
+//      closed-form one-centre Coulomb/exchange; off-diagonal blocks hold the
+//      two-centre exchange sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig}.
+#include <vector>
+
 #include "kernels.h"
+#include "model.h"
 #include "prof.h"
 
 namespace xs {
@@ -91,76 +96,135 @@ __device__ __forceinline__ void one_centre(const T* p, int a, int b, const T Rd[
   K1ba = K1(b, a);
 }
 
+// Atom-aligned tiles of G: a CTA owns one row group (a heavy atom's 4 AOs, or
+// up to 4 consecutive hydrogens) and one column tile (whole atoms, at most 64
+// AOs).  It stages the pair-integral block W[products of the rows' atoms]
+// [products of the columns' atoms] in shared memory once and then streams the
+// nvec matrices: per matrix, R's tile (and for TDHF its transpose tile) goes
+// through shared memory and every thread writes one G (and G-) element.
+constexpr int kGR = 4, kGC = 64, kGP = 10, kGQ = 160;
+
 template <typename T, GMode MODE>
-__global__ void __launch_bounds__(256) assemble_kernel(int n, int np, int nvec, const int* __restrict__ ao_atom,
-                                                       const int* __restrict__ ao_local,
-                                                       const int* __restrict__ atom_ao_off,
-                                                       const int* __restrict__ atom_nao,
-                                                       const int* __restrict__ atom_prod_off,
-                                                       const int* __restrict__ atom_elem,
-                                                       const double* __restrict__ par, const T* __restrict__ W,
-                                                       const T* __restrict__ J2, const T* __restrict__ Rall,
-                                                       T* __restrict__ Gall, T* __restrict__ Gmall) {
-  const int lam = blockIdx.x * 32 + threadIdx.x;
-  const int mu = blockIdx.y * 8 + threadIdx.y;
-  const int v = blockIdx.z;
-  if (lam >= n || mu >= n) return;
-  const T* R = Rall + (long long)v * n * n;
-  const int A = ao_atom[mu], B = ao_atom[lam];
-  const int a = ao_local[mu], b = ao_local[lam];
-  const int oA = atom_ao_off[A], oB = atom_ao_off[B];
-  const int nA = atom_nao[A], nB = atom_nao[B];
-  const int PA = atom_prod_off[A], PB = atom_prod_off[B];
-  T g, gm = T(0);
-  if (A == B) {
-    const double* pd = par + atom_elem[A] * XS_NPARAM;
-    T p[XS_NPARAM];
+__global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, const int4* __restrict__ rows,
+                                                    const int4* __restrict__ cols, const int* __restrict__ ao_atom,
+                                                    const int* __restrict__ ao_local,
+                                                    const int* __restrict__ atom_ao_off,
+                                                    const int* __restrict__ atom_nao,
+                                                    const int* __restrict__ atom_prod_off,
+                                                    const int* __restrict__ atom_elem,
+                                                    const double* __restrict__ par, const T* __restrict__ W,
+                                                    const T* __restrict__ J2, const T* __restrict__ Rall,
+                                                    T* __restrict__ Gall, T* __restrict__ Gmall) {
+  __shared__ T Ws[kGP][kGQ + 1];
+  __shared__ T Rt[kGR][kGC + 1];
+  __shared__ T Rtt[kGC][kGR + 1];
+  const int4 rg = rows[blockIdx.y], ct = cols[blockIdx.x];
+  const int ra = rg.x, nr = rg.y, cb = ct.x, nc = ct.y;
+  const int PA0 = atom_prod_off[rg.z], PB0 = atom_prod_off[ct.z];
+  const int nPA = atom_prod_off[rg.w - 1] + (atom_nao[rg.w - 1] == 4 ? 10 : 1) - PA0;
+  const int nPB = atom_prod_off[ct.w - 1] + (atom_nao[ct.w - 1] == 4 ? 10 : 1) - PB0;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < nPA * nPB; idx += blockDim.x) {
+    const int pr = idx / nPB, pc = idx % nPB;
+    Ws[pr][pc] = W[(long long)(PA0 + pr) * np + PB0 + pc];
+  }
+  const int ri = tid / kGC, ci = tid % kGC;
+  const bool active = ri < nr && ci < nc;
+  const int mu = ra + ri, lam = cb + ci;
+  int A = 0, B = 0, a = 0, b = 0, nA = 1, nB = 1, rA = 0, cA = 0, rB = 0, pA = 0, pB = 0, PA = 0;
+  T p[XS_NPARAM];
+  if (active) {
+    A = ao_atom[mu]; B = ao_atom[lam];
+    a = ao_local[mu]; b = ao_local[lam];
+    nA = atom_nao[A]; nB = atom_nao[B];
+    rA = atom_ao_off[A] - ra;          // A's first row in the tile
+    cA = atom_ao_off[A] - cb;          // A's first column (diagonal block)
+    rB = atom_ao_off[B] - cb;          // B's first column in the tile
+    PA = atom_prod_off[A];
+    pA = PA - PA0;
+    pB = atom_prod_off[B] - PB0;
+    if (A == B) {
+      const double* pd = par + atom_elem[A] * XS_NPARAM;
 #pragma unroll
-    for (int i = 0; i < XS_NPARAM; ++i) p[i] = T(pd[i]);
-    T J1, K1ab, K1ba;
-    if (nA == 1) {
-      T r00 = R[(long long)oA * n + oA];
-      J1 = p[4] * r00;
-      K1ab = K1ba = p[4] * r00;
-    } else {
-      T Rd[16];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) Rd[i * 4 + j] = R[(long long)(oA + i) * n + oA + j];
-      one_centre<T>(p, a, b, Rd, J1, K1ab, K1ba);
-    }
-    const int pab = (nA == 4) ? pidx(a, b) : 0;
-    const T J = J1 + J2[(long long)(PA + pab) * nvec + v];
-    if (MODE == G_CIS) {
-      g = T(2) * J - K1ab;
-    } else {
-      g = T(4) * J - (K1ab + K1ba);
-      gm = -(K1ab - K1ba);
-    }
-  } else {
-    // K(R)_{mu lam} = sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig}
-    // K(R^T)_{mu lam} = sum (mu nu|lam sig) R_{sig nu}
-    T kr = T(0), krt = T(0);
-    for (int nu = 0; nu < nA; ++nu) {
-      const int p = (nA == 4) ? pidx(a, nu) : 0;
-      const T* Wrow = W + (long long)(PA + p) * np + PB;
-      for (int sg = 0; sg < nB; ++sg) {
-        const int q = (nB == 4) ? pidx(b, sg) : 0;
-        const T w = Wrow[q];
-        kr = fma(w, R[(long long)(oA + nu) * n + oB + sg], kr);
-        if (MODE == G_RPA) krt = fma(w, R[(long long)(oB + sg) * n + oA + nu], krt);
-      }
-    }
-    if (MODE == G_CIS) {
-      g = -kr;
-    } else {
-      g = -(kr + krt);
-      gm = -(kr - krt);
+      for (int i = 0; i < XS_NPARAM; ++i) p[i] = T(pd[i]);
     }
   }
-  Gall[(long long)v * n * n + (long long)mu * n + lam] = g;
-  if (MODE == G_RPA) Gmall[(long long)v * n * n + (long long)mu * n + lam] = gm;
+  __syncthreads();
+  for (int v = 0; v < nvec; ++v) {
+    const T* R = Rall + (long long)v * n * n;
+    if (active) Rt[ri][ci] = R[(long long)mu * n + lam];
+    if (MODE == G_RPA) {
+      // transpose tile: consecutive threads along the (at most 4) contiguous
+      // row elements, so a warp reads 8 rows of up to 16 bytes
+      const int tr = tid % kGR, tc = tid / kGR;
+      if (tr < nr && tc < nc) Rtt[tc][tr] = R[(long long)(cb + tc) * n + ra + tr];
+    }
+    __syncthreads();
+    if (active) {
+      T g, gm = T(0);
+      if (A == B) {
+        T J1, K1ab, K1ba;
+        if (nA == 1) {
+          const T r00 = Rt[rA][cA];
+          J1 = p[4] * r00;
+          K1ab = K1ba = p[4] * r00;
+        } else {
+          T Rd[16];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Rd[i * 4 + j] = Rt[rA + i][cA + j];
+          one_centre<T>(p, a, b, Rd, J1, K1ab, K1ba);
+        }
+        const int pab = (nA == 4) ? pidx(a, b) : 0;
+        const T J = J1 + J2[(long long)(PA + pab) * nvec + v];
+        if (MODE == G_CIS) {
+          g = T(2) * J - K1ab;
+        } else {
+          g = T(4) * J - (K1ab + K1ba);
+          gm = -(K1ab - K1ba);
+        }
+      } else {
+        // K(R)_{mu lam} = sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig},
+        // K(R^T)_{mu lam} = sum (mu nu|lam sig) R_{sig nu}
+        T kr = T(0), krt = T(0);
+        for (int nu = 0; nu < nA; ++nu) {
+          const T* Wrow = Ws[pA + ((nA == 4) ? pidx(a, nu) : 0)] + pB;
+          for (int sg = 0; sg < nB; ++sg) {
+            const T w = Wrow[(nB == 4) ? pidx(b, sg) : 0];
+            kr = fma(w, Rt[rA + nu][rB + sg], kr);
+            if (MODE == G_RPA) krt = fma(w, Rtt[rB + sg][rA + nu], krt);
+          }
+        }
+        if (MODE == G_CIS) {
+          g = -kr;
+        } else {
+          g = -(kr + krt);
+          gm = -(kr - krt);
+        }
+      }
+      Gall[(long long)v * n * n + (long long)mu * n + lam] = g;
+      if (MODE == G_RPA) Gmall[(long long)v * n * n + (long long)mu * n + lam] = gm;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_tiles(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* W, const T* J2,
+                  const T* R, T* G, T* Gm) {
+  dim3 grid(m.gb_ncols, m.gb_nrows);
+  const int4* rows = reinterpret_cast<const int4*>(m.gb_rows.get());
+  const int4* cols = reinterpret_cast<const int4*>(m.gb_cols.get());
+  if (mode == G_CIS)
+    gtile_kernel<T, G_CIS><<<grid, 256, 0, s>>>(m.n, m.np, nvec, rows, cols, m.ao_atom.get(), m.ao_local.get(),
+                                                m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
+                                                m.atom_elem.get(), d_par, W, J2, R, G, nullptr);
+  else
+    gtile_kernel<T, G_RPA><<<grid, 256, 0, s>>>(m.n, m.np, nvec, rows, cols, m.ao_atom.get(), m.ao_local.get(),
+                                                m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
+                                                m.atom_elem.get(), d_par, W, J2, R, G, Gm);
+  XS_CHECK_LAUNCH();
 }
 
 }  // namespace
@@ -184,21 +248,11 @@ void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, in
   if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(m.W.get());
   else W = reinterpret_cast<const T*>(m.Wf.get());
   gemm<T>(s, false, false, np, nvec, np, T(1), W, np, 0, r, nvec, 0, T(0), J2, nvec, 0, 1);
-  dim3 block(32, 8);
-  dim3 grid((n + 31) / 32, (n + 7) / 8, nvec);
   // algorithmic traffic: read R, write G (and G-), read the pair integrals once
   const double outs = (mode == G_CIS) ? 1.0 : 2.0;
   ProfScope ps(s, sizeof(T) == 8 ? "gbuild_assemble_f64" : "gbuild_assemble_f32",
                sizeof(T) * ((double)nvec * n * n * (1.0 + outs) + (double)np * np), 0.0);
-  if (mode == G_CIS)
-    assemble_kernel<T, G_CIS><<<grid, block, 0, s>>>(n, np, nvec, m.ao_atom.get(), m.ao_local.get(),
-                                                     m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
-                                                     m.atom_elem.get(), d_par, W, J2, R, G, nullptr);
-  else
-    assemble_kernel<T, G_RPA><<<grid, block, 0, s>>>(n, np, nvec, m.ao_atom.get(), m.ao_local.get(),
-                                                     m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
-                                                     m.atom_elem.get(), d_par, W, J2, R, G, Gm);
-  XS_CHECK_LAUNCH();
+  launch_tiles<T>(s, m, d_par, mode, nvec, W, J2, R, G, Gm);
 }
 
 template <typename T>
@@ -217,17 +271,36 @@ void gbuild_raw(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode
   if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(m.W.get());
   else W = reinterpret_cast<const T*>(m.Wf.get());
   gemm<T>(s, false, false, np, nvec, np, T(1), W, np, 0, r, nvec, 0, T(0), J2, nvec, 0, 1);
-  dim3 block(32, 8);
-  dim3 grid((n + 31) / 32, (n + 7) / 8, nvec);
-  if (mode == G_CIS)
-    assemble_kernel<T, G_CIS><<<grid, block, 0, s>>>(n, np, nvec, m.ao_atom.get(), m.ao_local.get(),
-                                                     m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
-                                                     m.atom_elem.get(), d_par, W, J2, R, G, nullptr);
-  else
-    assemble_kernel<T, G_RPA><<<grid, block, 0, s>>>(n, np, nvec, m.ao_atom.get(), m.ao_local.get(),
-                                                     m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
-                                                     m.atom_elem.get(), d_par, W, J2, R, G, Gm);
-  XS_CHECK_LAUNCH();
+  launch_tiles<T>(s, m, d_par, mode, nvec, W, J2, R, G, Gm);
+}
+
+void build_gtiles(cudaStream_t s, DevMol& m) {
+  const MolLayout& L = m.L;
+  std::vector<int> rows, cols;   // per tile: first AO, AO count, first atom, end atom
+  for (int A = 0; A < L.natoms;) {
+    int A1 = A, cnt = 0;
+    if (L.nao_atom[A] == 4) {
+      A1 = A + 1;
+      cnt = 4;
+    } else {
+      while (A1 < L.natoms && L.nao_atom[A1] == 1 && cnt < kGR) { ++A1; ++cnt; }
+    }
+    rows.insert(rows.end(), {L.ao_off[A], cnt, A, A1});
+    A = A1;
+  }
+  for (int A = 0; A < L.natoms;) {
+    int A1 = A, cnt = 0;
+    while (A1 < L.natoms && cnt + L.nao_atom[A1] <= kGC) { cnt += L.nao_atom[A1]; ++A1; }
+    cols.insert(cols.end(), {L.ao_off[A], cnt, A, A1});
+    A = A1;
+  }
+  m.gb_nrows = static_cast<int>(rows.size() / 4);
+  m.gb_ncols = static_cast<int>(cols.size() / 4);
+  m.gb_rows.alloc(rows.size());
+  m.gb_cols.alloc(cols.size());
+  XS_CUDA(cudaMemcpyAsync(m.gb_rows.get(), rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, s));
+  XS_CUDA(cudaMemcpyAsync(m.gb_cols.get(), cols.data(), sizeof(int) * cols.size(), cudaMemcpyHostToDevice, s));
+  XS_CUDA(cudaStreamSynchronize(s));
 }
 
 template void gbuild<double>(cudaStream_t, const DevMol&, const double*, GMode, int, const double*, double*,

@@ -28,6 +28,9 @@ enum GMode { G_CIS = 0, G_RPA = 1 };
 template <typename T>
 void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* R,
             T* G, T* Gm, DevBuf<T>& ws);
+// Atom-aligned tiling of G used by gbuild (rows: one heavy atom or up to 4
+// hydrogens; columns: whole atoms, at most 64 AOs); built once per molecule.
+void build_gtiles(cudaStream_t s, DevMol& m);
 // The same with caller-provided scratch: r and J2 of np * nvec elements each.
 template <typename T>
 void gbuild_raw(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* R, T* G,

@@ -15,10 +15,14 @@
 //                   t = i + j of the digit pairs, so one float32 accumulator per
 //                   (l, k, t) sums exact integers; the epilogue weights t by
 //                   2^(-7t) (pairs with i + j > 9 fall below float64 rounding).
-// Warp 0 issues TMA loads through a STAGES-deep mbarrier ring, warp 1 owns
-// TMEM and issues the MMAs (M = 128, N = BN, K = 16 per instruction), warps
-// 2-5 drain the accumulators.  Every wait is bounded; a timeout raises the
-// error word and the CTA leaves after draining what it issued.
+// Persistent CTAs (one per SM) walk the tiles: warp 0 issues TMA loads
+// through a STAGES-deep mbarrier ring that runs on across tiles, warp 1 owns
+// TMEM and issues the MMAs (M = 128, N = BN, K = 16 per instruction) into two
+// alternating accumulators, warps 2-5 drain one accumulator while the next
+// tile accumulates in the other.  The epilogue folds the eight float32
+// digit sums with integer arithmetic (horner8) and two float64 conversions:
+// this part's float64 pipe is narrow.  Every wait is bounded; a timeout
+// raises the error word and the CTA leaves after draining what it issued.
 #include <algorithm>
 
 #include "kernels.h"
@@ -80,6 +84,8 @@ __device__ __forceinline__ uint4 pack8(const int* d) {
 
 struct OzArgs {
   int mode;          // 0: gram partials, 1: combination
+  int ntiles;        // work tiles of the launch
+  int n_mtiles;      // mode 0: 128-row tiles of A (tile t: row tile t % n_mtiles, chunk t / n_mtiles)
   int kb_total;      // K blocks of the whole product (mode 0)
   int kb_per_cta;    // mode 0: K blocks per chunk; mode 1: K blocks of this launch
   int kb_begin;      // mode 1: first K block of this launch (concatenated over blocks)
@@ -90,8 +96,8 @@ struct OzArgs {
   double* Y;         // mode 1
   long long ldy;
   long long L;
-  double alpha, beta;
-  const int* fexp;
+  double beta;
+  const double* scale;   // mode 1: per output k, alpha 2^(f_k - 42) and alpha 2^(f_k - 63)
 };
 
 template <int BN>
@@ -101,9 +107,32 @@ struct OzCfg {
   static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr int STAGES = (200 * 1024) / STAGE > 8 ? 8 : (200 * 1024) / STAGE;
   static constexpr int TCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
-  static constexpr size_t SMEM = 1024 + static_cast<size_t>(STAGES) * STAGE + (2 * STAGES + 1) * 8 + 16;
+  static constexpr size_t SMEM = 1024 + static_cast<size_t>(STAGES) * STAGE + (2 * STAGES + 4) * 8 + 16;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Eight float32 accumulators holding exact integers (|v| <= 2^24), weights
+// 2^(-7 t) relative to v[0]: split as h = v0 2^28 + v1 2^21 + v2 2^14 + v3 2^7 + v4
+// (< 2^53, exact in float64) and g = v5 2^14 + v6 2^7 + v7, formed in integer
+// arithmetic; two float64 conversions replace eight float64 multiply-adds.
+__device__ __forceinline__ void horner8(const float* v, double& h, double& g) {
+  long long hi = __float2int_rn(v[0]);
+#pragma unroll
+  for (int t = 1; t < 5; ++t) hi = hi * 128 + __float2int_rn(v[t]);
+  long long lo = __float2int_rn(v[5]);
+  lo = lo * 128 + __float2int_rn(v[6]);
+  lo = lo * 128 + __float2int_rn(v[7]);
+  h = static_cast<double>(hi);
+  g = static_cast<double>(lo);
+}
+
+// Persistent kernel: each CTA walks the tiles t = blockIdx.x, + gridDim.x ...;
+// the TMA producer streams the K blocks of consecutive tiles through one
+// stage ring without draining between tiles, the MMA warp alternates between
+// two TMEM accumulators so that the epilogue of one tile overlaps the next.
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
     oz_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
@@ -114,92 +143,126 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(base + C::STAGES * C::STAGE);
   uint64_t* empty = full + C::STAGES;
-  uint64_t* accfull = empty + C::STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
+  uint64_t* accf = empty + C::STAGES;    // [2]: accumulator ready for the epilogue
+  uint64_t* acce = accf + 2;             // [2]: accumulator drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m0 = blockIdx.x * BM;
-  int kb0, nk;
-  if (a.mode == 0) {
-    kb0 = blockIdx.y * a.kb_per_cta;
-    nk = min(a.kb_per_cta, a.kb_total - kb0);
-  } else {
-    kb0 = a.kb_begin;
-    nk = a.kb_per_cta;
-  }
+  auto tile_of = [&](int t, int& m0, int& kb0, int& nk, int& kc) {
+    if (a.mode == 0) {
+      kc = t / a.n_mtiles;
+      m0 = (t - kc * a.n_mtiles) * BM;
+      kb0 = kc * a.kb_per_cta;
+      nk = min(a.kb_per_cta, a.kb_total - kb0);
+    } else {
+      kc = 0;
+      m0 = t * BM;
+      kb0 = a.kb_begin;
+      nk = a.kb_per_cta;
+    }
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(tmem_slot, C::TCOLS);
+  if (warp == 1) tmem_alloc(tmem_slot, 2 * C::TCOLS);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    int issued = 0;
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % C::STAGES;
-      if (it >= C::STAGES && !mbar_wait(&empty[s], ((it / C::STAGES) + 1) & 1, err, 1)) break;
-      uint8_t* st = base + s * C::STAGE;
-      mbar_expect_tx(&full[s], C::STAGE);
-      const int kb = kb0 + it;
-      if (a.mode == 0) {
-        tma_load_2d(st, &tmA0, &full[s], kb * BKE, m0);
-      } else {
-        const int b = kb / a.kb_per_blk;
-        const CUtensorMap* ta = b == 0 ? &tmA0 : (b == 1 ? &tmA1 : &tmA2);
-        tma_load_2d(st, ta, &full[s], (kb - b * a.kb_per_blk) * BKE, m0);
+    // TMA producer
+    long long g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      int m0, kb0, nk, kc;
+      tile_of(t, m0, kb0, nk, kc);
+      for (int it = 0; it < nk; ++it, ++g) {
+        const int s = static_cast<int>(g % C::STAGES);
+        if (g >= C::STAGES && !mbar_wait(&empty[s], static_cast<uint32_t>(((g / C::STAGES) + 1) & 1), err, 1)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = base + s * C::STAGE;
+        mbar_expect_tx(&full[s], C::STAGE);
+        const int kb = kb0 + it;
+        if (a.mode == 0) {
+          tma_load_2d(st, &tmA0, &full[s], kb * BKE, m0);
+        } else {
+          const int b = kb / a.kb_per_blk;
+          const CUtensorMap* ta = b == 0 ? &tmA0 : (b == 1 ? &tmA1 : &tmA2);
+          tma_load_2d(st, ta, &full[s], (kb - b * a.kb_per_blk) * BKE, m0);
+        }
+        tma_load_2d(st + C::A_BYTES, &tmB, &full[s], kb * BKE, 0);
       }
-      tma_load_2d(st + C::A_BYTES, &tmB, &full[s], kb * BKE, 0);
-      ++issued;
     }
-    for (int it = (issued > C::STAGES ? issued - C::STAGES : 0); it < issued; ++it)
-      mbar_wait(&empty[it % C::STAGES], (it / C::STAGES) & 1, err, 0) || true;
+    // the copies still in flight complete before the CTA leaves (bounded)
+    for (long long q = (g > C::STAGES ? g - C::STAGES : 0); q < g; ++q)
+      mbar_wait(&empty[q % C::STAGES], static_cast<uint32_t>((q / C::STAGES) & 1), err, 0) || true;
   } else if (warp == 1 && lane == 0) {
+    // MMA issue
     constexpr uint32_t idesc = idesc_f32acc(1, BM, BN);
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % C::STAGES;
-      if (!mbar_wait(&full[s], (it / C::STAGES) & 1, err, 2)) break;
+    long long g = 0;
+    int i = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++i) {
+      int m0, kb0, nk, kc;
+      tile_of(t, m0, kb0, nk, kc);
+      const int buf = i & 1;
+      if (i >= 2 && !mbar_wait(&acce[buf], static_cast<uint32_t>(((i >> 1) + 1) & 1), err, 4)) break;
       fence_after_sync();
-      uint8_t* st = base + s * C::STAGE;
-      const uint32_t aa = smem_u32(st), bb = smem_u32(st + C::A_BYTES);
+      const uint32_t acc = tmem + static_cast<uint32_t>(buf * C::TCOLS);
+      for (int it = 0; it < nk; ++it, ++g) {
+        const int s = static_cast<int>(g % C::STAGES);
+        if (!mbar_wait(&full[s], static_cast<uint32_t>((g / C::STAGES) & 1), err, 2)) {
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        uint8_t* st = base + s * C::STAGE;
+        const uint32_t aa = smem_u32(st), bb = smem_u32(st + C::A_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BKE / 16; ++kk) {
-        const uint32_t off = kk * 32;   // 16 bf16 per MMA step
-        mma_bf16(tmem, sdesc(aa + off), sdesc(bb + off), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < BKE / 16; ++kk) {
+          const uint32_t off = kk * 32;   // 16 bf16 per MMA step
+          mma_bf16(acc, sdesc(aa + off), sdesc(bb + off), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(&empty[s]);
       }
-      mma_commit(&empty[s]);
+      if (ok) mma_commit(&accf[buf]);
     }
-    mma_commit(accfull);
   } else if (warp >= 2) {
+    // epilogue: TMEM lanes 32 (warp % 4) .. + 31
     const int q = warp & 3;
     const int r = 32 * q + lane;
-    const uint32_t trow = tmem + (static_cast<uint32_t>(32 * q) << 16);
-    const bool ok = mbar_wait(accfull, 0, err, 3);
-    fence_after_sync();
-    if (ok && !*reinterpret_cast<volatile int*>(err)) {
+    int i = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++i) {
+      int m0, kb0, nk, kc;
+      tile_of(t, m0, kb0, nk, kc);
+      const int buf = i & 1;
+      if (!mbar_wait(&accf[buf], static_cast<uint32_t>((i >> 1) & 1), err, 3)) break;
+      fence_after_sync();
+      const uint32_t trow = tmem + static_cast<uint32_t>(buf * C::TCOLS) + (static_cast<uint32_t>(32 * q) << 16);
       if (a.mode == 0) {
-        const int i = r & 7;
-        const double wi = ldexp(1.0, -7 * (i + 1));
+        // row r = digit plane i of vector m0/8 + r/8; column n*8 + j
+        const int di = r & 7;
+        const double c1 = ldexp(1.0, -35 - 7 * (di + 1)), c2 = ldexp(1.0, -56 - 7 * (di + 1));
         const int mv = (m0 + r) >> 3;
-        double* out = a.part + (static_cast<size_t>(blockIdx.y) * a.Mvec + mv) * a.ncols;
+        double* out = a.part + (static_cast<size_t>(kc) * a.Mvec + mv) * a.ncols;
         for (int n = 0; n < a.ncols; ++n) {
           float v[8];
           tmem_ld8(trow + n * 8, v);
-          double sum = 0.0, wj = 0.0078125;
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            sum = fma(static_cast<double>(v[j]), wj, sum);
-            wj *= 0.0078125;
-          }
-          sum *= wi;
+          double h, gg;
+          horner8(v, h, gg);
+          double sum = fma(h, c1, gg * c2);
           sum += __shfl_xor_sync(0xffffffffu, sum, 1);
           sum += __shfl_xor_sync(0xffffffffu, sum, 2);
           sum += __shfl_xor_sync(0xffffffffu, sum, 4);
@@ -210,27 +273,25 @@ __global__ void __launch_bounds__(192, 1)
         for (int k = 0; k < a.ncols; ++k) {
           float v[8];
           tmem_ld8(trow + k * 8, v);
-          double sum = 0.0, wt = 0.0078125 * 0.0078125;
-#pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            sum = fma(static_cast<double>(v[t]), wt, sum);
-            wt *= 0.0078125;
-          }
           if (l < a.L) {
-            double y = a.alpha * ldexp(sum, a.fexp[k]);
+            double h, gg;
+            horner8(v, h, gg);
+            double y = fma(h, a.scale[2 * k], gg * a.scale[2 * k + 1]);
             double* p = a.Y + static_cast<size_t>(k) * a.ldy + l;
             if (a.beta != 0.0) y = fma(a.beta, *p, y);
             *p = y;
           }
         }
       }
+      fence_before_sync();
+      mbar_arrive(&acce[buf]);
     }
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 1) {
     fence_after_sync();
-    tmem_dealloc(tmem, C::TCOLS);
+    tmem_dealloc(tmem, 2 * C::TCOLS);
   }
 }
 
@@ -303,8 +364,8 @@ struct CoefArgs {
 // column (k, t) of the product (row k * 8 + t here, K-major over the
 // concatenated blocks) holds at K index (b, m, i) the digit t - i of
 // c'[b][m] = coef_b[m][k] 2^(e_b[m]), split with the common exponent f[k].
-__global__ void oz_coef_kernel(int nb, int S, int Kp, int k0, CoefArgs ca, oz_t* __restrict__ bmat,
-                               int* __restrict__ fexp, int* err) {
+__global__ void oz_coef_kernel(int nb, int S, int Kp, int k0, CoefArgs ca, double alpha, oz_t* __restrict__ bmat,
+                               double* __restrict__ scale, int* err) {
   const int k = blockIdx.x;
   const int rowK = nb * Kp;
   const int per = Kp / kOzDigits;
@@ -324,7 +385,11 @@ __global__ void oz_coef_kernel(int nb, int S, int Kp, int k0, CoefArgs ca, oz_t*
   const int ex = static_cast<int>((M >> 52) & 0x7FF);
   if (threadIdx.x == 0 && ex == 0x7FF) atomicCAS(err, 0, 11);
   const int f = (M == 0) ? 0 : ex - 1021;
-  if (threadIdx.x == 0) fexp[k] = f;
+  if (threadIdx.x == 0) {
+    // output weights of the anti-diagonal sums split as in horner8
+    scale[2 * k] = alpha * ldexp(1.0, f - 42);
+    scale[2 * k + 1] = alpha * ldexp(1.0, f - 63);
+  }
   for (int idx = threadIdx.x; idx < nb * per; idx += blockDim.x) {
     const int b = idx / per, m = idx % per;
     int d[kOzDigits];
@@ -361,8 +426,18 @@ CUtensorMap make_map_bf16(const oz_t* ptr, long long inner, long long rows, long
   return m;
 }
 
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    XS_CUDA(cudaGetDevice(&dev));
+    XS_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return n;
+}
+
 template <int BN>
-void launch_oz(cudaStream_t s, dim3 grid, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
+void launch_oz(cudaStream_t s, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
                const CUtensorMap& b, const OzArgs& args, int* err) {
   using C = OzCfg<BN>;
   static bool attr = false;
@@ -371,19 +446,20 @@ void launch_oz(cudaStream_t s, dim3 grid, const CUtensorMap& a0, const CUtensorM
                                  static_cast<int>(C::SMEM)));
     attr = true;
   }
+  const int grid = std::min(args.ntiles, num_sms());   // persistent: one CTA per SM
   oz_kernel<BN><<<grid, 192, C::SMEM, s>>>(a0, a1, a2, b, args, err);
   XS_CHECK_LAUNCH();
 }
 
 int pick_bn(int cols) { return cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 192 ? 192 : 256; }
 
-void dispatch(cudaStream_t s, int bn, dim3 grid, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
+void dispatch(cudaStream_t s, int bn, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
               const CUtensorMap& b, const OzArgs& args, int* err) {
   switch (bn) {
-    case 64: launch_oz<64>(s, grid, a0, a1, a2, b, args, err); break;
-    case 128: launch_oz<128>(s, grid, a0, a1, a2, b, args, err); break;
-    case 192: launch_oz<192>(s, grid, a0, a1, a2, b, args, err); break;
-    default: launch_oz<256>(s, grid, a0, a1, a2, b, args, err); break;
+    case 64: launch_oz<64>(s, a0, a1, a2, b, args, err); break;
+    case 128: launch_oz<128>(s, a0, a1, a2, b, args, err); break;
+    case 192: launch_oz<192>(s, a0, a1, a2, b, args, err); break;
+    default: launch_oz<256>(s, a0, a1, a2, b, args, err); break;
   }
 }
 
@@ -433,15 +509,16 @@ void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long lo
     w.part.ensure(static_cast<size_t>(nchunk) * M * nn);
     OzArgs a{};
     a.mode = 0;
+    a.n_mtiles = (M * kOzDigits + BM - 1) / BM;
+    a.ntiles = a.n_mtiles * nchunk;
     a.kb_total = kb_total;
     a.kb_per_cta = KB_CHUNK;
     a.ncols = nn;
     a.Mvec = M;
     a.part = w.part.get();
-    dim3 grid((M * kOzDigits + BM - 1) / BM, nchunk);
     {
       ProfScope ps(s, "oz_gram", 2.0 * kOzDigits * static_cast<double>(L) * (M + nn), 2.0 * M * nn * (double)L);
-      dispatch(s, bn, grid, ta, ta, ta, tb, a, err);
+      dispatch(s, bn, ta, ta, ta, tb, a, err);
     }
     oz_reduce_kernel<<<grid1(static_cast<long long>(M) * nn, 256), 256, 0, s>>>(M, nn, nchunk, w.part.get(), eA,
                                                                                eB + n0, alpha, beta, C + n0, ldc);
@@ -471,14 +548,15 @@ void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, lon
     const int nk = std::min(kMaxCols, nout - k0);
     const int bn = pick_bn(nk * kOzDigits);
     w.bmat.ensure(static_cast<size_t>(nk) * kOzDigits * nb * Kp);
-    w.fexp.ensure(kMaxCols);
-    oz_coef_kernel<<<nk, 256, 0, s>>>(nb, S, Kp, k0, ca, w.bmat.get(), w.fexp.get(), err);
+    w.scale.ensure(2 * kMaxCols);
+    oz_coef_kernel<<<nk, 256, 0, s>>>(nb, S, Kp, k0, ca, alpha, w.bmat.get(), w.scale.get(), err);
     XS_CHECK_LAUNCH();
     const CUtensorMap tb = make_map_bf16(w.bmat.get(), static_cast<long long>(nb) * Kp,
                                          static_cast<long long>(nk) * kOzDigits, static_cast<long long>(nb) * Kp, bn);
     for (int kb = 0; kb < kb_total; kb += KB_CHUNK) {
       OzArgs a{};
       a.mode = 1;
+      a.ntiles = static_cast<int>((L + BM - 1) / BM);
       a.kb_begin = kb;
       a.kb_per_cta = std::min(KB_CHUNK, kb_total - kb);
       a.kb_per_blk = kb_per_blk;
@@ -486,15 +564,13 @@ void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, lon
       a.Y = Y + static_cast<size_t>(k0) * ldy;
       a.ldy = ldy;
       a.L = L;
-      a.alpha = alpha;
       a.beta = kb == 0 ? beta : 1.0;
-      a.fexp = w.fexp.get();
-      dim3 grid(static_cast<unsigned>((L + BM - 1) / BM), 1);
+      a.scale = w.scale.get();
       ProfScope ps(s, "oz_combine",
                    2.0 * kOzDigits * static_cast<double>(L) * a.kb_per_cta * BKE / kOzDigits +
                        8.0 * nk * (double)L * (a.beta != 0.0 ? 2 : 1),
                    2.0 * nk * (double)L * a.kb_per_cta * BKE / kOzDigits);
-      dispatch(s, bn, grid, ta[0], ta[1], ta[2], tb, a, err);
+      dispatch(s, bn, ta[0], ta[1], ta[2], tb, a, err);
     }
   }
 }

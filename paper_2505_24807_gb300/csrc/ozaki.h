@@ -28,7 +28,7 @@ constexpr int kOzChunk = 4096;   // digit products summed exactly per float32 ac
 struct OzWork {
   DevBuf<double> part;              // split partial sums of oz_gram
   DevBuf<oz_t> bmat;                // digit matrix of the oz_combine coefficients
-  DevBuf<int> fexp;                 // their per-output exponents
+  DevBuf<double> scale;             // their per-output weights (two per output)
   DevBuf<unsigned long long> mx;    // per-row max |x| bit patterns
 };
 
