@@ -404,8 +404,17 @@ def main():
     roof = kernel_roofline(top_name, kernels[top_name], pk) if top_name else None
     # the A.X product itself: its transforms (tensor cores) and G build (HBM)
     ax = {k: kernel_roofline(k, kernels[k], pk) for k in kernels if k.startswith(("tc_gemm", "gbuild"))}
+    def _rate(v):
+        sec = v["ms"] / 1e3
+        out = {}
+        if v["bytes"] > 0:
+            out["GBps"] = round(v["bytes"] / sec / 1e9, 1)
+        if v["flops"] > 0:
+            out["TFLOPps"] = round(v["flops"] / sec / 1e12, 2)
+        return out
+
     kernel_table = {k: dict(launches=v["launches"], ms=round(v["ms"], 3),
-                            share=round(v["ms"] / max(sum(x["ms"] for x in kernels.values()), 1e-9), 4))
+                            share=round(v["ms"] / max(sum(x["ms"] for x in kernels.values()), 1e-9), 4), **_rate(v))
                     for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["ms"])}
 
     cpu = None

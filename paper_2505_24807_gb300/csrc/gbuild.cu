@@ -38,8 +38,10 @@ __device__ __forceinline__ int pidx(int a, int b) {
   return base[lo] + (hi - lo);
 }
 
-template <typename T>
-__global__ void pack_diag_kernel(int natoms, int n, int nvec, const int* __restrict__ atom_ao_off,
+// product vectors of the diagonal atom blocks: r[q][v] (TR = false) or its
+// transpose r[v][q] (TR = true, the operand of the split-K product W r)
+template <typename T, bool TR>
+__global__ void pack_diag_kernel(int natoms, int n, int np, int nvec, const int* __restrict__ atom_ao_off,
                                  const int* __restrict__ atom_nao, const int* __restrict__ atom_prod_off,
                                  const T* __restrict__ R, T* __restrict__ r) {
   int A = blockIdx.x * blockDim.y + threadIdx.y;
@@ -48,14 +50,15 @@ __global__ void pack_diag_kernel(int natoms, int n, int nvec, const int* __restr
   for (; v < nvec; v += blockDim.x) {
     const T* Rv = R + (long long)v * n * n;
     int o = atom_ao_off[A], P = atom_prod_off[A];
+    auto at = [&](int q) -> T& { return TR ? r[(long long)v * np + q] : r[(long long)q * nvec + v]; };
     if (atom_nao[A] == 1) {
-      r[(long long)P * nvec + v] = Rv[(long long)o * n + o];
+      at(P) = Rv[(long long)o * n + o];
     } else {
       for (int a = 0; a < 4; ++a)
         for (int b = a; b < 4; ++b) {
           T val = Rv[(long long)(o + a) * n + o + b];
           if (b != a) val += Rv[(long long)(o + b) * n + o + a];
-          r[(long long)(P + pidx(a, b)) * nvec + v] = val;
+          at(P + pidx(a, b)) = val;
         }
     }
   }
@@ -115,9 +118,11 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
                                                     const double* __restrict__ par, const T* __restrict__ W,
                                                     const T* __restrict__ J2, const T* __restrict__ Rall,
                                                     T* __restrict__ Gall, T* __restrict__ Gmall) {
+  // R tiles padded by 4 rows / columns of zeros: a hydrogen's block is
+  // handled as a 4 x 4 block with zero weights past its single AO
   __shared__ T Ws[kGP][kGQ + 1];
-  __shared__ T Rt[kGR][kGC + 1];
-  __shared__ T Rtt[kGC][kGR + 1];
+  __shared__ T Rt[kGR + 4][kGC + 4];
+  __shared__ T Rtt[kGC + 4][kGR + 4];
   const int4 rg = rows[blockIdx.y], ct = cols[blockIdx.x];
   const int ra = rg.x, nr = rg.y, cb = ct.x, nc = ct.y;
   const int PA0 = atom_prod_off[rg.z], PB0 = atom_prod_off[ct.z];
@@ -127,6 +132,10 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
   for (int idx = tid; idx < nPA * nPB; idx += blockDim.x) {
     const int pr = idx / nPB, pc = idx % nPB;
     Ws[pr][pc] = W[(long long)(PA0 + pr) * np + PB0 + pc];
+  }
+  for (int idx = tid; idx < (kGR + 4) * (kGC + 4); idx += blockDim.x) {
+    (&Rt[0][0])[idx] = T(0);
+    (&Rtt[0][0])[idx] = T(0);
   }
   const int ri = tid / kGC, ci = tid % kGC;
   const bool active = ri < nr && ci < nc;
@@ -150,6 +159,19 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
     }
   }
   __syncthreads();
+  // this output's 16 exchange weights (mu nu|lam sig) for nu in A, sig in B,
+  // zero past a hydrogen's single AO; independent of the matrix index
+  T wv[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) wv[q] = T(0);
+  if (active && A != B) {
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu)
+#pragma unroll
+      for (int sg = 0; sg < 4; ++sg)
+        if (nu < nA && sg < nB)
+          wv[nu * 4 + sg] = Ws[pA + ((nA == 4) ? pidx(a, nu) : 0)][pB + ((nB == 4) ? pidx(b, sg) : 0)];
+  }
   for (int v = 0; v < nvec; ++v) {
     const T* R = Rall + (long long)v * n * n;
     if (active) Rt[ri][ci] = R[(long long)mu * n + lam];
@@ -188,14 +210,13 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
         // K(R)_{mu lam} = sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig},
         // K(R^T)_{mu lam} = sum (mu nu|lam sig) R_{sig nu}
         T kr = T(0), krt = T(0);
-        for (int nu = 0; nu < nA; ++nu) {
-          const T* Wrow = Ws[pA + ((nA == 4) ? pidx(a, nu) : 0)] + pB;
-          for (int sg = 0; sg < nB; ++sg) {
-            const T w = Wrow[(nB == 4) ? pidx(b, sg) : 0];
-            kr = fma(w, Rt[rA + nu][rB + sg], kr);
-            if (MODE == G_RPA) krt = fma(w, Rtt[rB + sg][rA + nu], krt);
+#pragma unroll
+        for (int nu = 0; nu < 4; ++nu)
+#pragma unroll
+          for (int sg = 0; sg < 4; ++sg) {
+            kr = fma(wv[nu * 4 + sg], Rt[rA + nu][rB + sg], kr);
+            if (MODE == G_RPA) krt = fma(wv[nu * 4 + sg], Rtt[rB + sg][rA + nu], krt);
           }
-        }
         if (MODE == G_CIS) {
           g = -kr;
         } else {
@@ -235,19 +256,22 @@ void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, in
   if (nvec <= 0) return;
   const int n = m.n, np = m.np;
   ws.ensure((size_t)2 * np * nvec);
-  T* r = ws.get();
+  T* rT = ws.get();
   T* J2 = ws.get() + (size_t)np * nvec;
   {
     dim3 block(8, 32);
     dim3 grid((m.L.natoms + 31) / 32);
-    pack_diag_kernel<T><<<grid, block, 0, s>>>(m.L.natoms, n, nvec, m.atom_ao_off.get(), m.atom_nao.get(),
-                                                m.atom_prod_off.get(), R, r);
+    pack_diag_kernel<T, true><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(), m.atom_nao.get(),
+                                                     m.atom_prod_off.get(), R, rT);
     XS_CHECK_LAUNCH();
   }
   const T* W = nullptr;
   if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(m.W.get());
   else W = reinterpret_cast<const T*>(m.Wf.get());
-  gemm<T>(s, false, false, np, nvec, np, T(1), W, np, 0, r, nvec, 0, T(0), J2, nvec, 0, 1);
+  // two-centre Coulomb J2 = W r: W streamed once, split over its columns so
+  // that the skinny product fills the GPU
+  static thread_local DevBuf<T> split_ws;
+  gram<T>(s, np, nvec, np, W, np, rT, np, J2, nvec, T(1), T(0), split_ws);
   // algorithmic traffic: read R, write G (and G-), read the pair integrals once
   const double outs = (mode == G_CIS) ? 1.0 : 2.0;
   ProfScope ps(s, sizeof(T) == 8 ? "gbuild_assemble_f64" : "gbuild_assemble_f32",
@@ -263,8 +287,8 @@ void gbuild_raw(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode
   {
     dim3 block(8, 32);
     dim3 grid((m.L.natoms + 31) / 32);
-    pack_diag_kernel<T><<<grid, block, 0, s>>>(m.L.natoms, n, nvec, m.atom_ao_off.get(), m.atom_nao.get(),
-                                                m.atom_prod_off.get(), R, r);
+    pack_diag_kernel<T, false><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(),
+                                                      m.atom_nao.get(), m.atom_prod_off.get(), R, r);
     XS_CHECK_LAUNCH();
   }
   const T* W = nullptr;

@@ -7,12 +7,15 @@
 // which keeps about 21 significant bits -- the "split-precision (hi + lo)
 // products" that carry the dense C X C^T transforms of the A*X product.
 //
-// One CTA computes one 128 x BN tile (cta_group::1, M = 128):
+// Persistent CTAs (one per SM) walk the 128 x BN output tiles (cta_group::1,
+// M = 128):
 //   warp 0      TMA producer: four 128-byte-swizzled boxes per K block of 32
-//   warp 1      TMEM allocation and the single-thread MMA issue
+//   warp 1      TMEM allocation and the single-thread MMA issue into two
+//               alternating accumulators
 //   warps 2..5  epilogue: tcgen05.ld of the 128 accumulator lanes, stores
-// A 3-stage mbarrier ring couples producer and MMA; tcgen05.commit frees a
-// stage and finally signals the epilogue.  Every wait is bounded by the
+// A 3-stage mbarrier ring couples producer and MMA across tiles;
+// tcgen05.commit frees a stage and signals the epilogue, which hands the
+// accumulator back through a second barrier pair.  Every wait is bounded by the
 // global timer; a timeout sets the error word, the CTA skips the remaining
 // work, waits (bounded) for its issued copies and MMAs, frees TMEM and exits.
 #include "kernels.h"
@@ -57,11 +60,19 @@ struct EpiArgs {
   int o;                // mode 2: number of occupied orbitals (eps offset of the virtuals)
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent: each CTA walks the output tiles t = blockIdx.x, + gridDim.x, ...
+// (batch entry major, then row tile, then column tile); the TMA ring runs on
+// across tiles and the MMA warp alternates two TMEM accumulators so that a
+// tile's epilogue overlaps the next tile's loads and MMAs.
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int M, int N,
-                   int Kpad, int a3, int b3, EpiArgs ep, int* err) {
+                   int Kpad, int a3, int b3, int ntm, int ntn, int ntiles, EpiArgs ep, int* err) {
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned stage buffers (the 128-byte swizzle repeats every 1024 bytes)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -71,79 +82,109 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t* stage_base = base;
   uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accfull = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
+  uint64_t* accf = empty + STAGES;   // [2]
+  uint64_t* acce = accf + 2;         // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, bz = blockIdx.z;
   const int nk = Kpad / BK;
+  auto tile_of = [&](int t, int& m0, int& n0, int& bz) {
+    bz = t / (ntm * ntn);
+    const int r = t - bz * ntm * ntn;
+    m0 = (r / ntn) * BM;
+    n0 = (r % ntn) * BN;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
-    tmem_alloc(tmem_slot, BN);
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
+  fence_before_sync();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
     // producer
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) + 1) & 1, err, 1)) break;
-      uint8_t* st = stage_base + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      const int k = kb * BK;
-      tma_load(st, &tmAh, &full[s], k, m0, bz, a3);
-      tma_load(st + A_BYTES, &tmAl, &full[s], k, m0, bz, a3);
-      tma_load(st + 2 * A_BYTES, &tmBh, &full[s], k, n0, bz, b3);
-      tma_load(st + 2 * A_BYTES + B_BYTES, &tmBl, &full[s], k, n0, bz, b3);
-      ++issued;
+    long long g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int m0, n0, bz;
+      tile_of(t, m0, n0, bz);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = static_cast<int>(g % STAGES);
+        if (g >= STAGES && !mbar_wait(&empty[s], static_cast<uint32_t>(((g / STAGES) + 1) & 1), err, 1)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = stage_base + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        const int k = kb * BK;
+        tma_load(st, &tmAh, &full[s], k, m0, bz, a3);
+        tma_load(st + A_BYTES, &tmAl, &full[s], k, m0, bz, a3);
+        tma_load(st + 2 * A_BYTES, &tmBh, &full[s], k, n0, bz, b3);
+        tma_load(st + 2 * A_BYTES + B_BYTES, &tmBl, &full[s], k, n0, bz, b3);
+      }
     }
     // wait for the copies still in flight before leaving (bounded)
-    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-      mbar_wait(&empty[kb % STAGES], ((kb / STAGES) + 0) & 1, err, 0) || true;
+    for (long long q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
+      mbar_wait(&empty[q % STAGES], static_cast<uint32_t>((q / STAGES) & 1), err, 0) || true;
   } else if (warp == 1 && lane == 0) {
     // MMA issue
     constexpr uint32_t idesc = idesc_f32acc(2, BM, BN);
+    long long g = 0;
+    int i = 0;
     bool ok = true;
-    for (int kb = 0; kb < nk && ok; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1, err, 2)) { ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint8_t* st = stage_base + s * STAGE_BYTES;
-      const uint32_t ah = smem_u32(st), al = smem_u32(st + A_BYTES);
-      const uint32_t bh = smem_u32(st + 2 * A_BYTES), bl = smem_u32(st + 2 * A_BYTES + B_BYTES);
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      if (i >= 2 && !mbar_wait(&acce[buf], static_cast<uint32_t>(((i >> 1) + 1) & 1), err, 4)) break;
+      fence_after_sync();
+      const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = static_cast<int>(g % STAGES);
+        if (!mbar_wait(&full[s], static_cast<uint32_t>((g / STAGES) & 1), err, 2)) {
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        uint8_t* st = stage_base + s * STAGE_BYTES;
+        const uint32_t ah = smem_u32(st), al = smem_u32(st + A_BYTES);
+        const uint32_t bh = smem_u32(st + 2 * A_BYTES), bl = smem_u32(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BK / 8; ++kk) {
-        const uint32_t off = kk * 32;  // 8 tf32 per MMA step
-        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(tmem, sdesc(ah + off), sdesc(bh + off), idesc, acc0);
-        mma_tf32(tmem, sdesc(ah + off), sdesc(bl + off), idesc, 1u);
-        mma_tf32(tmem, sdesc(al + off), sdesc(bh + off), idesc, 1u);
+        for (int kk = 0; kk < BK / 8; ++kk) {
+          const uint32_t off = kk * 32;  // 8 tf32 per MMA step
+          const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+          mma_tf32(acc, sdesc(ah + off), sdesc(bh + off), idesc, acc0);
+          mma_tf32(acc, sdesc(ah + off), sdesc(bl + off), idesc, 1u);
+          mma_tf32(acc, sdesc(al + off), sdesc(bh + off), idesc, 1u);
+        }
+        mma_commit(&empty[s]);
       }
-      mma_commit(&empty[s]);
+      if (ok) mma_commit(&accf[buf]);
     }
-    mma_commit(accfull);
   } else if (warp >= 2) {
     // epilogue: TMEM lanes 32*(warp % 4) .. +31 are this warp's rows
     const int lane_base = 32 * (warp % 4);
-    const int row = m0 + lane_base + lane;
-    bool ok = mbar_wait(accfull, 0, err, 3);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && !*reinterpret_cast<volatile int*>(err)) {
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      int m0, n0, bz;
+      tile_of(t, m0, n0, bz);
+      const int buf = i & 1;
+      if (!mbar_wait(&accf[buf], static_cast<uint32_t>((i >> 1) & 1), err, 3)) break;
+      fence_after_sync();
+      const int row = m0 + lane_base + lane;
+      const uint32_t trow = tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(lane_base) << 16);
       for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
-        tmem_ld16(tmem + (static_cast<uint32_t>(lane_base) << 16) + c0, v);
+        tmem_ld16(trow + c0, v);
         if (row >= M) continue;
         const long long rb = (long long)bz * ep.bstride + (long long)row * ep.ld;
 #pragma unroll
@@ -171,13 +212,15 @@ __global__ void __launch_bounds__(192, 1)
           }
         }
       }
+      fence_before_sync();
+      mbar_arrive(&acce[buf]);
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  fence_before_sync();
   __syncthreads();
   if (warp == 1) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    fence_after_sync();
+    tmem_dealloc(tmem, 2 * BN);
   }
 }
 
@@ -224,7 +267,7 @@ CUtensorMap make_map(const float* ptr, int rows, int kpad, int ld, int batch, lo
 
 template <int BN>
 size_t smem_bytes() {
-  return 1024 + STAGES * (2 * BM * BK * 4 + 2 * BN * BK * 4) + (2 * STAGES + 1) * 8 + 16;
+  return 1024 + STAGES * (2 * BM * BK * 4 + 2 * BN * BK * 4) + (2 * STAGES + 4) * 8 + 16;
 }
 
 }  // namespace
@@ -261,10 +304,18 @@ void tc_gemm(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int 
                                  static_cast<int>(smem)));
     attr_set = true;
   }
-  dim3 grid((N + BNv - 1) / BNv, (M + BM - 1) / BM, batch);
+  const int ntm = (M + BM - 1) / BM, ntn = (N + BNv - 1) / BNv;
+  const int ntiles = ntm * ntn * batch;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    XS_CUDA(cudaGetDevice(&dev));
+    XS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int grid = ntiles < nsm ? ntiles : nsm;   // persistent: one CTA per SM
   ProfScope ps(s, "tc_gemm_tf32x3", 0.0, 2.0 * 3.0 * M * N * (double)Kpad * batch);
   tc_gemm_kernel<BNv><<<grid, 192, smem, s>>>(ah, al, bh, bl, M, N, Kpad, A.batched && batch > 1 ? 1 : 0,
-                                              B.batched && batch > 1 ? 1 : 0, ep, d_err);
+                                              B.batched && batch > 1 ? 1 : 0, ntm, ntn, ntiles, ep, d_err);
   XS_CHECK_LAUNCH();
 }
 
