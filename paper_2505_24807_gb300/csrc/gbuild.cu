@@ -108,7 +108,7 @@ __device__ __forceinline__ void one_centre(const T* p, int a, int b, const T Rd[
 constexpr int kGR = 4, kGC = 64, kGP = 10, kGQ = 160;
 
 template <typename T, GMode MODE>
-__global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, const int4* __restrict__ rows,
+__global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, const int4* __restrict__ rows,
                                                     const int4* __restrict__ cols, const int* __restrict__ ao_atom,
                                                     const int* __restrict__ ao_local,
                                                     const int* __restrict__ atom_ao_off,
@@ -120,9 +120,11 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
                                                     T* __restrict__ Gall, T* __restrict__ Gmall) {
   // R tiles padded by 4 rows / columns of zeros: a hydrogen's block is
   // handled as a 4 x 4 block with zero weights past its single AO
+  // double-buffered: matrix v is read from one buffer while v + 1 is stored
+  // into the other from registers loaded before the compute
   __shared__ T Ws[kGP][kGQ + 1];
-  __shared__ T Rt[kGR + 4][kGC + 4];
-  __shared__ T Rtt[kGC + 4][kGR + 4];
+  __shared__ T Rt[2][kGR + 4][kGC + 4];
+  __shared__ T Rtt[2][kGC + 4][kGR + 5];   // odd row stride: the rows of different atoms hit different banks
   const int4 rg = rows[blockIdx.y], ct = cols[blockIdx.x];
   const int ra = rg.x, nr = rg.y, cb = ct.x, nc = ct.y;
   const int PA0 = atom_prod_off[rg.z], PB0 = atom_prod_off[ct.z];
@@ -133,10 +135,8 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
     const int pr = idx / nPB, pc = idx % nPB;
     Ws[pr][pc] = W[(long long)(PA0 + pr) * np + PB0 + pc];
   }
-  for (int idx = tid; idx < (kGR + 4) * (kGC + 4); idx += blockDim.x) {
-    (&Rt[0][0])[idx] = T(0);
-    (&Rtt[0][0])[idx] = T(0);
-  }
+  for (int idx = tid; idx < 2 * (kGR + 4) * (kGC + 4); idx += blockDim.x) (&Rt[0][0][0])[idx] = T(0);
+  for (int idx = tid; idx < 2 * (kGC + 4) * (kGR + 5); idx += blockDim.x) (&Rtt[0][0][0])[idx] = T(0);
   const int ri = tid / kGC, ci = tid % kGC;
   const bool active = ri < nr && ci < nc;
   const int mu = ra + ri, lam = cb + ci;
@@ -172,22 +172,29 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
         if (nu < nA && sg < nB)
           wv[nu * 4 + sg] = Ws[pA + ((nA == 4) ? pidx(a, nu) : 0)][pB + ((nB == 4) ? pidx(b, sg) : 0)];
   }
+  const int tr = tid % kGR, tc = tid / kGR;   // transpose tile: 4 consecutive threads per row
+  const bool tact = (MODE == G_RPA) && tr < nr && tc < nc;
+  __syncthreads();
+  if (nvec > 0) {
+    if (active) Rt[0][ri][ci] = Rall[(long long)mu * n + lam];
+    if (tact) Rtt[0][tc][tr] = Rall[(long long)(cb + tc) * n + ra + tr];
+  }
+  __syncthreads();
+  int buf = 0;
   for (int v = 0; v < nvec; ++v) {
-    const T* R = Rall + (long long)v * n * n;
-    if (active) Rt[ri][ci] = R[(long long)mu * n + lam];
-    if (MODE == G_RPA) {
-      // transpose tile: consecutive threads along the (at most 4) contiguous
-      // row elements, so a warp reads 8 rows of up to 16 bytes
-      const int tr = tid % kGR, tc = tid / kGR;
-      if (tr < nr && tc < nc) Rtt[tc][tr] = R[(long long)(cb + tc) * n + ra + tr];
+    // prefetch matrix v + 1 into registers
+    T nxt = T(0), nxtt = T(0);
+    if (v + 1 < nvec) {
+      const T* Rn = Rall + (long long)(v + 1) * n * n;
+      if (active) nxt = Rn[(long long)mu * n + lam];
+      if (tact) nxtt = Rn[(long long)(cb + tc) * n + ra + tr];
     }
-    __syncthreads();
     if (active) {
       T g, gm = T(0);
       if (A == B) {
         T J1, K1ab, K1ba;
         if (nA == 1) {
-          const T r00 = Rt[rA][cA];
+          const T r00 = Rt[buf][rA][cA];
           J1 = p[4] * r00;
           K1ab = K1ba = p[4] * r00;
         } else {
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) Rd[i * 4 + j] = Rt[rA + i][cA + j];
+            for (int j = 0; j < 4; ++j) Rd[i * 4 + j] = Rt[buf][rA + i][cA + j];
           one_centre<T>(p, a, b, Rd, J1, K1ab, K1ba);
         }
         const int pab = (nA == 4) ? pidx(a, b) : 0;
@@ -214,8 +221,8 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
         for (int nu = 0; nu < 4; ++nu)
 #pragma unroll
           for (int sg = 0; sg < 4; ++sg) {
-            kr = fma(wv[nu * 4 + sg], Rt[rA + nu][rB + sg], kr);
-            if (MODE == G_RPA) krt = fma(wv[nu * 4 + sg], Rtt[rB + sg][rA + nu], krt);
+            kr = fma(wv[nu * 4 + sg], Rt[buf][rA + nu][rB + sg], kr);
+            if (MODE == G_RPA) krt = fma(wv[nu * 4 + sg], Rtt[buf][rB + sg][rA + nu], krt);
           }
         if (MODE == G_CIS) {
           g = -kr;
@@ -227,7 +234,12 @@ __global__ void __launch_bounds__(256) gtile_kernel(int n, int np, int nvec, con
       Gall[(long long)v * n * n + (long long)mu * n + lam] = g;
       if (MODE == G_RPA) Gmall[(long long)v * n * n + (long long)mu * n + lam] = gm;
     }
+    if (v + 1 < nvec) {
+      if (active) Rt[buf ^ 1][ri][ci] = nxt;
+      if (tact) Rtt[buf ^ 1][tc][tr] = nxtt;
+    }
     __syncthreads();
+    buf ^= 1;
   }
 }
 

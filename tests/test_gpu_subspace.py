@@ -121,8 +121,11 @@ def test_davidson_emulated_subspace_matches_float64_pipe(method, precision):
         m = xs.XS_TDHF if method == "TDHF" else xs.XS_CIS
         p = xs.XS_MIXED if precision == "mixed" else xs.XS_FP64
         tol = 1e-5 if precision == "mixed" else 1e-7
-        ref = xs.xs_excited(h, method=m, nroots=6, tol=tol, precision=p, subspace=xs.XS_SUBSPACE_FP64)
-        emu = xs.xs_excited(h, method=m, nroots=6, tol=tol, precision=p, subspace=xs.XS_SUBSPACE_EMULATED)
+        # the same subspace cap for both (the default depends on the subspace arithmetic)
+        ref = xs.xs_excited(h, method=m, nroots=6, tol=tol, precision=p, subspace=xs.XS_SUBSPACE_FP64,
+                            max_subspace=72)
+        emu = xs.xs_excited(h, method=m, nroots=6, tol=tol, precision=p, subspace=xs.XS_SUBSPACE_EMULATED,
+                            max_subspace=72)
         assert ref["info"]["converged"] and emu["info"]["converged"]
         # float64 products: the two solves agree to rounding; mixed products
         # carry ~1e-7 relative noise, so the two solves stop at different
