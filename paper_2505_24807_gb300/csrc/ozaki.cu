@@ -59,14 +59,25 @@ __device__ __forceinline__ void oz_digits(double x, int e, int* d) {
     const int rs = -sh;
     q = rs >= 64 ? 0ull : (((mant >> (rs - 1)) + 1ull) >> 1);
   }
-  long long r = (bits >> 63) ? -static_cast<long long>(q) : static_cast<long long>(q);
+  const long long r = (bits >> 63) ? -static_cast<long long>(q) : static_cast<long long>(q);
+  // r = hi 2^28 + lo with 0 <= lo < 2^28: four digits from lo, its carry into
+  // hi, three more digits and the remainder from hi, all in 32-bit arithmetic
+  int lo = static_cast<int>(r & 0xFFFFFFF);
+  int hi = static_cast<int>(r >> 28);
 #pragma unroll
-  for (int i = kOzDigits - 1; i >= 1; --i) {
-    const long long di = ((r + 64) & 127) - 64;
-    d[i] = static_cast<int>(di);
-    r = (r - di) >> 7;
+  for (int i = kOzDigits - 1; i >= 4; --i) {
+    const int di = ((lo + 64) & 127) - 64;
+    d[i] = di;
+    lo = (lo - di) >> 7;
   }
-  d[0] = static_cast<int>(r);
+  hi += lo;
+#pragma unroll
+  for (int i = 3; i >= 1; --i) {
+    const int di = ((hi + 64) & 127) - 64;
+    d[i] = di;
+    hi = (hi - di) >> 7;
+  }
+  d[0] = hi;
 }
 
 __device__ __forceinline__ uint32_t digit_bits(int d) {
@@ -340,18 +351,23 @@ __global__ void oz_slice_kernel(int nvec, long long L, const double* __restrict_
   }
 }
 
-// C[m][n] = alpha 2^(eA[m] + eB[n]) sum_chunk part[chunk][m][n] + beta C[m][n]
+// C[m][n] = alpha 2^(eA[m] + eB[n]) sum_chunk part[chunk][m][n] + beta C[m][n];
+// one warp per output: lane-strided partial sums, then a fixed shuffle tree
+// (the same order on every run)
 __global__ void oz_reduce_kernel(int M, int N, int nchunk, const double* __restrict__ part, const int* __restrict__ eA,
                                  const int* __restrict__ eB, double alpha, double beta, double* C, int ldc) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= M * N) return;
-  const int m = idx / N, n = idx % N;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= M * N) return;
+  const int m = w / N, n = w % N;
   double sum = 0.0;
-  for (int c = 0; c < nchunk; ++c) sum += part[(static_cast<size_t>(c) * M + m) * N + n];
-  double y = alpha * ldexp(sum, eA[m] + eB[n]);
-  double* p = C + static_cast<size_t>(m) * ldc + n;
-  if (beta != 0.0) y = fma(beta, *p, y);
-  *p = y;
+  for (int c = lane; c < nchunk; c += 32) sum += part[(static_cast<size_t>(c) * M + m) * N + n];
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) {
+    double y = alpha * ldexp(sum, eA[m] + eB[n]);
+    double* p = C + static_cast<size_t>(m) * ldc + n;
+    if (beta != 0.0) y = fma(beta, *p, y);
+    *p = y;
+  }
 }
 
 struct CoefArgs {
@@ -520,8 +536,8 @@ void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long lo
       ProfScope ps(s, "oz_gram", 2.0 * kOzDigits * static_cast<double>(L) * (M + nn), 2.0 * M * nn * (double)L);
       dispatch(s, bn, ta, ta, ta, tb, a, err);
     }
-    oz_reduce_kernel<<<grid1(static_cast<long long>(M) * nn, 256), 256, 0, s>>>(M, nn, nchunk, w.part.get(), eA,
-                                                                               eB + n0, alpha, beta, C + n0, ldc);
+    oz_reduce_kernel<<<grid1(32LL * M * nn, 256), 256, 0, s>>>(M, nn, nchunk, w.part.get(), eA, eB + n0, alpha, beta,
+                                                                C + n0, ldc);
     XS_CHECK_LAUNCH();
   }
 }

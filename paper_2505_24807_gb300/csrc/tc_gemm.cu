@@ -31,7 +31,10 @@ using namespace tc5;
 
 constexpr int BM = 128;
 constexpr int BK = 32;       // 32 tf32 = 128 bytes = one swizzle atom row
-constexpr int STAGES = 3;
+// stage ring depth: 3 stages of 64 KB for 128-wide tiles, 2 of 96 KB for
+// 256-wide tiles (which halve the A-tile re-reads per flop)
+template <int BN>
+__host__ __device__ constexpr int stages_for() { return BN >= 256 ? 2 : 3; }
 
 __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y, int z,
                                          int rank3) {
@@ -76,6 +79,7 @@ __global__ void __launch_bounds__(192, 1)
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned stage buffers (the 128-byte swizzle repeats every 1024 bytes)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int STAGES = stages_for<BN>();
   constexpr int A_BYTES = BM * BK * 4;
   constexpr int B_BYTES = BN * BK * 4;
   constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -267,6 +271,7 @@ CUtensorMap make_map(const float* ptr, int rows, int kpad, int ld, int batch, lo
 
 template <int BN>
 size_t smem_bytes() {
+  constexpr int STAGES = stages_for<BN>();
   return 1024 + STAGES * (2 * BM * BK * 4 + 2 * BN * BK * 4) + (2 * STAGES + 4) * 8 + 16;
 }
 
@@ -288,10 +293,11 @@ template void split_pad<double>(cudaStream_t, int, int, int, const double*, int,
 template void split_pad<float>(cudaStream_t, int, int, int, const float*, int, long long, long long, int, bool,
                                float*, float*);
 
-void tc_gemm(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int N, int Kpad, int batch,
-             const TcEpilogue& e, int* d_err) {
-  if (M <= 0 || N <= 0 || batch <= 0) return;
-  constexpr int BNv = 128;
+namespace {
+
+template <int BNv>
+void launch_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int N, int Kpad, int batch,
+               const TcEpilogue& e, int* d_err) {
   const CUtensorMap ah = make_map(A.hi, M, Kpad, A.ld, A.batched ? batch : 1, A.bstride, BM);
   const CUtensorMap al = make_map(A.lo, M, Kpad, A.ld, A.batched ? batch : 1, A.bstride, BM);
   const CUtensorMap bh = make_map(B.hi, N, Kpad, B.ld, B.batched ? batch : 1, B.bstride, BNv);
@@ -317,6 +323,15 @@ void tc_gemm(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int 
   tc_gemm_kernel<BNv><<<grid, 192, smem, s>>>(ah, al, bh, bl, M, N, Kpad, A.batched && batch > 1 ? 1 : 0,
                                               B.batched && batch > 1 ? 1 : 0, ntm, ntn, ntiles, ep, d_err);
   XS_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void tc_gemm(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int N, int Kpad, int batch,
+             const TcEpilogue& e, int* d_err) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (N >= 512) launch_tc<256>(s, A, B, M, N, Kpad, batch, e, d_err);
+  else launch_tc<128>(s, A, B, M, N, Kpad, batch, e, d_err);
 }
 
 }  // namespace xs
