@@ -327,27 +327,46 @@ __global__ void oz_exp_kernel(int nvec, const unsigned long long* __restrict__ m
   e[r] = (b == 0) ? 0 : ex - 1021;
 }
 
-__global__ void oz_slice_kernel(int nvec, long long L, const double* __restrict__ X, long long ldx,
-                                const int* __restrict__ e, oz_t* __restrict__ tn, long long Lp, int tn_r0,
-                                oz_t* __restrict__ nn, int ldk, int nn_r0) {
-  const long long l = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (l >= (tn ? Lp : L)) return;
-  for (int r = 0; r < nvec; ++r) {
+// One CTA per 64 consecutive amplitudes l and up to 32 vectors: digits are
+// formed with l along the threads (coalesced float64 loads and tn plane
+// stores) and staged in shared memory, then the nn rows are written with the
+// vectors along the threads, so each row's nvec x 16 bytes go out contiguously.
+constexpr int kSliceL = 64, kSliceR = 32;
+
+__global__ void __launch_bounds__(256) oz_slice_kernel(int nvec, long long L, const double* __restrict__ X,
+                                                       long long ldx, const int* __restrict__ e,
+                                                       oz_t* __restrict__ tn, long long Lp, int tn_r0,
+                                                       oz_t* __restrict__ nn, int ldk, int nn_r0) {
+  __shared__ uint4 tile[kSliceR][kSliceL];
+  const long long l0 = static_cast<long long>(blockIdx.x) * kSliceL;
+  const int r0 = blockIdx.y * kSliceR;
+  const int nr = min(kSliceR, nvec - r0);
+  for (int item = threadIdx.x; item < nr * kSliceL; item += blockDim.x) {
+    const int r = item / kSliceL, li = item % kSliceL;
+    const long long l = l0 + li;
+    const int rv = r0 + r;
     int d[kOzDigits];
     if (l < L) {
-      oz_digits(X[static_cast<size_t>(r) * ldx + l], e[r], d);
+      oz_digits(X[static_cast<size_t>(rv) * ldx + l], e[rv], d);
     } else {
 #pragma unroll
       for (int i = 0; i < kOzDigits; ++i) d[i] = 0;
     }
-    if (tn) {
+    if (tn && l < Lp) {
 #pragma unroll
       for (int i = 0; i < kOzDigits; ++i)
-        tn[(static_cast<size_t>(tn_r0 + r) * kOzDigits + i) * Lp + l] = static_cast<oz_t>(digit_bits(d[i]));
+        tn[(static_cast<size_t>(tn_r0 + rv) * kOzDigits + i) * Lp + l] = static_cast<oz_t>(digit_bits(d[i]));
     }
-    if (nn && l < L)
-      *reinterpret_cast<uint4*>(nn + static_cast<size_t>(l) * ldk + static_cast<size_t>(nn_r0 + r) * kOzDigits) =
-          pack8(d);
+    if (nn) tile[r][li] = pack8(d);
+  }
+  if (!nn) return;
+  __syncthreads();
+  for (int item = threadIdx.x; item < kSliceL * nr; item += blockDim.x) {
+    const int li = item / nr, r = item % nr;
+    const long long l = l0 + li;
+    if (l < L)
+      *reinterpret_cast<uint4*>(nn + static_cast<size_t>(l) * ldk + static_cast<size_t>(nn_r0 + r0 + r) * kOzDigits) =
+          tile[r][li];
   }
 }
 
@@ -504,7 +523,8 @@ void oz_slice(cudaStream_t s, int nvec, long long L, const double* X, long long 
   if (nn && ldk % 64) throw Error(XS_EINVAL, "oz_slice: bad nn stride");
   const long long span = tn ? Lp : L;
   ProfScope ps(s, "oz_slice", 8.0 * nvec * L + (tn ? 16.0 * nvec * Lp : 0.0) + (nn ? 16.0 * nvec * L : 0.0), 0.0);
-  oz_slice_kernel<<<grid1(span, 256), 256, 0, s>>>(nvec, L, X, ldx, e, tn, Lp, tn_r0, nn, ldk, nn_r0);
+  dim3 grid(static_cast<unsigned>((span + kSliceL - 1) / kSliceL), (nvec + kSliceR - 1) / kSliceR);
+  oz_slice_kernel<<<grid, 256, 0, s>>>(nvec, L, X, ldx, e, tn, Lp, tn_r0, nn, ldk, nn_r0);
   XS_CHECK_LAUNCH();
 }
 

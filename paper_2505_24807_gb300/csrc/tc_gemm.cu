@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* accf = empty + STAGES;   // [2]
   uint64_t* acce = accf + 2;         // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  // epilogue staging: per epilogue warp a 32 x 16 block, transposed so that
+  // global stores run along rows
+  float* stage_ep = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(acce + 2) + 16);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nk = Kpad / BK;
@@ -184,37 +187,45 @@ __global__ void __launch_bounds__(192, 1)
       const int buf = i & 1;
       if (!mbar_wait(&accf[buf], static_cast<uint32_t>((i >> 1) & 1), err, 3)) break;
       fence_after_sync();
-      const int row = m0 + lane_base + lane;
       const uint32_t trow = tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(lane_base) << 16);
+      float* st = stage_ep + (warp - 2) * 32 * 17;
+      const int c2 = lane & 15, rb = lane >> 4;
       for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
         tmem_ld16(trow + c0, v);
-        if (row >= M) continue;
-        const long long rb = (long long)bz * ep.bstride + (long long)row * ep.ld;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
+        for (int j = 0; j < 16; ++j) st[lane * 17 + j] = v[j];
+        __syncwarp();
+        const int col = n0 + c0 + c2;
+#pragma unroll 4
+        for (int k = 0; k < 16; ++k) {
+          const int r2 = rb + 2 * k;
+          const int row = m0 + lane_base + r2;
+          if (row >= M) continue;
+          const float x = st[r2 * 17 + c2];
+          const long long rbo = (long long)bz * ep.bstride + (long long)row * ep.ld;
           if (col >= N) {
             // a TF32-pair output feeds the next GEMM as a K-major operand:
             // its padding columns up to the row stride must read as zero
             if (ep.mode == 1 && col < ep.ld) {
-              ep.D[rb + col] = 0.0f;
-              ep.Dlo[rb + col] = 0.0f;
+              ep.D[rbo + col] = 0.0f;
+              ep.Dlo[rbo + col] = 0.0f;
             }
             continue;
           }
           if (ep.mode == 0) {
-            ep.D[rb + col] = v[j];
+            ep.D[rbo + col] = x;
           } else if (ep.mode == 1) {
             float h, l;
-            tf32_split(v[j], h, l);
-            ep.D[rb + col] = h;
-            ep.Dlo[rb + col] = l;
+            tf32_split(x, h, l);
+            ep.D[rbo + col] = h;
+            ep.Dlo[rbo + col] = l;
           } else {
             const double de = ep.eps[ep.o + col] - ep.eps[row];
-            ep.Y[rb + col] = static_cast<double>(v[j]) + de * ep.X[rb + col];
+            ep.Y[rbo + col] = static_cast<double>(x) + de * ep.X[rbo + col];
           }
         }
+        __syncwarp();
       }
       fence_before_sync();
       mbar_arrive(&acce[buf]);
@@ -272,7 +283,7 @@ CUtensorMap make_map(const float* ptr, int rows, int kpad, int ld, int batch, lo
 template <int BN>
 size_t smem_bytes() {
   constexpr int STAGES = stages_for<BN>();
-  return 1024 + STAGES * (2 * BM * BK * 4 + 2 * BN * BK * 4) + (2 * STAGES + 4) * 8 + 16;
+  return 1024 + STAGES * (2 * BM * BK * 4 + 2 * BN * BK * 4) + (2 * STAGES + 4) * 8 + 16 + 4 * 32 * 17 * 4;
 }
 
 }  // namespace
