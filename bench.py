@@ -36,9 +36,9 @@ WORKLOADS = {
                    desc="TDHF, seeded chain of 100 C/N/O + 200 H atoms, 600 AOs, 10 roots"),
     "batch": dict(method="CIS", nroots=6, tol=1e-5, n_mol=256,
                   desc="CIS, 256 seeded molecules of 20-200 atoms (40% heavy), 6 roots each, batched"),
-    "learned": dict(method="TDHF", nroots=8, tol=1e-5, n_train=256, n_test=64,
-                    desc="TDHF, 8 roots; MLP guess trained on 256 seeded molecules of 20-120 atoms, "
-                         "evaluated on 64 held-out molecules of 20-300 atoms, batched"),
+    "learned": dict(method="TDHF", nroots=8, tol=1e-5, n_train=256, n_test=512,
+                    desc="TDHF, 8 roots; MLP guess (the committed network, trained on seeded molecules of "
+                         "20-120 atoms) evaluated on 512 held-out molecules of 20-300 atoms, batched"),
 }
 METRIC = "TDHF roots/s @1e-5 eV"
 
@@ -166,15 +166,29 @@ def cpu_sample(wl, seconds_budget=20.0):
     return per_vector, n, t_ints
 
 
+def oracle_products(workload, method):
+    """Trial-vector count of the oracle's own Davidson run stored in
+    tests/golden (written by the oracle only): this workload's if stored, else
+    the medium molecule's."""
+    for name in (workload, "medium"):
+        path = os.path.join(ROOT, "tests", "golden", f"{name}.json")
+        if os.path.exists(path):
+            with open(path) as f:
+                g = json.load(f)
+            if method in g.get("roots", {}):
+                return int(g["roots"][method]["products"]), f"oracle Davidson product count, {name} molecule"
+    return 200, "no stored oracle run: 200 products"
+
+
 def run_reference(args, wl):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    # each step: the oracle's products for the number of trial vectors a solve of
-    # this workload needs (taken from the oracle's own medium-size Davidson count
-    # scaled by root count is not available here, so a fixed 200-vector solve)
+    # each step: the oracle's products for the number of trial vectors the
+    # oracle's own Davidson needs on this workload (its stored run of the same
+    # molecule and method, else of the medium molecule), timed on a sample
     per_vector, n, _ = cpu_sample(wl, seconds_budget=max(5.0, 20.0 / max(args.steps, 1)))
-    products_per_solve = 200
+    products_per_solve, source = oracle_products(args.workload, "RPA" if wl["method"] == "TDHF" else "CIS")
     step_s = per_vector * products_per_solve
     value = wl["nroots"] / step_s
     line = dict(impl="reference", metric=METRIC, value=value, unit="roots/s", n_gpus=args.gpus, steps=args.steps,
@@ -184,7 +198,7 @@ def run_reference(args, wl):
                 cpu_baseline=dict(kind="oracle", value=value, unit="roots/s", cores=os.cpu_count(),
                                   sample=f"{n} oracle (A+B)X,(A-B)X products on the {args.workload} molecule "
                                          f"(seeded orbitals), {per_vector:.3f} s each, x{products_per_solve} "
-                                         f"products per solve"),
+                                         f"products per solve ({source})"),
                 e2e=dict(value=value, unit="roots/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -216,6 +230,15 @@ def run_many(args, wl):
     if args.workload == "batch":
         mols = [molgen.config_batch(s) for s in range(wl["n_mol"])]
         guess = xs.XS_GUESS_PLAIN
+    elif os.path.exists(os.path.join(ROOT, "paper_2505_24807_gb300", "guess_weights.f32")):
+        # the committed network (paper_2505_24807_gb300/train_guess.py), seeds disjoint from the test set
+        base = os.path.join(ROOT, "paper_2505_24807_gb300", "guess_weights")
+        xs.xs_mlp_set_weights(ctx, np.fromfile(base + ".f32", dtype=np.float32))
+        if os.path.exists(base + ".json"):
+            with open(base + ".json") as f:
+                extra["training"] = json.load(f)
+        mols = [molgen.config_sized(9000 + s, 20 + (s * 4099) % 281) for s in range(wl["n_test"])]
+        guess = xs.XS_GUESS_LEARNED
     else:
         train = [molgen.config_sized(1000 + s, 20 + (s * 7919) % 101) for s in range(wl["n_train"])]
         mols = [molgen.config_sized(9000 + s, 20 + (s * 4099) % 281) for s in range(wl["n_test"])]

@@ -1,12 +1,13 @@
 """Trains the learned Davidson guess/preconditioner network on the GPU and
 writes its weights (float32, xs_mlp_nparams() values) to a file.
 
-Training data: seeded molecules of 20-120 atoms (molgen.config_sized), their
-ground states and TDHF roots from libxs itself, pair features and targets
-from xs_mlp_features / xs_mlp_targets; the network is trained by libxs's
-own kernels (xs_mlp_train).
+Training data: seeded molecules of 20-120 atoms (molgen.config_sized, seeds
+1000 + s), their ground states and TDHF roots from libxs itself, pair features
+and targets from xs_mlp_features / xs_mlp_targets; the network is trained by
+libxs's own kernels (xs_mlp_train).  The training record goes to a JSON file
+beside the weights (same name, .json).
 
-  python -m paper_2505_24807_gb300.train_guess --molecules 256 --out weights.f32
+  python -m paper_2505_24807_gb300.train_guess --molecules 4096 --epochs 20 --out guess_weights.f32
 """
 from __future__ import annotations
 
@@ -47,7 +48,8 @@ def train(n_mol=256, nroots=8, pairs=2048, epochs=60, seed=1, ctx=None):
     xs.xs_mlp_init(ctx, seed=seed)
     loss = xs.xs_mlp_train(ctx, F[perm], T[perm], epochs=epochs, batch=4096, lr=2e-3)
     w = xs.xs_mlp_get_weights(ctx)
-    info = dict(molecules=n_mol, samples=int(len(F)), epochs=epochs, loss_first=float(loss[0]),
+    info = dict(molecules=n_mol, atoms="20-120", molecule_seeds=f"1000..{1000 + n_mol - 1}", nroots=nroots,
+                pairs_per_molecule=pairs, samples=int(len(F)), epochs=epochs, loss_first=float(loss[0]),
                 loss_last=float(loss[-1]), seconds=time.perf_counter() - t0)
     if own:
         xs.xs_destroy(ctx)
@@ -62,6 +64,8 @@ def main():
     args = ap.parse_args()
     w, info = train(args.molecules, epochs=args.epochs)
     w.astype(np.float32).tofile(args.out)
+    with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
+        json.dump(info, f, indent=1)
     print(json.dumps(info))
 
 
