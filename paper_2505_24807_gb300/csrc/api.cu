@@ -262,10 +262,12 @@ int xs_apply(xs_ctx* ctx, int mol, int kind, int nvec, const double* in, double*
       copy_any(s, X.get(), in, sizeof(double) * nvec * ov);
       if (kind == XS_KIND_A) {
         xs::products(c, m, XS_CIS, precision, nvec, X.get(), Y1.get(), nullptr);
+        xs::check_device_error(c);
         copy_any(s, out, Y1.get(), sizeof(double) * nvec * ov);
       } else {
         Y2.alloc((size_t)nvec * ov);
         xs::products(c, m, XS_TDHF, precision, nvec, X.get(), Y1.get(), Y2.get());
+        xs::check_device_error(c);
         copy_any(s, out, (kind == XS_KIND_APB ? Y1 : Y2).get(), sizeof(double) * nvec * ov);
       }
     } else {

@@ -107,6 +107,7 @@ struct Ctx {
   DevBuf<float> fs0, fs1, fs2;
   Profiler prof;
   DevBuf<int> tc_err;   // error word of the tensor-core kernels' bounded waits
+  std::shared_ptr<void> dav_cache;  // Davidson workspace kept between solves (davidson.cu)
   // batched solves: worker contexts (own stream and scratch), reused across calls
   std::vector<std::unique_ptr<Ctx>> workers;
   // learned guess / preconditioner network (shared by the workers)

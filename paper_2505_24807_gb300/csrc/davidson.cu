@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <numeric>
 #include <vector>
 
@@ -133,18 +134,35 @@ void sync_copy(cudaStream_t s, void* dst, const void* src, size_t bytes) {
   XS_CUDA(cudaStreamSynchronize(s));
 }
 
+// Page-locked host staging for the once-per-iteration read-back of the Ritz
+// values, residual norms and status words (one stream synchronisation per
+// iteration instead of one per value).
+struct HostStage {
+  double* p = nullptr;
+  size_t n = 0;
+  explicit HostStage(size_t count) : n(count) { XS_CUDA(cudaMallocHost(&p, sizeof(double) * count)); }
+  ~HostStage() { if (p) cudaFreeHost(p); }
+  HostStage(const HostStage&) = delete;
+  HostStage& operator=(const HostStage&) = delete;
+};
+
+// nrm2[r] = 1 / nrm[r] (0 for a zero row)
+__global__ void inv_norms_kernel(int n, const double* __restrict__ nrm, double* __restrict__ inv) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) inv[r] = nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0;
+}
+
 // Orthonormalise the nnew rows of T against V[0:S] (classical Gram-Schmidt,
 // repeated when the first pass cancels much of a row) and among themselves (Loewdin, dropping directions whose Gram
 // eigenvalue is below kLowdinThresh); writes the kept rows to V[S:].
 int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double* Vout) {
   cudaStream_t s = c.stream;
-  // unit rows first
+  // unit rows first (on the device: no host round trip)
   row_norms(s, nnew, ov, w.T.get(), w.nrm.get());
-  std::vector<double> h(nnew);
-  sync_copy(s, h.data(), w.nrm.get(), sizeof(double) * nnew);
-  for (auto& x : h) x = (x > 0.0) ? 1.0 / x : 0.0;
-  XS_CUDA(cudaMemcpyAsync(w.nrm2.get(), h.data(), sizeof(double) * nnew, cudaMemcpyHostToDevice, s));
+  inv_norms_kernel<<<grid1(nnew, 64), 64, 0, s>>>(nnew, w.nrm.get(), w.nrm2.get());
+  XS_CHECK_LAUNCH();
   scale_rows(s, nnew, ov, w.T.get(), w.nrm2.get());
+  std::vector<double> h(nnew);
   for (int pass = 0; pass < 2 && S > 0; ++pass) {
     if (w.oz) {
       slice_T(c, w, ov, w.T.get(), nnew);
@@ -315,66 +333,97 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   // residual, are still converged far below 1e-5 eV at a 1e-4 eV residual.
   const double tol_eff = (opt.precision == XS_MIXED) ? std::max(opt.tol, kMixedResidualFloor) : opt.tol;
 
-  Work w;
-  w.V.alloc((size_t)Smax * ov);
-  w.S1.alloc((size_t)Smax * ov);
-  if (rpa) w.S2.alloc((size_t)Smax * ov);
-  w.a1.alloc((size_t)Smax * Smax);
-  if (rpa) w.a2.alloc((size_t)Smax * Smax);
+  // the workspace persists in the context between solves (buffers only grow):
+  // repeated solves of similar molecules allocate nothing
+  if (!c.dav_cache) c.dav_cache = std::shared_ptr<void>(new Work(), [](void* p) { delete static_cast<Work*>(p); });
+  Work& w = *static_cast<Work*>(c.dav_cache.get());
+  w.V.ensure((size_t)Smax * ov);
+  w.S1.ensure((size_t)Smax * ov);
+  if (rpa) w.S2.ensure((size_t)Smax * ov);
+  w.a1.ensure((size_t)Smax * Smax);
+  if (rpa) w.a2.ensure((size_t)Smax * Smax);
   // small matrices: S x S subspace work and up to 2k x 2k blocks (tiny molecules can have Smax < 2k)
   const size_t SB = (size_t)std::max(Smax, 2 * kk + 2);
   const size_t SS = SB * SB;
-  w.E.alloc(SS); w.Q.alloc(SS); w.w.alloc(SB); w.Sh.alloc(SS);
-  w.tS.alloc(SS);
-  w.E2.alloc(SS); w.Q2.alloc(SS); w.w2.alloc(SB);
-  w.cu.alloc((size_t)Smax * 2 * kk); w.cw.alloc((size_t)Smax * kk);
-  w.X.alloc((size_t)2 * kk * ov); w.R1.alloc((size_t)(rpa ? 2 : 1) * kk * ov);
+  w.E.ensure(SS); w.Q.ensure(SS); w.w.ensure(SB); w.Sh.ensure(SS);
+  w.tS.ensure(SS);
+  w.E2.ensure(SS); w.Q2.ensure(SS); w.w2.ensure(SB);
+  w.cu.ensure((size_t)Smax * 2 * kk); w.cw.ensure((size_t)Smax * kk);
+  w.X.ensure((size_t)2 * kk * ov); w.R1.ensure((size_t)(rpa ? 2 : 1) * kk * ov);
   w.AX = w.X.get() + (size_t)kk * ov;
-  w.T.alloc((size_t)maxnew * ov);
-  if (rpa) w.MW.alloc((size_t)kk * ov);
+  w.T.ensure((size_t)maxnew * ov);
+  if (rpa) w.MW.ensure((size_t)kk * ov);
   // residual rows: R1 (CIS: A X - omega X; TDHF: r1), R2 (TDHF: r2)
   double* R1p = w.R1.get();
   double* R2p = rpa ? w.R1.get() + (size_t)kk * ov : nullptr;
   w.oz = use_oz;
   if (w.oz) {
     if (!c.tc_err.get()) {
-      c.tc_err.alloc(1);
+      c.tc_err.ensure(1);
       XS_CUDA(cudaMemsetAsync(c.tc_err.get(), 0, sizeof(int), s));
     }
     w.Lp = oz_lp(ov);
     w.ldk = oz_ldk(Smax);
     w.bcap = std::max(maxnew, std::max(nguess, 2 * kk));
-    w.Vtn.alloc((size_t)Smax * kOzDigits * w.Lp);
-    w.Btn.alloc((size_t)w.bcap * kOzDigits * w.Lp);
+    w.Vtn.ensure((size_t)Smax * kOzDigits * w.Lp);
+    w.Btn.ensure((size_t)w.bcap * kOzDigits * w.Lp);
     w.ldkT = oz_ldk(w.bcap);
-    w.Tnn.alloc((size_t)ov * w.ldkT);
-    XS_CUDA(cudaMemsetAsync(w.Tnn.get(), 0, sizeof(oz_t) * ov * w.ldkT, s));
-    // combination operands: digit columns past S * 8 are read (times zero
-    // coefficients) and must hold finite values
-    w.Vnn.alloc((size_t)ov * w.ldk);
-    w.S1nn.alloc((size_t)ov * w.ldk);
-    XS_CUDA(cudaMemsetAsync(w.Vnn.get(), 0, sizeof(oz_t) * ov * w.ldk, s));
-    XS_CUDA(cudaMemsetAsync(w.S1nn.get(), 0, sizeof(oz_t) * ov * w.ldk, s));
-    if (rpa) {
-      w.S2nn.alloc((size_t)ov * w.ldk);
-      XS_CUDA(cudaMemsetAsync(w.S2nn.get(), 0, sizeof(oz_t) * ov * w.ldk, s));
-    }
-    w.eV.alloc(Smax); w.eS1.alloc(Smax); w.eS2.alloc(Smax); w.eB.alloc(w.bcap);
-    w.coef.alloc((size_t)4 * Smax * 2 * kk);
+    // digit rows past the live vectors are read (times zero coefficients) and
+    // must be finite: zero them when (re)allocated; later contents are digits
+    auto ensure_zeroed = [&](DevBuf<oz_t>& b, size_t count) {
+      const oz_t* before = b.get();
+      b.ensure(count);
+      if (b.get() != before) XS_CUDA(cudaMemsetAsync(b.get(), 0, sizeof(oz_t) * b.n, s));
+    };
+    ensure_zeroed(w.Tnn, (size_t)ov * w.ldkT);
+    ensure_zeroed(w.Vnn, (size_t)ov * w.ldk);
+    ensure_zeroed(w.S1nn, (size_t)ov * w.ldk);
+    if (rpa) ensure_zeroed(w.S2nn, (size_t)ov * w.ldk);
+    w.eV.ensure(Smax); w.eS1.ensure(Smax); w.eS2.ensure(Smax); w.eB.ensure(w.bcap);
+    w.coef.ensure((size_t)4 * Smax * 2 * kk);
   }
-  w.nrm.alloc(2 * kk + 2); w.nrm2.alloc(2 * kk + 2); w.omega.alloc(kk); w.Bm.alloc(4 * kk * kk + 4);
-  w.flag.alloc(4);
+  w.nrm.ensure(2 * kk + 2); w.nrm2.ensure(2 * kk + 2); w.omega.ensure(kk); w.Bm.ensure(4 * kk * kk + 4);
+  w.flag.ensure(4);
   XS_CUDA(cudaMemsetAsync(w.flag.get(), 0, 4 * sizeof(int), s));
 
-  auto t_prod = clk::duration::zero();
   int prod_prec = opt.precision;
+  std::vector<double> hw(kk), hn(2 * kk);
+  // products timed by CUDA events on the stream (read once at the end)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prod_events;
+  struct EventsGuard {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& ev;
+    ~EventsGuard() {
+      for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    }
+  } events_guard{prod_events};
   auto apply = [&](int first, int count) {
-    auto t0 = clk::now();
+    cudaEvent_t e0, e1;
+    XS_CUDA(cudaEventCreate(&e0));
+    XS_CUDA(cudaEventCreate(&e1));
+    prod_events.emplace_back(e0, e1);
+    XS_CUDA(cudaEventRecord(e0, s));
     products(c, m, opt.method, prod_prec, count, w.V.get() + first * ov, w.S1.get() + first * ov,
              rpa ? w.S2.get() + first * ov : nullptr);
-    XS_CUDA(cudaStreamSynchronize(s));
-    t_prod += clk::now() - t0;
+    XS_CUDA(cudaEventRecord(e1, s));
     st.products += count;
+  };
+  HostStage hs(3 * (size_t)kk + 8);
+  // read back omega (k), residual norms (nn) and the status words in one synchronisation
+  auto fetch = [&](int k, int nn) {
+    XS_CUDA(cudaMemcpyAsync(hs.p, w.omega.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    XS_CUDA(cudaMemcpyAsync(hs.p + kk, w.nrm.get(), sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+    XS_CUDA(cudaMemcpyAsync(hs.p + 3 * kk, w.flag.get() + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (c.tc_err.get())
+      XS_CUDA(cudaMemcpyAsync(hs.p + 3 * kk + 1, c.tc_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    else
+      std::memset(hs.p + 3 * kk + 1, 0, sizeof(double));
+    XS_CUDA(cudaStreamSynchronize(s));
+    std::copy(hs.p, hs.p + k, hw.begin());
+    std::copy(hs.p + kk, hs.p + kk + nn, hn.begin());
+    int flag3 = 0, tcerr = 0;
+    std::memcpy(&flag3, hs.p + 3 * kk, sizeof(int));
+    std::memcpy(&tcerr, hs.p + 3 * kk + 1, sizeof(int));
+    return std::make_pair(flag3, tcerr);
   };
 
   // learned guess and diagonal shift: MLP outputs on the lowest-gap pairs
@@ -416,7 +465,6 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   slice_V(c, w, ov, 0, S);
   apply(0, S);
 
-  std::vector<double> hw(kk), hn(2 * kk), hn2(kk);
   std::vector<char> conv(kk, 0);
   int it = 0, kq = 1;
   bool converged = false, polishing = false;
@@ -463,16 +511,16 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
                      static_cast<int>(ov), 0, 0.0, w.AX, static_cast<int>(ov), 0, 1);
         residual_norms(s, k, ov, w.AX, w.X.get(), w.omega.get(), w.nrm.get(), R1p);
       }
-      sync_copy(s, hw.data(), w.omega.get(), sizeof(double) * k);
-      sync_copy(s, hn.data(), w.nrm.get(), sizeof(double) * k);
+      const auto st_words = fetch(k, k);
+      if (st_words.second) check_device_error(c);
     } else {
       // a- = L L^T (Cholesky; failure = unstable reference), M = L^T a+ L
       XS_CUDA(cudaMemsetAsync(w.flag.get() + 3, 0, sizeof(int), s));
       sym_upper(s, S, w.a2.get(), Smax, w.Sh.get(), S);   // Sh <- a-, factored in place into L
+      // a non-positive pivot (unstable reference) is read back with the
+      // residual norms below; the launches in between run on whatever the
+      // factor holds and their results are discarded
       cholesky(s, S, w.Sh.get(), S, w.flag.get() + 3);
-      int notpd = 0;
-      sync_copy(s, &notpd, w.flag.get() + 3, sizeof(int));
-      if (notpd) { status = XS_EUNSTABLE; break; }
       sym_upper(s, S, w.a1.get(), Smax, w.E2.get(), S);   // E2 = a+
       gemm<double>(s, true, false, S, S, S, 1.0, w.Sh.get(), S, 0, w.E2.get(), S, 0, 0.0, w.tS.get(), S, 0, 1);
       gemm<double>(s, false, false, S, S, S, 1.0, w.tS.get(), S, 0, w.Sh.get(), S, 0, 0.0, w.E.get(), S, 0, 1);
@@ -522,11 +570,14 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       residual_norms(s, k, ov, R1p, w.AX, w.omega.get(), w.nrm.get(), R1p);
       residual_norms(s, k, ov, w.MW.get(), w.X.get(), w.omega.get(), w.nrm.get() + kk, R2p);
       }
-      int bad = 0;
-      sync_copy(s, &bad, w.flag.get() + 3, sizeof(int));
-      if (bad) { status = XS_EUNSTABLE; break; }
-      sync_copy(s, hw.data(), w.omega.get(), sizeof(double) * k);
-      sync_copy(s, hn.data(), w.nrm.get(), sizeof(double) * 2 * kk);
+      const auto st_words = fetch(k, 2 * kk);
+      if (st_words.first) {
+        // unstable reference: later launches saw a garbage factor; drop their error word
+        if (c.tc_err.get()) XS_CUDA(cudaMemsetAsync(c.tc_err.get(), 0, sizeof(int), s));
+        status = XS_EUNSTABLE;
+        break;
+      }
+      if (st_words.second) check_device_error(c);
       for (int j = 0; j < k; ++j) hn[j] = std::max(hn[j], hn[kk + j]);
     }
     bool all = true;
@@ -670,11 +721,18 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     Sold = S;
     S += nkeep;
     apply(Sold, nkeep);
-    if (w.oz) check_device_error(c);
-    XS_CUDA(cudaStreamSynchronize(s));
   }
+  check_device_error(c);
   st.iterations = std::min(it, max_iter);
-  st.seconds_products = std::chrono::duration<double>(t_prod).count();
+  {
+    XS_CUDA(cudaStreamSynchronize(s));
+    double ms_total = 0.0;
+    for (auto& e : prod_events) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) ms_total += ms;
+    }
+    st.seconds_products = ms_total / 1e3;
+  }
   if (status != XS_OK) return status;
 
   // keep the roots: U = X+Y (CIS: X), W = X-Y (CIS: X)

@@ -9,6 +9,10 @@
 // shapes, from 64x64 for square problems to 8x512 (Ritz vectors and
 // Gram-Schmidt updates: M = roots) and 256x8 (split-K Gram products: N = new
 // vectors); the one that pads the problem least is launched.
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
 #include "kernels.h"
 #include "prof.h"
 
@@ -331,7 +335,85 @@ void launch_gemm(cudaStream_t s, int sh, int M, int N, int K, T alpha, const T* 
 #undef XS_GEMM_CASE
 }
 
+// ---- tile-shape autotuner ----------------------------------------------------
+// The first time a problem class is met -- element type, transposes, batch > 1
+// and M, N, K rounded up to powers of two -- every tile shape whose padded
+// area is within 1.5x of the least is timed on a scratch output (one warm-up
+// launch, then two timed with CUDA events on the caller's stream) and the
+// fastest is kept for the process.  Classes whose output exceeds 8M elements,
+// calls inside stream capture and calls from allocation-free entry points use
+// the least-padding rule directly.
+thread_local int g_no_tune = 0;
+
+int ceil_log2(long long x) {
+  int l = 0;
+  while ((1LL << l) < x) ++l;
+  return l;
+}
+
+std::mutex g_tune_mutex;
+std::unordered_map<unsigned long long, int> g_tuned;
+
+template <typename T>
+int tuned_shape(cudaStream_t s, bool tA, bool tB, int M, int N, int K, const T* A, int lda, long long sA,
+                const T* B, int ldb, long long sB, int batch) {
+  const int heuristic = pick_shape(M, N);
+  if (g_no_tune || (long long)M * N * batch > (8LL << 20)) return heuristic;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return heuristic;
+  const unsigned long long key = (unsigned long long)(sizeof(T) == 8) | ((unsigned long long)tA << 1) |
+                                 ((unsigned long long)tB << 2) | ((unsigned long long)(batch > 1) << 3) |
+                                 ((unsigned long long)ceil_log2(M) << 8) | ((unsigned long long)ceil_log2(N) << 16) |
+                                 ((unsigned long long)ceil_log2(K) << 24);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  const auto area = [&](int sh) {
+    return (double)((M + kShapes[sh].bm - 1) / kShapes[sh].bm) * kShapes[sh].bm *
+           (double)((N + kShapes[sh].bn - 1) / kShapes[sh].bn) * kShapes[sh].bn;
+  };
+  const double amin = area(heuristic);
+  T* Cs = nullptr;
+  if (cudaMalloc(&Cs, sizeof(T) * (size_t)M * N * batch) != cudaSuccess) {
+    cudaGetLastError();
+    return heuristic;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = heuristic;
+  float best_ms = 1e30f;
+  for (int sh = 0; sh < kNumShapes; ++sh) {
+    if (area(sh) > 1.5 * amin) continue;
+    launch_gemm<T>(s, sh, M, N, K, T(1), A, lda, sA, tA, B, ldb, sB, tB, T(0), Cs, N, (long long)M * N, batch, 1, 0);
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 2; ++r)
+      launch_gemm<T>(s, sh, M, N, K, T(1), A, lda, sA, tA, B, ldb, sB, tB, T(0), Cs, N, (long long)M * N, batch, 1,
+                     0);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = sh;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(Cs);
+  XS_CHECK_LAUNCH();
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned[key] = best;
+  return best;
+}
+
 }  // namespace
+
+NoTuneScope::NoTuneScope() { ++g_no_tune; }
+NoTuneScope::~NoTuneScope() { --g_no_tune; }
 
 template <typename T>
 void gemm(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha, const T* A, int lda, long long sA,
@@ -346,8 +428,8 @@ void gemm(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha
     XS_CHECK_LAUNCH();
     return;
   }
-  launch_gemm<T>(s, pick_shape(M, N), M, N, K, alpha, A, lda, sA, transA, B, ldb, sB, transB, beta, C, ldc, sC, batch,
-                 1, 0);
+  const int sh = tuned_shape<T>(s, transA, transB, M, N, K, A, lda, sA, B, ldb, sB, batch);
+  launch_gemm<T>(s, sh, M, N, K, alpha, A, lda, sA, transA, B, ldb, sB, transB, beta, C, ldc, sC, batch, 1, 0);
   XS_CHECK_LAUNCH();
 }
 

@@ -15,6 +15,14 @@ void gemm(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha
           int lda, long long sA, const T* B, int ldb, long long sB, T beta, T* C, int ldc,
           long long sC, int batch = 1);
 
+// While alive on a thread, GEMM calls skip the tile-shape autotuner (which
+// allocates a scratch output and synchronises the stream on a new problem
+// class): for allocation-free entry points.
+struct NoTuneScope {
+  NoTuneScope();
+  ~NoTuneScope();
+};
+
 // C (M x N) = alpha A (M x L) B(N x L)^T + beta C for long L (split over L).
 template <typename T>
 void gram(cudaStream_t s, int M, int N, int L, const T* A, int lda, const T* B, int ldb, T* C,

@@ -66,6 +66,7 @@ extern "C" int xs_gbuild_noalloc(xs_ctx* ctx, int mol, int nvec, const double* R
     if (!R || !G || !is_device_pointer(R) || !is_device_pointer(G))
       throw xs::Error(XS_EINVAL, "xs_gbuild_noalloc: R and G must be device pointers");
     double* scratch = noalloc_scratch(c.device);
+    xs::NoTuneScope no_tune;
     xs::gbuild_raw<double>(c.stream, m, c.d_par.get(), xs::G_CIS, nvec, R, G, nullptr, scratch,
                            scratch + static_cast<size_t>(m.np) * nvec);
     return XS_OK;
