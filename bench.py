@@ -285,10 +285,11 @@ def run_many(args, wl):
                                     mean_iterations=float(np.mean(plain["iters"])),
                                     max_abs_domega_vs_learned_eV=float(np.abs(plain["omega"] - res["omega"]).max()))
         extra["learned_guess"] = dict(mean_iterations=float(np.mean(res["iters"])), fallback=res["info"]["fallback"])
-    r64, s64 = timed(torch, stream, lambda: solve(g=xs.XS_GUESS_PLAIN, prec=xs.XS_FP64))
-    extra["fp64_gpu"] = dict(value=nm * K / s64, unit="roots/s", seconds=s64,
-                             max_abs_domega_vs_chosen_eV=float(np.abs(r64["omega"] - res["omega"]).max()),
-                             speedup_of_chosen_form=value / (nm * K / s64))
+    if not args.no_fp64_baseline:
+        r64, s64 = timed(torch, stream, lambda: solve(g=xs.XS_GUESS_PLAIN, prec=xs.XS_FP64))
+        extra["fp64_gpu"] = dict(value=nm * K / s64, unit="roots/s", seconds=s64,
+                                 max_abs_domega_vs_chosen_eV=float(np.abs(r64["omega"] - res["omega"]).max()),
+                                 speedup_of_chosen_form=value / (nm * K / s64))
     line = dict(metric=METRIC.replace("TDHF", wl["method"]), value=value, unit="roots/s", n_gpus=1,
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * sec / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32+f64", data="synthetic",
@@ -426,7 +427,11 @@ def main():
 
     # roofline of the dominant kernel, from the library's CUDA-event profile
     pk = peaks()
-    kernels = {k: v for k, v in prof.items() if k != "all_launches" and v["launches"] > 0}
+    kernels = {k: v for k, v in prof.items()
+               if k != "all_launches" and not k.startswith("host:") and v["launches"] > 0}
+    # host wall time of the solver's phases (setup, iteration loop, time spent
+    # waiting for the device at the per-iteration read-back), per step
+    host_phases = {k[5:]: round(v["ms"] / args.steps, 2) for k, v in prof.items() if k.startswith("host:")}
     top_name = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
     roof = kernel_roofline(top_name, kernels[top_name], pk) if top_name else None
     # the A.X product itself: its transforms (tensor cores) and G build (HBM)
@@ -466,7 +471,8 @@ def main():
                     iterations=int(last["info"]["iterations"]), products=int(last["info"]["products"]),
                     converged=int(last["info"]["converged"]),
                     max_abs_err_vs_oracle_eV=oracle_err,
-                    roofline=roof, ax_product=ax, kernels=kernel_table, cpu_baseline=cpu, e2e=e2e,
+                    roofline=roof, ax_product=ax, kernels=kernel_table, host_ms_per_step=host_phases,
+                    cpu_baseline=cpu, e2e=e2e,
                     gpu_launches=int(prof.get("all_launches", {}).get("launches", 0)),
                     clocks=clk, fp64_gpu=fp64)
         print(json.dumps(line), flush=True)

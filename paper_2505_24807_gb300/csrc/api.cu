@@ -455,7 +455,8 @@ int xs_mlp_features(xs_ctx* ctx, int mol, int npairs, float* features, long long
     std::vector<long long> pr = xs::lowest_gap_pairs(c, m, npairs);
     DevBuf<float> F(pr.size() * xs::kMlpFeatures);
     DevBuf<long long> dp;
-    xs::pair_features(c, m, pr, F.get(), dp);
+    xs::FeatureWork fw;
+    xs::pair_features(c, m, pr, F.get(), dp, fw);
     copy_any(c.stream, features, F.get(), sizeof(float) * F.n);
     if (pairs) copy_any(c.stream, pairs, pr.data(), sizeof(long long) * pr.size());
     XS_CUDA(cudaStreamSynchronize(c.stream));

@@ -40,6 +40,9 @@ constexpr double kMixedResidualFloor = 1e-4;
 // mixed solves of at least this many amplitudes run the float64 subspace
 // products on the tensor cores (exact digit splitting)
 constexpr long long kOzMinLength = 32768;
+// learned guess: candidate pairs (the lowest orbital-energy gaps) that the
+// network scores; its preconditioner shift covers these pairs
+constexpr long long kLearnedPairs = 16384;
 
 struct Work {
   DevBuf<double> V, S1, S2;        // Smax x ov
@@ -64,6 +67,29 @@ struct Work {
   DevBuf<int> eV, eS1, eS2, eB;
   DevBuf<double> coef;
   OzWork ozw;
+  // learned guess: features, network activations, predicted shift
+  FeatureWork fw;
+  DevBuf<float> F;
+  DevBuf<long long> dpairs;
+  std::vector<DevBuf<float>> Z, H;
+  DevBuf<double> lshift, dsh, fdev;
+  // page-locked host staging of the per-iteration read-back
+  double* hpin = nullptr;
+  size_t hpin_n = 0;
+  double* host_stage(size_t count) {
+    if (count > hpin_n) {
+      if (hpin) cudaFreeHost(hpin);
+      hpin = nullptr;
+      hpin_n = 0;
+      XS_CUDA(cudaMallocHost(&hpin, sizeof(double) * count));
+      hpin_n = count;
+    }
+    return hpin;
+  }
+  Work() = default;
+  Work(const Work&) = delete;
+  Work& operator=(const Work&) = delete;
+  ~Work() { if (hpin) cudaFreeHost(hpin); }
 };
 
 // digits of V rows [first, first + count) in both layouts
@@ -75,20 +101,21 @@ void slice_V(Ctx& c, Work& w, long long ov, int first, int count) {
 }
 
 // digits of product rows [first, first + count) (S1 or S2): nn layout, and the
-// tn layout into the scratch operand Btn when with_tn
+// tn layout into rows tn_r0.. of the scratch operand Btn when with_tn
 void slice_P(Ctx& c, Work& w, long long ov, const double* P, DevBuf<int>& e, DevBuf<oz_t>& nn, int first, int count,
-             bool with_tn) {
+             bool with_tn, int tn_r0 = 0) {
   if (!w.oz || count <= 0) return;
-  if (with_tn && count > w.bcap) throw Error(XS_EINVAL, "subspace scratch operand too small");
+  if (with_tn && tn_r0 + count > w.bcap) throw Error(XS_EINVAL, "subspace scratch operand too small");
   const double* X = P + (size_t)first * ov;
   oz_exponents(c.stream, count, ov, X, ov, e.get() + first, w.ozw, c.tc_err.get());
-  oz_slice(c.stream, count, ov, X, ov, e.get() + first, with_tn ? w.Btn.get() : nullptr, w.Lp, 0, nn.get(), w.ldk,
-           first);
+  oz_slice(c.stream, count, ov, X, ov, e.get() + first, with_tn ? w.Btn.get() : nullptr, w.Lp, tn_r0, nn.get(),
+           w.ldk, first);
 }
 
 // digits of count scratch rows T into Btn (exponents eB), and into Tnn when with_nn
 void slice_T(Ctx& c, Work& w, long long ov, const double* T, int count, bool with_nn = false) {
-  if (count > w.bcap) throw Error(XS_EINVAL, "subspace scratch operand too small");
+  if (count > w.bcap || (with_nn && count * kOzDigits > w.ldkT))
+    throw Error(XS_EINVAL, "subspace scratch operand too small");
   oz_exponents(c.stream, count, ov, T, ov, w.eB.get(), w.ozw, c.tc_err.get());
   oz_slice(c.stream, count, ov, T, ov, w.eB.get(), w.Btn.get(), w.Lp, 0, with_nn ? w.Tnn.get() : nullptr, w.ldkT, 0);
 }
@@ -130,21 +157,11 @@ __global__ void rpa_coef_kernel(int S, int k, int kk, const double* __restrict__
 }
 
 void sync_copy(cudaStream_t s, void* dst, const void* src, size_t bytes) {
+  // a copy into pageable host memory waits for the stream inside the copy call
+  HostScope h_wait("host:sync_wait");
   XS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
   XS_CUDA(cudaStreamSynchronize(s));
 }
-
-// Page-locked host staging for the once-per-iteration read-back of the Ritz
-// values, residual norms and status words (one stream synchronisation per
-// iteration instead of one per value).
-struct HostStage {
-  double* p = nullptr;
-  size_t n = 0;
-  explicit HostStage(size_t count) : n(count) { XS_CUDA(cudaMallocHost(&p, sizeof(double) * count)); }
-  ~HostStage() { if (p) cudaFreeHost(p); }
-  HostStage(const HostStage&) = delete;
-  HostStage& operator=(const HostStage&) = delete;
-};
 
 // nrm2[r] = 1 / nrm[r] (0 for a zero row)
 __global__ void inv_norms_kernel(int n, const double* __restrict__ nrm, double* __restrict__ inv) {
@@ -223,19 +240,12 @@ void make_guess(Ctx& c, const DevMol& m, Work& w, int nguess, long long ov, cons
   } else {
     std::vector<double> eps(m.n);
     sync_copy(s, eps.data(), m.eps.get(), sizeof(double) * m.n);
-    order.resize(ov);
-    std::iota(order.begin(), order.end(), 0LL);
-    auto de = [&](long long k) { return eps[m.o + k % m.v] - eps[k / m.v]; };
-    std::partial_sort(order.begin(), order.begin() + nguess, order.end(), [&](long long x, long long y) {
-      double dx = de(x), dy = de(y);
-      return dx < dy || (dx == dy && x < y);
-    });
+    order = lowest_gaps(eps, m.o, m.v, nguess);
   }
   XS_CUDA(cudaMemsetAsync(w.V.get(), 0, sizeof(double) * nguess * ov, s));
   w.idx.ensure(nguess);
   XS_CUDA(cudaMemcpyAsync(w.idx.get(), order.data(), sizeof(long long) * nguess, cudaMemcpyHostToDevice, s));
   unit_vectors(s, nguess, ov, w.idx.get(), w.V.get());
-  XS_CUDA(cudaStreamSynchronize(s));
 }
 
 // Transition dipoles through the MO dipole integrals D^x_ia = <i|r_x|a>
@@ -333,6 +343,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   // residual, are still converged far below 1e-5 eV at a 1e-4 eV residual.
   const double tol_eff = (opt.precision == XS_MIXED) ? std::max(opt.tol, kMixedResidualFloor) : opt.tol;
 
+  HostScope h_setup("host:setup");
   // the workspace persists in the context between solves (buffers only grow):
   // repeated solves of similar molecules allocate nothing
   if (!c.dav_cache) c.dav_cache = std::shared_ptr<void>(new Work(), [](void* p) { delete static_cast<Work*>(p); });
@@ -346,7 +357,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   const size_t SB = (size_t)std::max(Smax, 2 * kk + 2);
   const size_t SS = SB * SB;
   w.E.ensure(SS); w.Q.ensure(SS); w.w.ensure(SB); w.Sh.ensure(SS);
-  w.tS.ensure(SS);
+  w.tS.ensure(std::max(SS, (size_t)Smax * (4 * kk + 4)));   // also the S x 2 new-block TDHF projections
   w.E2.ensure(SS); w.Q2.ensure(SS); w.w2.ensure(SB);
   w.cu.ensure((size_t)Smax * 2 * kk); w.cw.ensure((size_t)Smax * kk);
   w.X.ensure((size_t)2 * kk * ov); w.R1.ensure((size_t)(rpa ? 2 : 1) * kk * ov);
@@ -364,10 +375,11 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     }
     w.Lp = oz_lp(ov);
     w.ldk = oz_ldk(Smax);
-    w.bcap = std::max(maxnew, std::max(nguess, 2 * kk));
+    const int tcap = std::max(maxnew, std::max(nguess, 2 * kk));   // rows of a new block
+    w.bcap = (rpa ? 2 : 1) * tcap;                                  // TDHF projections: two blocks
     w.Vtn.ensure((size_t)Smax * kOzDigits * w.Lp);
     w.Btn.ensure((size_t)w.bcap * kOzDigits * w.Lp);
-    w.ldkT = oz_ldk(w.bcap);
+    w.ldkT = oz_ldk(tcap);
     // digit rows past the live vectors are read (times zero coefficients) and
     // must be finite: zero them when (re)allocated; later contents are digits
     auto ensure_zeroed = [&](DevBuf<oz_t>& b, size_t count) {
@@ -407,49 +419,50 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     XS_CUDA(cudaEventRecord(e1, s));
     st.products += count;
   };
-  HostStage hs(3 * (size_t)kk + 8);
+  // read-back staging (page-locked, kept in the workspace): omega, norms, status words
+  double* const hs = w.host_stage(3 * (size_t)kk + 8);
   // read back omega (k), residual norms (nn) and the status words in one synchronisation
   auto fetch = [&](int k, int nn) {
-    XS_CUDA(cudaMemcpyAsync(hs.p, w.omega.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-    XS_CUDA(cudaMemcpyAsync(hs.p + kk, w.nrm.get(), sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
-    XS_CUDA(cudaMemcpyAsync(hs.p + 3 * kk, w.flag.get() + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+    XS_CUDA(cudaMemcpyAsync(hs, w.omega.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    XS_CUDA(cudaMemcpyAsync(hs + kk, w.nrm.get(), sizeof(double) * nn, cudaMemcpyDeviceToHost, s));
+    XS_CUDA(cudaMemcpyAsync(hs + 3 * kk, w.flag.get() + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (c.tc_err.get())
-      XS_CUDA(cudaMemcpyAsync(hs.p + 3 * kk + 1, c.tc_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+      XS_CUDA(cudaMemcpyAsync(hs + 3 * kk + 1, c.tc_err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     else
-      std::memset(hs.p + 3 * kk + 1, 0, sizeof(double));
-    XS_CUDA(cudaStreamSynchronize(s));
-    std::copy(hs.p, hs.p + k, hw.begin());
-    std::copy(hs.p + kk, hs.p + kk + nn, hn.begin());
+      std::memset(hs + 3 * kk + 1, 0, sizeof(double));
+    {
+      HostScope h_wait("host:fetch_wait");
+      XS_CUDA(cudaStreamSynchronize(s));
+    }
+    std::copy(hs, hs + k, hw.begin());
+    std::copy(hs + kk, hs + kk + nn, hn.begin());
     int flag3 = 0, tcerr = 0;
-    std::memcpy(&flag3, hs.p + 3 * kk, sizeof(int));
-    std::memcpy(&tcerr, hs.p + 3 * kk + 1, sizeof(int));
+    std::memcpy(&flag3, hs + 3 * kk, sizeof(int));
+    std::memcpy(&tcerr, hs + 3 * kk + 1, sizeof(int));
     return std::make_pair(flag3, tcerr);
   };
 
   // learned guess and diagonal shift: MLP outputs on the lowest-gap pairs
-  DevBuf<double> lshift;
   const double* shift = nullptr;
   std::vector<long long> learned_pairs;
   if (opt.guess == XS_GUESS_LEARNED && c.mlp && c.mlp->ready) {
-    const int npairs = static_cast<int>(std::min<long long>(ov, 65536));
+    HostScope h_learned("host:learned_guess");
+    const int npairs = static_cast<int>(std::min<long long>(ov, kLearnedPairs));
     std::vector<long long> pairs = lowest_gap_pairs(c, m, npairs);
-    DevBuf<float> F((size_t)pairs.size() * kMlpFeatures);
-    DevBuf<long long> dpairs;
-    pair_features(c, m, pairs, F.get(), dpairs);
-    std::vector<DevBuf<float>> Z, H;
-    c.mlp->forward(s, static_cast<int>(pairs.size()), F.get(), Z, H);
+    w.F.ensure((size_t)pairs.size() * kMlpFeatures);
+    pair_features(c, m, pairs, w.F.get(), w.dpairs, w.fw);
+    c.mlp->forward(s, static_cast<int>(pairs.size()), w.F.get(), w.Z, w.H);
     std::vector<float> out(pairs.size() * kMlpOutputs);
-    sync_copy(s, out.data(), H[kMlpLayers - 1].get(), sizeof(float) * out.size());
+    sync_copy(s, out.data(), w.H[kMlpLayers - 1].get(), sizeof(float) * out.size());
     // preconditioner shift on the candidate pairs, zero elsewhere
     std::vector<double> sh(pairs.size());
     for (size_t q = 0; q < pairs.size(); ++q) sh[q] = out[q * kMlpOutputs];
-    lshift.alloc((size_t)ov);
-    XS_CUDA(cudaMemsetAsync(lshift.get(), 0, sizeof(double) * ov, s));
-    DevBuf<double> dsh(sh.size());
-    XS_CUDA(cudaMemcpyAsync(dsh.get(), sh.data(), sizeof(double) * sh.size(), cudaMemcpyHostToDevice, s));
-    scatter(s, static_cast<int>(pairs.size()), dpairs.get(), dsh.get(), lshift.get());
-    XS_CUDA(cudaStreamSynchronize(s));
-    shift = lshift.get();
+    w.lshift.ensure((size_t)ov);
+    XS_CUDA(cudaMemsetAsync(w.lshift.get(), 0, sizeof(double) * ov, s));
+    w.dsh.ensure(sh.size());
+    XS_CUDA(cudaMemcpyAsync(w.dsh.get(), sh.data(), sizeof(double) * sh.size(), cudaMemcpyHostToDevice, s));
+    scatter(s, static_cast<int>(pairs.size()), w.dpairs.get(), w.dsh.get(), w.lshift.get());
+    shift = w.lshift.get();
     // guess: the pairs with the highest predicted weight in the low roots
     std::vector<size_t> idx(pairs.size());
     std::iota(idx.begin(), idx.end(), size_t(0));
@@ -465,6 +478,8 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   slice_V(c, w, ov, 0, S);
   apply(0, S);
 
+  h_setup.stop();
+  HostScope h_loop("host:loop");
   std::vector<char> conv(kk, 0);
   int it = 0, kq = 1;
   bool converged = false, polishing = false;
@@ -472,13 +487,23 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   for (it = 1; it <= max_iter + 1; ++it) {
     // projected matrices: new columns Sold..S-1 over all rows 0..S-1
     if (w.oz) {
-      slice_P(c, w, ov, w.S1.get(), w.eS1, w.S1nn, Sold, S - Sold, true);
-      oz_gram(s, S, S - Sold, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS1.get() + Sold, 1.0, 0.0,
-              w.a1.get() + Sold, Smax, w.ozw, c.tc_err.get());
-      if (rpa) {
-        slice_P(c, w, ov, w.S2.get(), w.eS2, w.S2nn, Sold, S - Sold, true);
-        oz_gram(s, S, S - Sold, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS2.get() + Sold, 1.0, 0.0,
-                w.a2.get() + Sold, Smax, w.ozw, c.tc_err.get());
+      const int cnt = S - Sold;
+      slice_P(c, w, ov, w.S1.get(), w.eS1, w.S1nn, Sold, cnt, true, 0);
+      if (!rpa) {
+        oz_gram(s, S, cnt, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS1.get() + Sold, 1.0, 0.0,
+                w.a1.get() + Sold, Smax, w.ozw, c.tc_err.get());
+      } else {
+        // V^T [(A+B) V_new | (A-B) V_new] in one pass over V's digits
+        slice_P(c, w, ov, w.S2.get(), w.eS2, w.S2nn, Sold, cnt, true, cnt);
+        XS_CUDA(cudaMemcpyAsync(w.eB.get(), w.eS1.get() + Sold, sizeof(int) * cnt, cudaMemcpyDeviceToDevice, s));
+        XS_CUDA(cudaMemcpyAsync(w.eB.get() + cnt, w.eS2.get() + Sold, sizeof(int) * cnt, cudaMemcpyDeviceToDevice,
+                                s));
+        oz_gram(s, S, 2 * cnt, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eB.get(), 1.0, 0.0, w.tS.get(),
+                2 * cnt, w.ozw, c.tc_err.get());
+        XS_CUDA(cudaMemcpy2DAsync(w.a1.get() + Sold, sizeof(double) * Smax, w.tS.get(), sizeof(double) * 2 * cnt,
+                                  sizeof(double) * cnt, S, cudaMemcpyDeviceToDevice, s));
+        XS_CUDA(cudaMemcpy2DAsync(w.a2.get() + Sold, sizeof(double) * Smax, w.tS.get() + cnt,
+                                  sizeof(double) * 2 * cnt, sizeof(double) * cnt, S, cudaMemcpyDeviceToDevice, s));
       }
     } else {
       gram<double>(s, S, S - Sold, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S1.get() + Sold * ov,
@@ -722,6 +747,8 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     S += nkeep;
     apply(Sold, nkeep);
   }
+  h_loop.stop();
+  HostScope h_finish("host:finish");
   check_device_error(c);
   st.iterations = std::min(it, max_iter);
   {
@@ -743,12 +770,12 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   XS_CUDA(cudaMemcpyAsync(m.U.get(), w.X.get(), sizeof(double) * kk * ov, cudaMemcpyDeviceToDevice, s));
   XS_CUDA(cudaMemcpyAsync(m.Wv.get(), rpa ? w.AX : w.X.get(), sizeof(double) * kk * ov,
                           cudaMemcpyDeviceToDevice, s));
-  DevBuf<double> fdev(kk);
-  oscillator_strengths(c, m, kk, m.U.get(), w.omega.get(), fdev.get());
+  w.fdev.ensure(kk);
+  oscillator_strengths(c, m, kk, m.U.get(), w.omega.get(), w.fdev.get());
   m.omega.assign(hw.begin(), hw.begin() + kk);
   m.resid.assign(hn.begin(), hn.begin() + kk);
   m.osc.resize(kk);
-  sync_copy(s, m.osc.data(), fdev.get(), sizeof(double) * kk);
+  sync_copy(s, m.osc.data(), w.fdev.get(), sizeof(double) * kk);
   m.iterations = st.iterations;
   st.converged = converged;
   return converged ? XS_OK : XS_ENOCONV;

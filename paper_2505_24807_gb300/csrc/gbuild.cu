@@ -107,7 +107,25 @@ __device__ __forceinline__ void one_centre(const T* p, int a, int b, const T Rd[
 // through shared memory and every thread writes one G (and G-) element.
 constexpr int kGR = 4, kGC = 64, kGP = 10, kGQ = 160;
 
-template <typename T, GMode MODE>
+// TF32 pair of a float (hi rounded to TF32, lo = x - hi exact): the split
+// epilogue writes the tensor-core operand of the back-transform directly
+__device__ __forceinline__ void tf32_pair(float x, float& hi, float& lo) {
+  const uint32_t bits = __float_as_uint(x);
+  hi = __uint_as_float((bits + 0x1000u) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+// Output of the tile kernel: plain G (and G-) with row stride n, or (SPLIT)
+// their TF32 pairs with row stride ldo (batch stride n * ldo)
+template <typename T>
+struct GOut {
+  T* G;
+  T* Gm;
+  float *Gh, *Gl, *Gmh, *Gml;
+  int ldo;
+};
+
+template <typename T, GMode MODE, bool SPLIT>
 __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, const int4* __restrict__ rows,
                                                     const int4* __restrict__ cols, const int* __restrict__ ao_atom,
                                                     const int* __restrict__ ao_local,
@@ -117,7 +135,7 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
                                                     const int* __restrict__ atom_elem,
                                                     const double* __restrict__ par, const T* __restrict__ W,
                                                     const T* __restrict__ J2, const T* __restrict__ Rall,
-                                                    T* __restrict__ Gall, T* __restrict__ Gmall) {
+                                                    const GOut<T> out) {
   // R tiles padded by 4 rows / columns of zeros: a hydrogen's block is
   // handled as a 4 x 4 block with zero weights past its single AO
   // double-buffered: matrix v is read from one buffer while v + 1 is stored
@@ -231,8 +249,21 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
           gm = -(kr - krt);
         }
       }
-      Gall[(long long)v * n * n + (long long)mu * n + lam] = g;
-      if (MODE == G_RPA) Gmall[(long long)v * n * n + (long long)mu * n + lam] = gm;
+      if constexpr (SPLIT) {
+        const long long at = (long long)v * n * out.ldo + (long long)mu * out.ldo + lam;
+        float h, l;
+        tf32_pair(static_cast<float>(g), h, l);
+        out.Gh[at] = h;
+        out.Gl[at] = l;
+        if (MODE == G_RPA) {
+          tf32_pair(static_cast<float>(gm), h, l);
+          out.Gmh[at] = h;
+          out.Gml[at] = l;
+        }
+      } else {
+        out.G[(long long)v * n * n + (long long)mu * n + lam] = g;
+        if (MODE == G_RPA) out.Gm[(long long)v * n * n + (long long)mu * n + lam] = gm;
+      }
     }
     if (v + 1 < nvec) {
       if (active) Rt[buf ^ 1][ri][ci] = nxt;
@@ -243,21 +274,32 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
   }
 }
 
-template <typename T>
+template <typename T, bool SPLIT>
 void launch_tiles(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* W, const T* J2,
-                  const T* R, T* G, T* Gm) {
+                  const T* R, const GOut<T>& out) {
   dim3 grid(m.gb_ncols, m.gb_nrows);
   const int4* rows = reinterpret_cast<const int4*>(m.gb_rows.get());
   const int4* cols = reinterpret_cast<const int4*>(m.gb_cols.get());
   if (mode == G_CIS)
-    gtile_kernel<T, G_CIS><<<grid, 256, 0, s>>>(m.n, m.np, nvec, rows, cols, m.ao_atom.get(), m.ao_local.get(),
-                                                m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
-                                                m.atom_elem.get(), d_par, W, J2, R, G, nullptr);
+    gtile_kernel<T, G_CIS, SPLIT><<<grid, 256, 0, s>>>(m.n, m.np, nvec, rows, cols, m.ao_atom.get(),
+                                                       m.ao_local.get(), m.atom_ao_off.get(), m.atom_nao.get(),
+                                                       m.atom_prod_off.get(), m.atom_elem.get(), d_par, W, J2, R, out);
   else
-    gtile_kernel<T, G_RPA><<<grid, 256, 0, s>>>(m.n, m.np, nvec, rows, cols, m.ao_atom.get(), m.ao_local.get(),
-                                                m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
-                                                m.atom_elem.get(), d_par, W, J2, R, G, Gm);
+    gtile_kernel<T, G_RPA, SPLIT><<<grid, 256, 0, s>>>(m.n, m.np, nvec, rows, cols, m.ao_atom.get(),
+                                                       m.ao_local.get(), m.atom_ao_off.get(), m.atom_nao.get(),
+                                                       m.atom_prod_off.get(), m.atom_elem.get(), d_par, W, J2, R, out);
   XS_CHECK_LAUNCH();
+}
+
+// zero columns [n, ldo) of rows x ldo matrices (batch stride rows * ldo)
+__global__ void zero_pad_cols_kernel(int rows, int n, int ldo, int nvec, float* a, float* b) {
+  const int w = ldo - n;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nvec * rows * w) return;
+  const long long r = idx / w;
+  const long long at = r * ldo + n + idx % w;
+  a[at] = 0.0f;
+  if (b) b[at] = 0.0f;
 }
 
 }  // namespace
@@ -288,7 +330,37 @@ void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, in
   const double outs = (mode == G_CIS) ? 1.0 : 2.0;
   ProfScope ps(s, sizeof(T) == 8 ? "gbuild_assemble_f64" : "gbuild_assemble_f32",
                sizeof(T) * ((double)nvec * n * n * (1.0 + outs) + (double)np * np), 0.0);
-  launch_tiles<T>(s, m, d_par, mode, nvec, W, J2, R, G, Gm);
+  launch_tiles<T, false>(s, m, d_par, mode, nvec, W, J2, R, GOut<T>{G, Gm, nullptr, nullptr, nullptr, nullptr, 0});
+}
+
+void gbuild_split(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const float* R,
+                  float* Gh, float* Gl, float* Gmh, float* Gml, int ldo, DevBuf<float>& ws) {
+  if (nvec <= 0) return;
+  const int n = m.n, np = m.np;
+  if (ldo < n) throw Error(XS_EINVAL, "gbuild_split: row stride below n");
+  ws.ensure((size_t)2 * np * nvec);
+  float* rT = ws.get();
+  float* J2 = ws.get() + (size_t)np * nvec;
+  {
+    dim3 block(8, 32);
+    dim3 grid((m.L.natoms + 31) / 32);
+    pack_diag_kernel<float, true><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(),
+                                                         m.atom_nao.get(), m.atom_prod_off.get(), R, rT);
+    XS_CHECK_LAUNCH();
+  }
+  const float* W = m.Wf.get();
+  static thread_local DevBuf<float> split_ws;
+  gram<float>(s, np, nvec, np, W, np, rT, np, J2, nvec, 1.0f, 0.0f, split_ws);
+  if (ldo > n) {
+    const long long cnt = (long long)nvec * n * (ldo - n);
+    zero_pad_cols_kernel<<<grid1(cnt, 256), 256, 0, s>>>(n, n, ldo, nvec, Gh, Gl);
+    if (mode != G_CIS) zero_pad_cols_kernel<<<grid1(cnt, 256), 256, 0, s>>>(n, n, ldo, nvec, Gmh, Gml);
+    XS_CHECK_LAUNCH();
+  }
+  // algorithmic traffic: read R, write the G (and G-) TF32 pairs, read the pair integrals once
+  const double outs = (mode == G_CIS) ? 1.0 : 2.0;
+  ProfScope ps(s, "gbuild_assemble_f32", 4.0 * ((double)nvec * n * n * (1.0 + 2.0 * outs) + (double)np * np), 0.0);
+  launch_tiles<float, true>(s, m, d_par, mode, nvec, W, J2, R, GOut<float>{nullptr, nullptr, Gh, Gl, Gmh, Gml, ldo});
 }
 
 template <typename T>
@@ -307,7 +379,7 @@ void gbuild_raw(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode
   if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(m.W.get());
   else W = reinterpret_cast<const T*>(m.Wf.get());
   gemm<T>(s, false, false, np, nvec, np, T(1), W, np, 0, r, nvec, 0, T(0), J2, nvec, 0, 1);
-  launch_tiles<T>(s, m, d_par, mode, nvec, W, J2, R, G, Gm);
+  launch_tiles<T, false>(s, m, d_par, mode, nvec, W, J2, R, GOut<T>{G, Gm, nullptr, nullptr, nullptr, nullptr, 0});
 }
 
 void build_gtiles(cudaStream_t s, DevMol& m) {

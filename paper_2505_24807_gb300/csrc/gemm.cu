@@ -414,6 +414,7 @@ int tuned_shape(cudaStream_t s, bool tA, bool tB, int M, int N, int K, const T* 
 
 NoTuneScope::NoTuneScope() { ++g_no_tune; }
 NoTuneScope::~NoTuneScope() { --g_no_tune; }
+bool tuning_disabled() { return g_no_tune > 0; }
 
 template <typename T>
 void gemm(cudaStream_t s, bool transA, bool transB, int M, int N, int K, T alpha, const T* A, int lda, long long sA,

@@ -22,6 +22,8 @@ struct NoTuneScope {
   NoTuneScope();
   ~NoTuneScope();
 };
+// True while a NoTuneScope is alive on this thread.
+bool tuning_disabled();
 
 // C (M x N) = alpha A (M x L) B(N x L)^T + beta C for long L (split over L).
 template <typename T>
@@ -36,6 +38,11 @@ enum GMode { G_CIS = 0, G_RPA = 1 };
 template <typename T>
 void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* R,
             T* G, T* Gm, DevBuf<T>& ws);
+// Float32 G build whose output is the TF32 pair (hi, lo) of G (and G- for
+// TDHF) with row stride ldo >= n (batch stride n * ldo, columns n..ldo-1
+// zeroed): the back-transform's tensor-core operand without a separate split.
+void gbuild_split(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const float* R,
+                  float* Gh, float* Gl, float* Gmh, float* Gml, int ldo, DevBuf<float>& ws);
 // Atom-aligned tiling of G used by gbuild (rows: one heavy atom or up to 4
 // hydrogens; columns: whole atoms, at most 64 AOs); built once per molecule.
 void build_gtiles(cudaStream_t s, DevMol& m);
@@ -68,9 +75,9 @@ void transpose(cudaStream_t s, int rows, int cols, const double* a, double* b);
 void check_device_error(Ctx& c);
 
 // ---- small dense eigenproblems (small.cu) -----------------------------------
-// Symmetric eigen-decomposition of batch matrices (n <= 512) by cyclic Jacobi
-// in one CTA each: A (n x n, lda) is overwritten, V gets the eigenvectors in
-// columns (ldv), w the eigenvalues in ascending order.
+// Symmetric eigen-decomposition (n <= 1024) by cyclic Jacobi in one CTA
+// (shared-memory resident for n <= 64): A (n x n, lda) may be overwritten, V
+// gets the eigenvectors in columns (ldv), w the eigenvalues in ascending order.
 void jacobi_eig(cudaStream_t s, int n, double* A, int lda, double* V, int ldv, double* w, int* info);
 
 }  // namespace xs

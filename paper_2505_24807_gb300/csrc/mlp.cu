@@ -167,8 +167,9 @@ __global__ void features_kernel(int npairs, int n, int o, int v, int natoms, con
 }
 
 // atomic populations q[A][p] = sum_{mu on A} C_mu,p^2 (natoms x n)
+// Mulliken-like atomic populations of every MO: qT[p][A] = sum_{u on A} C[u][p]^2
 __global__ void populations_kernel(int n, int natoms, const double* __restrict__ CT,
-                                   const int* __restrict__ atom_ao_off, const int* __restrict__ atom_nao, double* q) {
+                                   const int* __restrict__ atom_ao_off, const int* __restrict__ atom_nao, double* qT) {
   const int p = blockIdx.y;
   const int A = blockIdx.x * blockDim.x + threadIdx.x;
   if (A >= natoms) return;
@@ -177,7 +178,7 @@ __global__ void populations_kernel(int n, int natoms, const double* __restrict__
     const double c = CT[(long long)p * n + atom_ao_off[A] + u];
     s += c * c;
   }
-  q[(long long)A * n + p] = s;
+  qT[(long long)p * natoms + A] = s;
 }
 
 // monopole Coulomb matrix gamma_AB = (s_A s_A | s_B s_B), gamma_AA = gss_A
@@ -189,11 +190,21 @@ __global__ void gamma_kernel(int natoms, int np, const double* __restrict__ W, c
                                           : W[(long long)atom_prod_off[A] * np + atom_prod_off[B]];
 }
 
-__global__ void gather_pairs_kernel(int npairs, int o, int v, const long long* __restrict__ pairs,
-                                    const double* __restrict__ Jov, float* F) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// monopole Coulomb energy of each pair's orbital densities, one warp per pair:
+// J = sum_A qT[i][A] tT[a][A] with tT = q_vir^T gamma; feature 10 = J / 10
+__global__ void pair_coulomb_kernel(int npairs, int o, int v, int natoms, const long long* __restrict__ pairs,
+                                    const double* __restrict__ qT, const double* __restrict__ tT, float* F) {
+  const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
   if (k >= npairs) return;
-  F[(long long)k * kMlpFeatures + 10] = static_cast<float>(Jov[pairs[k]] / 10.0);
+  const long long pk = pairs[k];
+  const int i = static_cast<int>(pk / v), a = static_cast<int>(pk % v);
+  const double* qi = qT + (long long)i * natoms;
+  const double* ta = tT + (long long)a * natoms;
+  double sum = 0.0;
+  for (int A = lane; A < natoms; A += 32) sum += qi[A] * ta[A];
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if (lane == 0) F[(long long)k * kMlpFeatures + 10] = static_cast<float>(sum / 10.0);
 }
 
 __device__ __forceinline__ int pidx_m(int a, int b) {
@@ -419,49 +430,59 @@ float Mlp::train_step(cudaStream_t s, int rows, const float* X, const float* T, 
 
 // ---- features and targets ----------------------------------------------------
 
+std::vector<long long> lowest_gaps(const std::vector<double>& eps, int o, int v, long long k) {
+  // (gap, pair) for every pair without per-comparison index arithmetic; the k
+  // smallest by selection (linear) and a sort of those k; ties by pair index
+  const long long ov = (long long)o * v;
+  k = std::min(k, ov);
+  std::vector<std::pair<double, long long>> g((size_t)ov);
+  for (int i = 0; i < o; ++i)
+    for (int a = 0; a < v; ++a) g[(size_t)i * v + a] = {eps[o + a] - eps[i], (long long)i * v + a};
+  if (k < ov) std::nth_element(g.begin(), g.begin() + k, g.end());
+  std::sort(g.begin(), g.begin() + k);
+  std::vector<long long> out((size_t)k);
+  for (long long q = 0; q < k; ++q) out[(size_t)q] = g[(size_t)q].second;
+  return out;
+}
+
 std::vector<long long> lowest_gap_pairs(Ctx& c, const DevMol& m, int npairs) {
   std::vector<double> eps(m.n);
   XS_CUDA(cudaMemcpyAsync(eps.data(), m.eps.get(), sizeof(double) * m.n, cudaMemcpyDeviceToHost, c.stream));
   XS_CUDA(cudaStreamSynchronize(c.stream));
-  const long long ov = (long long)m.o * m.v;
-  npairs = static_cast<int>(std::min<long long>(npairs, ov));
-  std::vector<long long> order(ov);
-  std::iota(order.begin(), order.end(), 0LL);
-  auto de = [&](long long k) { return eps[m.o + k % m.v] - eps[k / m.v]; };
-  std::partial_sort(order.begin(), order.begin() + npairs, order.end(), [&](long long x, long long y) {
-    const double dx = de(x), dy = de(y);
-    return dx < dy || (dx == dy && x < y);
-  });
-  order.resize(npairs);
-  return order;
+  return lowest_gaps(eps, m.o, m.v, npairs);
 }
 
 void pair_features(Ctx& c, const DevMol& m, const std::vector<long long>& pairs, float* F_dev,
-                   DevBuf<long long>& dpairs) {
+                   DevBuf<long long>& dpairs, FeatureWork& fw) {
   cudaStream_t s = c.stream;
   const int npairs = static_cast<int>(pairs.size());
   dpairs.ensure(npairs);
   XS_CUDA(cudaMemcpyAsync(dpairs.get(), pairs.data(), sizeof(long long) * npairs, cudaMemcpyHostToDevice, s));
-  DevBuf<double> stats((size_t)m.n * 6);
-  mo_stats_kernel<<<m.n, 128, 0, s>>>(m.n, m.CT.get(), m.ao_atom.get(), m.ao_local.get(), m.xyz.get(), stats.get());
+  fw.stats.ensure((size_t)m.n * 6);
+  mo_stats_kernel<<<m.n, 128, 0, s>>>(m.n, m.CT.get(), m.ao_atom.get(), m.ao_local.get(), m.xyz.get(),
+                                      fw.stats.get());
   XS_CHECK_LAUNCH();
   features_kernel<<<grid1(npairs, 128), 128, 0, s>>>(npairs, m.n, m.o, m.v, m.L.natoms, dpairs.get(), m.CT.get(),
-                                                     m.eps.get(), stats.get(), m.atom_ao_off.get(), m.atom_nao.get(),
-                                                     F_dev);
+                                                     m.eps.get(), fw.stats.get(), m.atom_ao_off.get(),
+                                                     m.atom_nao.get(), F_dev);
   XS_CHECK_LAUNCH();
-  // monopole Coulomb energy of the orbital densities: J = Q_occ^T Gamma Q_vir (o x v)
+  // monopole Coulomb energy of the orbital densities of each pair:
+  // J_ia = q(i)^T Gamma q(a), q(p) the atomic populations of MO p
   const int N = m.L.natoms;
-  DevBuf<double> q((size_t)N * m.n), gam((size_t)N * N), t((size_t)N * m.v), J((size_t)m.o * m.v);
+  fw.q.ensure((size_t)N * m.n);
+  fw.gam.ensure((size_t)N * N);
+  fw.t.ensure((size_t)N * m.v);
   populations_kernel<<<dim3((N + 127) / 128, m.n), 128, 0, s>>>(m.n, N, m.CT.get(), m.atom_ao_off.get(),
-                                                               m.atom_nao.get(), q.get());
+                                                               m.atom_nao.get(), fw.q.get());
   gamma_kernel<<<dim3((N + 127) / 128, N), 128, 0, s>>>(N, m.np, m.W.get(), m.atom_prod_off.get(), m.atom_elem.get(),
-                                                        c.d_par.get(), gam.get());
+                                                        c.d_par.get(), fw.gam.get());
   XS_CHECK_LAUNCH();
-  gemm<double>(s, false, false, N, m.v, N, 1.0, gam.get(), N, 0, q.get() + m.o, m.n, 0, 0.0, t.get(), m.v, 0, 1);
-  gemm<double>(s, true, false, m.o, m.v, N, 1.0, q.get(), m.n, 0, t.get(), m.v, 0, 0.0, J.get(), m.v, 0, 1);
-  gather_pairs_kernel<<<grid1(npairs, 128), 128, 0, s>>>(npairs, m.o, m.v, dpairs.get(), J.get(), F_dev);
+  // tT (v x N) = q_vir^T Gamma (Gamma symmetric)
+  gemm<double>(s, false, false, m.v, N, N, 1.0, fw.q.get() + (size_t)m.o * N, N, 0, fw.gam.get(), N, 0, 0.0,
+               fw.t.get(), N, 0, 1);
+  pair_coulomb_kernel<<<grid1((long long)npairs * 32, 256), 256, 0, s>>>(npairs, m.o, m.v, N, dpairs.get(),
+                                                                        fw.q.get(), fw.t.get(), F_dev);
   XS_CHECK_LAUNCH();
-  XS_CUDA(cudaStreamSynchronize(s));
 }
 
 void diagonal_shift(Ctx& c, const DevMol& m, const std::vector<long long>& pairs, double* shift_dev) {

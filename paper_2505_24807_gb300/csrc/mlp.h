@@ -31,11 +31,19 @@ struct Mlp {
                    DevBuf<float>& scratch);
 };
 
-// the npairs lowest eps_a - eps_i pairs (flattened i * nvir + a), ties by index
+// indices i * nvir + a of the k lowest orbital-energy gaps eps[o + a] - eps[i],
+// ascending (ties: lower index first)
+std::vector<long long> lowest_gaps(const std::vector<double>& eps, int o, int v, long long k);
+// the npairs lowest-gap pairs of a molecule (reads its orbital energies back)
 std::vector<long long> lowest_gap_pairs(Ctx& c, const DevMol& m, int npairs);
-// features (npairs x kMlpFeatures, device) of the given pairs
+// device scratch of pair_features, kept by the caller between calls
+struct FeatureWork {
+  DevBuf<double> stats, q, gam, t;
+};
+// features (npairs x kMlpFeatures, device) of the given pairs; dpairs receives
+// the pair list on the device.  Asynchronous on the context's stream.
 void pair_features(Ctx& c, const DevMol& m, const std::vector<long long>& pairs, float* F_dev,
-                   DevBuf<long long>& dpairs);
+                   DevBuf<long long>& dpairs, FeatureWork& fw);
 // exact diagonal shift 2 (ia|ia) - (ii|aa) of the given pairs (device, float64)
 void diagonal_shift(Ctx& c, const DevMol& m, const std::vector<long long>& pairs, double* shift_dev);
 

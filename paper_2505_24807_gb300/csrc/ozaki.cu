@@ -462,12 +462,12 @@ CUtensorMap make_map_bf16(const oz_t* ptr, long long inner, long long rows, long
 }
 
 int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {
+    int dev = 0, count = 0;
     XS_CUDA(cudaGetDevice(&dev));
-    XS_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
-  }
+    XS_CUDA(cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev));
+    return count;
+  }();
   return n;
 }
 
@@ -475,12 +475,12 @@ template <int BN>
 void launch_oz(cudaStream_t s, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
                const CUtensorMap& b, const OzArgs& args, int* err) {
   using C = OzCfg<BN>;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {   // once per process (thread-safe initialisation)
     XS_CUDA(cudaFuncSetAttribute(oz_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(C::SMEM)));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int grid = std::min(args.ntiles, num_sms());   // persistent: one CTA per SM
   oz_kernel<BN><<<grid, 192, C::SMEM, s>>>(a0, a1, a2, b, args, err);
   XS_CHECK_LAUNCH();

@@ -58,4 +58,17 @@ ProfScope::~ProfScope() {
   ent->pending.emplace_back(a, b);
 }
 
+HostScope::HostScope(const char* name) {
+  if (!g_prof || !g_prof->on) return;
+  ent = &g_prof->e[name];
+  ent->launches += 1;
+  t0 = std::chrono::steady_clock::now();
+}
+
+void HostScope::stop() {
+  if (!ent) return;
+  ent->ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  ent = nullptr;
+}
+
 }  // namespace xs

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <map>
 #include <string>
 #include <vector>
@@ -39,6 +40,16 @@ struct ProfScope {
   cudaStream_t s = nullptr;
   ProfScope(cudaStream_t stream, const char* name, double bytes, double flops);
   ~ProfScope();
+};
+
+// Host wall time of a region of an API call, recorded under its name (by
+// convention "host:..."; launches counts the entries) while profiling is on.
+struct HostScope {
+  ProfEntry* ent = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  explicit HostScope(const char* name);
+  void stop();
+  ~HostScope() { stop(); }
 };
 
 }  // namespace xs

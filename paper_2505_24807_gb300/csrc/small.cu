@@ -15,19 +15,31 @@ namespace xs {
 
 namespace {
 
+// reciprocal to ~1e-14 relative (float32 estimate, one float64 Newton step);
+// exact division outside the float32 range
+__device__ __forceinline__ double rcp_approx(double x) {
+  const float ax = fabsf(static_cast<float>(x));
+  if (!(ax > 1e-36f && ax < 1e36f)) return 1.0 / x;
+  const double r = static_cast<double>(__frcp_rn(static_cast<float>(x)));
+  return r * fma(-x, r, 2.0);
+}
+
 __device__ __forceinline__ int tour(int i, int r, int m) {
   // player at seat i in round r of an m-player round robin (seat 0 fixed)
   return (i == 0) ? 0 : ((i - 1 + r) % (m - 1)) + 1;
 }
 
-__global__ void __launch_bounds__(1024) jacobi_kernel(int n, double* A, int lda, double* V, int ldv, double* w,
-                                                      int* info, int max_sweeps) {
-  extern __shared__ double sh[];
+// Sweeps of cyclic two-sided Jacobi on A (n x n, row stride lda) accumulating
+// the rotations into V (row stride ldv, initialised here to the identity),
+// run by the whole CTA; A and V may live in global or shared memory.
+// scratch: 2 * (m / 2) doubles + 2 * (m / 2) ints (m = n rounded up to even).
+// Returns the number of sweeps taken (max_sweeps when not converged).
+__device__ int jacobi_sweeps(int n, double* A, int lda, double* V, int ldv, double* scratch, int max_sweeps) {
   const int m = n + (n & 1);
   const int half = m / 2;
-  double* cs = sh;            // c of each pair
-  double* sn = sh + half;     // s of each pair
-  int* pp = reinterpret_cast<int*>(sh + 2 * half);
+  double* cs = scratch;            // c of each pair
+  double* sn = scratch + half;     // s of each pair
+  int* pp = reinterpret_cast<int*>(scratch + 2 * half);
   int* qq = pp + half;
   __shared__ double red[2][32];
   __shared__ int done;
@@ -70,10 +82,14 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int n, double* A, int lda,
           double apq = A[(long long)p * lda + q];
           double app = A[(long long)p * lda + p], aqq = A[(long long)q * lda + q];
           if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-            double theta = (aqq - app) / (2.0 * apq);
-            double t = (fabs(theta) > 1e150) ? 0.5 / theta
-                                             : copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
+            // the float64 pipe's divide and square root are slow: approximate
+            // reciprocals for the angle (any angle near the exact one keeps
+            // the quadratic convergence), c = rsqrt(1 + t^2), s = t c keeps
+            // the rotation orthogonal to rounding
+            double theta = (aqq - app) * rcp_approx(2.0 * apq);
+            double t = (fabs(theta) > 1e150) ? 0.5 * rcp_approx(theta)
+                                             : copysign(rcp_approx(fabs(theta) + sqrt(fma(theta, theta, 1.0))), theta);
+            c = rsqrt(fma(t, t, 1.0));
             s = t * c;
           }
         }
@@ -109,6 +125,14 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int n, double* A, int lda,
       __syncthreads();
     }
   }
+  return sweep;
+}
+
+__global__ void __launch_bounds__(1024) jacobi_kernel(int n, double* A, int lda, double* V, int ldv, double* w,
+                                                      int* info, int max_sweeps) {
+  extern __shared__ double sh[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int sweep = jacobi_sweeps(n, A, lda, V, ldv, sh, max_sweeps);
   // eigenvalues ascending (rank by value, ties by index); V columns permuted
   // through A as scratch
   double* wv = sh;                                   // reuse: n values
@@ -131,6 +155,49 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int n, double* A, int lda,
   for (int idx = tid; idx < n * n; idx += nt) {
     int i = idx / n, j = idx % n;
     V[(long long)i * ldv + rk[j]] = A[(long long)i * lda + j];
+  }
+  if (tid == 0 && info) *info = (sweep >= max_sweeps) ? 1 : 0;
+}
+
+// Small matrices (n <= kJacobiSmemMax): A and V staged in shared memory (odd
+// row stride n + 1 against bank conflicts), a 256-thread CTA; the same
+// rotations in the same order as the global-memory form.  The input A is left
+// unchanged.
+constexpr int kJacobiSmemMax = 64;
+
+__global__ void __launch_bounds__(256) jacobi_smem_kernel(int n, const double* __restrict__ A, int lda,
+                                                          double* __restrict__ V, int ldv, double* __restrict__ w,
+                                                          int* info, int max_sweeps) {
+  extern __shared__ double sh[];
+  const int ld = n + 1;
+  const int m = n + (n & 1);
+  double* As = sh;
+  double* Vs = As + (size_t)n * ld;
+  double* scratch = Vs + (size_t)n * ld;   // 2 (m / 2) doubles + 2 (m / 2) ints
+  int* rk = reinterpret_cast<int*>(scratch + 2 * m);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    As[i * ld + j] = A[(long long)i * lda + j];
+  }
+  __syncthreads();
+  const int sweep = jacobi_sweeps(n, As, ld, Vs, ld, scratch, max_sweeps);
+  __syncthreads();
+  // eigenvalues ascending (rank by value, ties by index), V columns permuted
+  for (int j = tid; j < n; j += nt) {
+    const double x = As[j * ld + j];
+    int r = 0;
+    for (int i = 0; i < n; ++i) {
+      const double y = As[i * ld + i];
+      r += (y < x) || (y == x && i < j);
+    }
+    rk[j] = r;
+    w[r] = x;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    V[(long long)i * ldv + rk[j]] = Vs[i * ld + j];
   }
   if (tid == 0 && info) *info = (sweep >= max_sweeps) ? 1 : 0;
 }
@@ -210,10 +277,25 @@ void jacobi_eig(cudaStream_t s, int n, double* A, int lda, double* V, int ldv, d
   if (n <= 0) return;
   if (n > 1024) throw Error(XS_EINVAL, "jacobi_eig: matrix larger than 1024");
   int m = n + (n & 1);
+  ProfScope ps(s, "jacobi_f64", 0.0, 0.0);
+  if (n <= kJacobiSmemMax) {
+    // A, V (n x (n + 1)), scratch 2m doubles (c, s, and the pair indices), n ranks
+    const size_t smem = sizeof(double) * (2 * (size_t)n * (n + 1) + 2 * m) + sizeof(int) * n;
+    static const bool attr = [] {   // once per process (thread-safe initialisation)
+      const size_t most = sizeof(double) * (2 * (size_t)kJacobiSmemMax * (kJacobiSmemMax + 1) + 2 * kJacobiSmemMax) +
+                          sizeof(int) * kJacobiSmemMax;
+      XS_CUDA(cudaFuncSetAttribute(jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(most)));
+      return true;
+    }();
+    (void)attr;
+    jacobi_smem_kernel<<<1, 256, smem, s>>>(n, A, lda, V, ldv, w, info, 60);
+    XS_CHECK_LAUNCH();
+    return;
+  }
   size_t smem = sizeof(double) * (2 * (m / 2)) + sizeof(int) * 2 * (m / 2);
   size_t smem2 = sizeof(double) * n + sizeof(int) * n;
   if (smem2 > smem) smem = smem2;
-  ProfScope ps(s, "jacobi_f64", 0.0, 0.0);
   jacobi_kernel<<<1, 1024, smem, s>>>(n, A, lda, V, ldv, w, info, 60);
   XS_CHECK_LAUNCH();
 }

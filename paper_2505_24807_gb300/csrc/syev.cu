@@ -7,9 +7,10 @@
 // costs ~640 cycles, so the kernel keeps float64 work in as few warps as hold
 // data and moves what can be approximate to float32:
 //   1. Householder tridiagonalisation Q^T A Q = T in float64 (shared memory
-//      when S <= kSmemMax, else global scratch); the reflectors go to global
-//      scratch, the matrix-vector product of each step is split over row
-//      segments, reductions run only in the warps that hold data;
+//      when S <= kSmemMax, else global scratch) on the lower triangle only
+//      (half the rank-2 update's float64 instructions); the reflectors go to
+//      global scratch, the matrix-vector product of each step is split over
+//      row segments, reductions run only in the warps that hold data;
 //   2. the k lowest eigenvalues of T by Sturm-count multisection in float32,
 //      one warp per eigenvalue and 32 counts per round, to ~2e-7 |T|;
 //   3. float64 inverse iteration on T (pivoted tridiagonal LU, one thread per
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(1024) syevk_kernel(int S, int k, const double*
       const bool sk = !(nx > 1e-300) || nx <= 1e-300 * scale_ref;
       const double al = sk ? x0 : ((x0 > 0.0) ? -nx : nx);
       scal[0] = al;
-      scal[1] = sk ? 0.0 : 1.0 / sqrt(2.0 * (sigma - x0 * al));
+      scal[1] = sk ? 0.0 : rsqrt(2.0 * (sigma - x0 * al));
       scal[2] = sk ? 1.0 : 0.0;
     }
     __syncthreads();
@@ -288,15 +289,18 @@ __global__ void __launch_bounds__(1024) syevk_kernel(int S, int k, const double*
     }
     __syncthreads();
     if (!skip) {
-      // p = B v (B symmetric: column i read by consecutive threads), split over
-      // nseg row segments, the segments summed in order
+      // p = B v, B symmetric and held as its lower triangle (B[i][l] read
+      // from row max(i, l)), split over nseg row segments summed in order
       const int nseg = min(kSeg, nt / m);
       const int len = (m + nseg - 1) / nseg;
       if (tid < nseg * m) {
         const int i = tid % m, g = tid / m;
         const int l1 = min(m, (g + 1) * len);
         double acc = 0.0;
-        for (int l = g * len; l < l1; ++l) acc = fma(a[(r0 + l) * ld + r0 + i], v[l], acc);
+        for (int l = g * len; l < l1; ++l) {
+          const int at = (l >= i) ? (r0 + l) * ld + r0 + i : (r0 + i) * ld + r0 + l;
+          acc = fma(a[at], v[l], acc);
+        }
         ps[g * m + i] = acc;
       }
       __syncthreads();
@@ -308,10 +312,11 @@ __global__ void __launch_bounds__(1024) syevk_kernel(int S, int k, const double*
       const double K = active_sum(kp, red, m);
       if (tid < m) p[tid] = 2.0 * pi - 2.0 * K * v[tid];   // w
       __syncthreads();
+      // rank-2 update of the lower triangle only: B -= v w^T + w v^T
       for (int i = warp; i < m; i += nwarp) {
         const double vi = v[i], wi = p[i];
         double* row = a + (r0 + i) * ld + r0;
-        for (int l = lane; l < m; l += 32) row[l] -= fma(vi, p[l], wi * v[l]);
+        for (int l = lane; l <= i; l += 32) row[l] = fma(-vi, p[l], fma(-wi, v[l], row[l]));
       }
     }
     if (tid == 0) {
@@ -498,30 +503,50 @@ __global__ void __launch_bounds__(1024) syevk_kernel(int S, int k, const double*
 }
 
 // a = L L^T (lower L, in place, lda), flag[0] = 1 when a pivot is not positive
+// Right-looking Cholesky on the lower triangle, one CTA: the matrix staged in
+// shared memory (row stride S + 1) when it fits, the column scaled by one
+// reciprocal per step, the trailing update one warp per row.
+constexpr int kCholSmemMax = 120;
+
+template <bool SMEM>
 __global__ void __launch_bounds__(1024) cholesky_kernel(int S, double* A, int lda, int* flag) {
-  __shared__ double piv;
+  extern __shared__ double sh[];
+  __shared__ double inv;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int j = 0; j < S; ++j) {
-    if (tid == 0) {
-      double x = A[(long long)j * lda + j];
-      if (!(x > 0.0)) { *flag = 1; x = 1e-300; }
-      piv = sqrt(x);
-      A[(long long)j * lda + j] = piv;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  const int ld = SMEM ? S + 1 : lda;
+  double* L = SMEM ? sh : A;
+  if (SMEM) {
+    for (int idx = tid; idx < S * S; idx += nt) {
+      const int i = idx / S, l = idx % S;
+      if (l <= i) L[i * ld + l] = A[(long long)i * lda + l];
     }
     __syncthreads();
-    for (int i = j + 1 + tid; i < S; i += nt) A[(long long)i * lda + j] /= piv;
+  }
+  for (int j = 0; j < S; ++j) {
+    if (tid == 0) {
+      double x = L[(long long)j * ld + j];
+      if (!(x > 0.0)) { *flag = 1; x = 1e-300; }
+      const double piv = sqrt(x);
+      L[(long long)j * ld + j] = piv;
+      inv = 1.0 / piv;
+    }
+    __syncthreads();
+    const double r = inv;
+    for (int i = j + 1 + tid; i < S; i += nt) L[(long long)i * ld + j] *= r;
     __syncthreads();
     // trailing update of the lower triangle
-    const int m = S - j - 1;
-    for (int idx = tid; idx < m * m; idx += nt) {
-      const int i = j + 1 + idx / m, l = j + 1 + idx % m;
-      if (l <= i) A[(long long)i * lda + l] -= A[(long long)i * lda + j] * A[(long long)l * lda + j];
+    for (int i = j + 1 + warp; i < S; i += nwarp) {
+      const double lij = L[(long long)i * ld + j];
+      double* row = L + (long long)i * ld;
+      for (int l = j + 1 + lane; l <= i; l += 32) row[l] = fma(-lij, L[(long long)l * ld + j], row[l]);
     }
     __syncthreads();
   }
   for (int idx = tid; idx < S * S; idx += nt) {
     const int i = idx / S, l = idx % S;
     if (l > i) A[(long long)i * lda + l] = 0.0;
+    else if (SMEM) A[(long long)i * lda + l] = L[i * ld + l];
   }
 }
 
@@ -544,12 +569,12 @@ void syevk(cudaStream_t s, int S, int k, const double* A, int lda, double* w, do
   ProfScope ps(s, "syevk_f64", 0.0, (4.0 / 3.0) * S * (double)S * S);
   if (S <= kSmemMax) {
     const size_t smem = sizeof(double) * wd;
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr = [&] {   // once per process (thread-safe initialisation)
       XS_CUDA(cudaFuncSetAttribute(syevk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    static_cast<int>(sizeof(double) * work_doubles(kSmemMax))));
-      attr = true;
-    }
+      return true;
+    }();
+    (void)attr;
     syevk_kernel<true><<<1, 1024, smem, s>>>(S, k, A, lda, w, Z, ldz, scratch.get(), info);
   } else {
     syevk_kernel<false><<<1, 1024, 0, s>>>(S, k, A, lda, w, Z, ldz, scratch.get(), info);
@@ -560,7 +585,18 @@ void syevk(cudaStream_t s, int S, int k, const double* A, int lda, double* w, do
 void cholesky(cudaStream_t s, int S, double* A, int lda, int* flag) {
   if (S <= 0) return;
   ProfScope ps(s, "cholesky_f64", 0.0, S * (double)S * S / 3.0);
-  cholesky_kernel<<<1, 1024, 0, s>>>(S, A, lda, flag);
+  if (S <= kCholSmemMax) {
+    const size_t smem = sizeof(double) * (size_t)S * (S + 1);
+    static const bool attr = [] {   // once per process (thread-safe initialisation)
+      XS_CUDA(cudaFuncSetAttribute(cholesky_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(sizeof(double) * kCholSmemMax * (kCholSmemMax + 1))));
+      return true;
+    }();
+    (void)attr;
+    cholesky_kernel<true><<<1, 1024, smem, s>>>(S, A, lda, flag);
+  } else {
+    cholesky_kernel<false><<<1, 1024, 0, s>>>(S, A, lda, flag);
+  }
   XS_CHECK_LAUNCH();
 }
 

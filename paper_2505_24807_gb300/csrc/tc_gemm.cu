@@ -18,6 +18,9 @@
 // accumulator back through a second barrier pair.  Every wait is bounded by the
 // global timer; a timeout sets the error word, the CTA skips the remaining
 // work, waits (bounded) for its issued copies and MMAs, frees TMEM and exits.
+#include <mutex>
+#include <unordered_map>
+
 #include "kernels.h"
 #include "prof.h"
 #include "tc_gemm.h"
@@ -31,10 +34,11 @@ using namespace tc5;
 
 constexpr int BM = 128;
 constexpr int BK = 32;       // 32 tf32 = 128 bytes = one swizzle atom row
-// stage ring depth: 3 stages of 64 KB for 128-wide tiles, 2 of 96 KB for
-// 256-wide tiles (which halve the A-tile re-reads per flop)
+// stage ring depth: 4 stages of 48 KB for 64-wide tiles, 3 of 64 KB for
+// 128-wide tiles, 2 of 96 KB for 256-wide tiles (which halve the A-tile
+// re-reads per flop)
 template <int BN>
-__host__ __device__ constexpr int stages_for() { return BN >= 256 ? 2 : 3; }
+__host__ __device__ constexpr int stages_for() { return BN >= 256 ? 2 : (BN >= 128 ? 3 : 4); }
 
 __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y, int z,
                                          int rank3) {
@@ -263,6 +267,37 @@ __global__ void split_pad_kernel(int rows, int cols, int ld_dst, const S* __rest
   lo[b * dstride + idx] = l;
 }
 
+// transposing form for float64 sources through 32 x 32 shared-memory tiles
+// (coalesced on both sides): dst[r][c] = split(src[c][r]) for c < cols, zero
+// for cols <= c < ld_dst; src holds cols rows of row stride ld_src
+__global__ void split_pad_t_kernel(int rows, int cols, int ld_dst, const double* __restrict__ src, int ld_src,
+                                   long long sstride, long long dstride, float* __restrict__ hi,
+                                   float* __restrict__ lo) {
+  __shared__ double t[32][33];
+  const int b = blockIdx.z;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const double* sb = src + b * sstride;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    t[k][threadIdx.x] = (c < cols && r < rows) ? sb[(long long)c * ld_src + r] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r >= rows || c >= ld_dst) continue;
+    const double x = t[threadIdx.x][k];
+    float h = 0.0f, l = 0.0f;
+    if (c < cols) {
+      const uint32_t bits = __float_as_uint(static_cast<float>(x));
+      h = __uint_as_float((bits + 0x1000u) & 0xFFFFE000u);
+      l = static_cast<float>(x - static_cast<double>(h));
+    }
+    const long long at = b * dstride + (long long)r * ld_dst + c;
+    hi[at] = h;
+    lo[at] = l;
+  }
+}
+
 // rows x kpad float32 matrix (row stride ld floats), batch entries bstride apart
 CUtensorMap make_map(const float* ptr, int rows, int kpad, int ld, int batch, long long bstride, int box_rows) {
   CUtensorMap m;
@@ -301,34 +336,48 @@ void split_pad(cudaStream_t s, int rows, int cols, int ld_dst, const S* src, int
 }
 template void split_pad<double>(cudaStream_t, int, int, int, const double*, int, long long, long long, int, bool,
                                 float*, float*);
+
+void split_pad_t(cudaStream_t s, int rows, int cols, int ld_dst, const double* src, int ld_src, long long sstride,
+                 long long dstride, int batch, float* hi, float* lo) {
+  if (rows <= 0 || batch <= 0) return;
+  dim3 grid(static_cast<unsigned>((ld_dst + 31) / 32), static_cast<unsigned>((rows + 31) / 32), batch);
+  split_pad_t_kernel<<<grid, dim3(32, 8), 0, s>>>(rows, cols, ld_dst, src, ld_src, sstride, dstride, hi, lo);
+  XS_CHECK_LAUNCH();
+}
 template void split_pad<float>(cudaStream_t, int, int, int, const float*, int, long long, long long, int, bool,
                                float*, float*);
 
 namespace {
 
+int sm_count() {
+  static const int nsm = [] {
+    int dev = 0, count = 0;
+    XS_CUDA(cudaGetDevice(&dev));
+    XS_CUDA(cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev));
+    return count;
+  }();
+  return nsm;
+}
+
 template <int BNv>
 void launch_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int N, int Kpad, int batch,
                const TcEpilogue& e, int* d_err) {
+  static_assert(BNv == 64 || BNv == 128 || BNv == 256, "tile width");
   const CUtensorMap ah = make_map(A.hi, M, Kpad, A.ld, A.batched ? batch : 1, A.bstride, BM);
   const CUtensorMap al = make_map(A.lo, M, Kpad, A.ld, A.batched ? batch : 1, A.bstride, BM);
   const CUtensorMap bh = make_map(B.hi, N, Kpad, B.ld, B.batched ? batch : 1, B.bstride, BNv);
   const CUtensorMap bl = make_map(B.lo, N, Kpad, B.ld, B.batched ? batch : 1, B.bstride, BNv);
   EpiArgs ep{e.mode, e.D, e.Dlo, e.Y, e.X, e.eps, e.ld, e.bstride, e.o};
   const size_t smem = smem_bytes<BNv>();
-  static bool attr_set = false;
-  if (!attr_set) {
+  static const bool attr_set = [smem] {   // once per process (thread-safe initialisation)
     XS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BNv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem)));
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   const int ntm = (M + BM - 1) / BM, ntn = (N + BNv - 1) / BNv;
   const int ntiles = ntm * ntn * batch;
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    XS_CUDA(cudaGetDevice(&dev));
-    XS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  }
+  const int nsm = sm_count();
   const int grid = ntiles < nsm ? ntiles : nsm;   // persistent: one CTA per SM
   ProfScope ps(s, "tc_gemm_tf32x3", 0.0, 2.0 * 3.0 * M * N * (double)Kpad * batch);
   tc_gemm_kernel<BNv><<<grid, 192, smem, s>>>(ah, al, bh, bl, M, N, Kpad, A.batched && batch > 1 ? 1 : 0,
@@ -338,11 +387,88 @@ void launch_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, in
 
 }  // namespace
 
+namespace {
+
+void launch_bn(int bn, cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int N, int Kpad, int batch,
+               const TcEpilogue& e, int* d_err) {
+  if (bn == 256) launch_tc<256>(s, A, B, M, N, Kpad, batch, e, d_err);
+  else if (bn == 128) launch_tc<128>(s, A, B, M, N, Kpad, batch, e, d_err);
+  else launch_tc<64>(s, A, B, M, N, Kpad, batch, e, d_err);
+}
+
+// Estimated time of a launch with tile width bn, in units of one wave of
+// 256-wide tiles: waves of persistent CTAs times the relative cost of a tile
+// (a narrower tile runs shorter MMAs but re-reads the A tile more often).
+double tile_estimate(int bn, int M, int N, int batch) {
+  const long long tiles = (long long)((M + BM - 1) / BM) * ((N + bn - 1) / bn) * batch;
+  const long long waves = (tiles + sm_count() - 1) / sm_count();
+  const double cost = bn == 256 ? 1.0 : (bn == 128 ? 0.6 : 0.4);
+  return waves * cost;
+}
+
+// Tile width per problem: the first launch of a (M, N, K, batch, epilogue)
+// class times every width whose estimate is within 1.5x of the best estimate
+// (each candidate writes the same output, so the real launch is the timing
+// run) and keeps the fastest for the process; calls inside stream capture and
+// from allocation-free entry points take the best estimate.
+std::mutex g_tc_mutex;
+std::unordered_map<unsigned long long, int> g_tc_tuned;
+
+}  // namespace
+
 void tc_gemm(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int N, int Kpad, int batch,
              const TcEpilogue& e, int* d_err) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
-  if (N >= 512) launch_tc<256>(s, A, B, M, N, Kpad, batch, e, d_err);
-  else launch_tc<128>(s, A, B, M, N, Kpad, batch, e, d_err);
+  constexpr int kWidths[3] = {256, 128, 64};
+  double est[3], best_est = 1e300;
+  int guess = 256;
+  for (int j = 0; j < 3; ++j) {
+    est[j] = tile_estimate(kWidths[j], M, N, batch);
+    if (est[j] < best_est) { best_est = est[j]; guess = kWidths[j]; }
+  }
+  const bool keyable = M < (1 << 16) && N < (1 << 16) && Kpad < (1 << 16) && batch < (1 << 10);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (!keyable || tuning_disabled() || cudaStreamIsCapturing(s, &cap) != cudaSuccess ||
+      cap != cudaStreamCaptureStatusNone) {
+    launch_bn(guess, s, A, B, M, N, Kpad, batch, e, d_err);
+    return;
+  }
+  const unsigned long long key = (unsigned long long)M | ((unsigned long long)N << 16) |
+                                 ((unsigned long long)Kpad << 32) | ((unsigned long long)batch << 48) |
+                                 ((unsigned long long)(e.mode & 3) << 58) |
+                                 ((unsigned long long)(A.batched ? 1 : 0) << 60) |
+                                 ((unsigned long long)(B.batched ? 1 : 0) << 61);
+  {
+    std::lock_guard<std::mutex> lock(g_tc_mutex);
+    auto it = g_tc_tuned.find(key);
+    if (it != g_tc_tuned.end()) {
+      launch_bn(it->second, s, A, B, M, N, Kpad, batch, e, d_err);
+      return;
+    }
+  }
+  cudaEvent_t e0, e1;
+  XS_CUDA(cudaEventCreate(&e0));
+  XS_CUDA(cudaEventCreate(&e1));
+  int best = guess;
+  float best_ms = 1e30f;
+  for (int j = 0; j < 3; ++j) {
+    if (est[j] > 1.5 * best_est) continue;
+    launch_bn(kWidths[j], s, A, B, M, N, Kpad, batch, e, d_err);   // warm-up (first launch sets attributes)
+    XS_CUDA(cudaEventRecord(e0, s));
+    launch_bn(kWidths[j], s, A, B, M, N, Kpad, batch, e, d_err);
+    XS_CUDA(cudaEventRecord(e1, s));
+    XS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    XS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = kWidths[j];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lock(g_tc_mutex);
+  g_tc_tuned[key] = best;
 }
 
 }  // namespace xs

@@ -43,6 +43,12 @@ template <typename S>
 void split_pad(cudaStream_t s, int rows, int cols, int ld_dst, const S* src, int ld_src, long long sstride,
                long long dstride, int batch, bool transpose, float* hi, float* lo);
 
+// Transposed split of float64 matrices through shared-memory tiles:
+// dst[r][c] (rows x ld_dst) = TF32 pair of src[c][r] for c < cols, zero up to
+// ld_dst; src holds cols rows of row stride ld_src; batched over grid.z.
+void split_pad_t(cudaStream_t s, int rows, int cols, int ld_dst, const double* src, int ld_src, long long sstride,
+                 long long dstride, int batch, float* hi, float* lo);
+
 int pad32(int k);
 
 }  // namespace xs

@@ -61,6 +61,28 @@ def test_products_match_oracle(small_case, kind, okind, precision):
     assert rel_err(Y, ref) < tol
 
 
+@pytest.mark.parametrize("kind,okind", [(0, "A"), (1, "ApB"), (2, "AmB")])
+def test_mixed_products_hydrocarbon(kind, okind):
+    """An alkane has nocc == nvir, so the mixed path builds R = C_occ X C_vir^T
+    contracting its n x n product over nocc (molecules with N or O, nvir <
+    nocc, contract over nvir): the other branch of the contraction order."""
+    from oracle import excited
+    params = molgen.make_params(0)
+    Z, xyz = molgen.make_chain(3, 12, 26)
+    mol, ints, res = oracle_ground_state(Z, xyz, params)
+    assert mol.nocc == mol.nvir
+    ctx = context(params)
+    try:
+        xs.xs_ground_state(ctx.h, [(Z, xyz)])
+        xs.xs_set_orbitals(ctx.h, 0, res.C, res.eps)
+        X = molgen.trial_vectors(9, 3, mol.nocc, mol.nvir)
+        Y = xs.xs_apply(ctx.h, 0, kind, X.reshape(3, -1), precision=1).reshape(X.shape)
+        ref = excited.apply_kind(mol, ints, res.C, res.eps, mol.nocc, X, okind)
+        assert rel_err(Y, ref) < 3e-5
+    finally:
+        ctx.close()
+
+
 @pytest.mark.parametrize("method", ["CIS", "RPA"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_roots_match_bruteforce(small_case, method, precision):
