@@ -33,9 +33,9 @@ namespace {
 __device__ __forceinline__ int pidx(int a, int b) {
   // product index of AOs a, b (0 = s, 1..3 = p) on a heavy atom
   const int lo = a < b ? a : b, hi = a < b ? b : a;
-  // rows: s: 0 1 2 3 | x: 4 5 6 | y: 7 8 | z: 9
-  const int base[4] = {0, 4, 7, 9};
-  return base[lo] + (hi - lo);
+  // rows: s: 0 1 2 3 | x: 4 5 6 | y: 7 8 | z: 9; row lo starts at
+  // lo (9 - lo) / 2 = 0, 4, 7, 9 (arithmetic: no local-memory table)
+  return ((lo * (9 - lo)) >> 1) + (hi - lo);
 }
 
 // product vectors of the diagonal atom blocks: r[q][v] (TR = false) or its
@@ -103,9 +103,14 @@ __device__ __forceinline__ void one_centre(const T* p, int a, int b, const T Rd[
 // up to 4 consecutive hydrogens) and one column tile (whole atoms, at most 64
 // AOs).  It stages the pair-integral block W[products of the rows' atoms]
 // [products of the columns' atoms] in shared memory once and then streams the
-// nvec matrices: per matrix, R's tile (and for TDHF its transpose tile) goes
-// through shared memory and every thread writes one G (and G-) element.
+// nvec matrices in groups of GV: per matrix, R's tile (and for TDHF its
+// transpose tile) goes through shared memory and every thread writes one G
+// (and G-) element.  The next group's tiles are loaded into registers while
+// the current group is computed, so each thread keeps GV loads in flight (the
+// loads are 4-byte elements: one matrix at a time left HBM mostly idle).
 constexpr int kGR = 4, kGC = 64, kGP = 10, kGQ = 160;
+template <typename T>
+__host__ __device__ constexpr int gv_for() { return sizeof(T) == 4 ? 4 : 1; }   // float32: 4 matrices per group (shared memory)
 
 // TF32 pair of a float (hi rounded to TF32, lo = x - hi exact): the split
 // epilogue writes the tensor-core operand of the back-transform directly
@@ -138,28 +143,28 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
                                                     const GOut<T> out) {
   // R tiles padded by 4 rows / columns of zeros: a hydrogen's block is
   // handled as a 4 x 4 block with zero weights past its single AO
-  // double-buffered: matrix v is read from one buffer while v + 1 is stored
-  // into the other from registers loaded before the compute
+  // double-buffered groups: group g is read from one buffer while group g + 1
+  // is stored into the other from registers loaded before the compute
+  constexpr int GV = gv_for<T>();
   __shared__ T Ws[kGP][kGQ + 1];
-  __shared__ T Rt[2][kGR + 4][kGC + 4];
-  __shared__ T Rtt[2][kGC + 4][kGR + 5];   // odd row stride: the rows of different atoms hit different banks
+  __shared__ T Rt[2][GV][kGR + 4][kGC + 4];
+  __shared__ T Rtt[2][GV][kGC + 4][kGR + 5];   // odd row stride: the rows of different atoms hit different banks
   const int4 rg = rows[blockIdx.y], ct = cols[blockIdx.x];
   const int ra = rg.x, nr = rg.y, cb = ct.x, nc = ct.y;
   const int PA0 = atom_prod_off[rg.z], PB0 = atom_prod_off[ct.z];
   const int nPA = atom_prod_off[rg.w - 1] + (atom_nao[rg.w - 1] == 4 ? 10 : 1) - PA0;
   const int nPB = atom_prod_off[ct.w - 1] + (atom_nao[ct.w - 1] == 4 ? 10 : 1) - PB0;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < nPA * nPB; idx += blockDim.x) {
-    const int pr = idx / nPB, pc = idx % nPB;
-    Ws[pr][pc] = W[(long long)(PA0 + pr) * np + PB0 + pc];
-  }
-  for (int idx = tid; idx < 2 * (kGR + 4) * (kGC + 4); idx += blockDim.x) (&Rt[0][0][0])[idx] = T(0);
-  for (int idx = tid; idx < 2 * (kGC + 4) * (kGR + 5); idx += blockDim.x) (&Rtt[0][0][0])[idx] = T(0);
+  // one warp per pair-integral row, lanes along the row (no integer division)
+  for (int pr = tid >> 5; pr < nPA; pr += blockDim.x >> 5)
+    for (int pc = tid & 31; pc < nPB; pc += 32) Ws[pr][pc] = W[(long long)(PA0 + pr) * np + PB0 + pc];
+  for (int idx = tid; idx < 2 * GV * (kGR + 4) * (kGC + 4); idx += blockDim.x) (&Rt[0][0][0][0])[idx] = T(0);
+  for (int idx = tid; idx < 2 * GV * (kGC + 4) * (kGR + 5); idx += blockDim.x) (&Rtt[0][0][0][0])[idx] = T(0);
   const int ri = tid / kGC, ci = tid % kGC;
   const bool active = ri < nr && ci < nc;
   const int mu = ra + ri, lam = cb + ci;
   int A = 0, B = 0, a = 0, b = 0, nA = 1, nB = 1, rA = 0, cA = 0, rB = 0, pA = 0, pB = 0, PA = 0;
-  T p[XS_NPARAM];
+  const double* pd = par;   // the diagonal block's element parameters (read where used)
   if (active) {
     A = ao_atom[mu]; B = ao_atom[lam];
     a = ao_local[mu]; b = ao_local[lam];
@@ -170,11 +175,7 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
     PA = atom_prod_off[A];
     pA = PA - PA0;
     pB = atom_prod_off[B] - PB0;
-    if (A == B) {
-      const double* pd = par + atom_elem[A] * XS_NPARAM;
-#pragma unroll
-      for (int i = 0; i < XS_NPARAM; ++i) p[i] = T(pd[i]);
-    }
+    if (A == B) pd = par + atom_elem[A] * XS_NPARAM;
   }
   __syncthreads();
   // this output's 16 exchange weights (mu nu|lam sig) for nu in A, sig in B,
@@ -192,35 +193,52 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
   }
   const int tr = tid % kGR, tc = tid / kGR;   // transpose tile: 4 consecutive threads per row
   const bool tact = (MODE == G_RPA) && tr < nr && tc < nc;
+  const long long nn = (long long)n * n;
+  const long long at_r = (long long)mu * n + lam, at_t = (long long)(cb + tc) * n + ra + tr;
   __syncthreads();
-  if (nvec > 0) {
-    if (active) Rt[0][ri][ci] = Rall[(long long)mu * n + lam];
-    if (tact) Rtt[0][tc][tr] = Rall[(long long)(cb + tc) * n + ra + tr];
+#pragma unroll
+  for (int q = 0; q < GV; ++q) {
+    if (q < nvec) {
+      if (active) Rt[0][q][ri][ci] = Rall[q * nn + at_r];
+      if (tact) Rtt[0][q][tc][tr] = Rall[q * nn + at_t];
+    }
   }
   __syncthreads();
   int buf = 0;
-  for (int v = 0; v < nvec; ++v) {
-    // prefetch matrix v + 1 into registers
-    T nxt = T(0), nxtt = T(0);
-    if (v + 1 < nvec) {
-      const T* Rn = Rall + (long long)(v + 1) * n * n;
-      if (active) nxt = Rn[(long long)mu * n + lam];
-      if (tact) nxtt = Rn[(long long)(cb + tc) * n + ra + tr];
+  for (int v0 = 0; v0 < nvec; v0 += GV) {
+    // prefetch the next group into registers
+    T nxt[GV], nxtt[GV];
+#pragma unroll
+    for (int q = 0; q < GV; ++q) {
+      nxt[q] = T(0);
+      nxtt[q] = T(0);
+      const int vn = v0 + GV + q;
+      if (vn < nvec) {
+        if (active) nxt[q] = Rall[vn * nn + at_r];
+        if (tact) nxtt[q] = Rall[vn * nn + at_t];
+      }
     }
-    if (active) {
+#pragma unroll
+    for (int q = 0; q < GV; ++q) {
+      const int v = v0 + q;
+      if (!active || v >= nvec) continue;
       T g, gm = T(0);
       if (A == B) {
         T J1, K1ab, K1ba;
         if (nA == 1) {
-          const T r00 = Rt[buf][rA][cA];
-          J1 = p[4] * r00;
-          K1ab = K1ba = p[4] * r00;
+          const T r00 = Rt[buf][q][rA][cA];
+          const T gss = T(pd[4]);
+          J1 = gss * r00;
+          K1ab = K1ba = gss * r00;
         } else {
           T Rd[16];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) Rd[i * 4 + j] = Rt[buf][rA + i][cA + j];
+            for (int j = 0; j < 4; ++j) Rd[i * 4 + j] = Rt[buf][q][rA + i][cA + j];
+          T p[XS_NPARAM];
+#pragma unroll
+          for (int i = 0; i < XS_NPARAM; ++i) p[i] = (i >= 4 && i <= 8) ? T(pd[i]) : T(0);
           one_centre<T>(p, a, b, Rd, J1, K1ab, K1ba);
         }
         const int pab = (nA == 4) ? pidx(a, b) : 0;
@@ -233,15 +251,36 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
         }
       } else {
         // K(R)_{mu lam} = sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig},
-        // K(R^T)_{mu lam} = sum (mu nu|lam sig) R_{sig nu}
+        // K(R^T)_{mu lam} = sum (mu nu|lam sig) R_{sig nu}; a hydrogen has
+        // one AO, so only the nonzero weights are visited (warps are nearly
+        // always uniform in the atom kinds: heavy atoms precede hydrogens in
+        // the AO order of the generated molecules).  The terms come in the
+        // same order as in the full 4 x 4 sum, so the result is identical.
         T kr = T(0), krt = T(0);
+        if (nA == 4 && nB == 4) {
 #pragma unroll
-        for (int nu = 0; nu < 4; ++nu)
+          for (int nu = 0; nu < 4; ++nu)
+#pragma unroll
+            for (int sg = 0; sg < 4; ++sg) {
+              kr = fma(wv[nu * 4 + sg], Rt[buf][q][rA + nu][rB + sg], kr);
+              if (MODE == G_RPA) krt = fma(wv[nu * 4 + sg], Rtt[buf][q][rB + sg][rA + nu], krt);
+            }
+        } else if (nA == 4) {
+#pragma unroll
+          for (int nu = 0; nu < 4; ++nu) {
+            kr = fma(wv[nu * 4], Rt[buf][q][rA + nu][rB], kr);
+            if (MODE == G_RPA) krt = fma(wv[nu * 4], Rtt[buf][q][rB][rA + nu], krt);
+          }
+        } else if (nB == 4) {
 #pragma unroll
           for (int sg = 0; sg < 4; ++sg) {
-            kr = fma(wv[nu * 4 + sg], Rt[buf][rA + nu][rB + sg], kr);
-            if (MODE == G_RPA) krt = fma(wv[nu * 4 + sg], Rtt[buf][rB + sg][rA + nu], krt);
+            kr = fma(wv[sg], Rt[buf][q][rA][rB + sg], kr);
+            if (MODE == G_RPA) krt = fma(wv[sg], Rtt[buf][q][rB + sg][rA], krt);
           }
+        } else {
+          kr = fma(wv[0], Rt[buf][q][rA][rB], kr);
+          if (MODE == G_RPA) krt = fma(wv[0], Rtt[buf][q][rB][rA], krt);
+        }
         if (MODE == G_CIS) {
           g = -kr;
         } else {
@@ -261,13 +300,16 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
           out.Gml[at] = l;
         }
       } else {
-        out.G[(long long)v * n * n + (long long)mu * n + lam] = g;
-        if (MODE == G_RPA) out.Gm[(long long)v * n * n + (long long)mu * n + lam] = gm;
+        out.G[v * nn + at_r] = g;
+        if (MODE == G_RPA) out.Gm[v * nn + at_r] = gm;
       }
     }
-    if (v + 1 < nvec) {
-      if (active) Rt[buf ^ 1][ri][ci] = nxt;
-      if (tact) Rtt[buf ^ 1][tc][tr] = nxtt;
+    if (v0 + GV < nvec) {
+#pragma unroll
+      for (int q = 0; q < GV; ++q) {
+        if (active) Rt[buf ^ 1][q][ri][ci] = nxt[q];
+        if (tact) Rtt[buf ^ 1][q][tc][tr] = nxtt[q];
+      }
     }
     __syncthreads();
     buf ^= 1;

@@ -341,23 +341,38 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(int nvec, long long L, co
   const long long l0 = static_cast<long long>(blockIdx.x) * kSliceL;
   const int r0 = blockIdx.y * kSliceR;
   const int nr = min(kSliceR, nvec - r0);
-  for (int item = threadIdx.x; item < nr * kSliceL; item += blockDim.x) {
-    const int r = item / kSliceL, li = item % kSliceL;
+  // each thread splits two consecutive amplitudes, so every tn plane gets one
+  // 4-byte store per pair (Lp and the pair's first index are even)
+  constexpr int kPairs = kSliceL / 2;
+  for (int item = threadIdx.x; item < nr * kPairs; item += blockDim.x) {
+    const int r = item / kPairs, li = 2 * (item % kPairs);
     const long long l = l0 + li;
     const int rv = r0 + r;
-    int d[kOzDigits];
+    int d0[kOzDigits], d1[kOzDigits];
+    const double* xr = X + static_cast<size_t>(rv) * ldx;
     if (l < L) {
-      oz_digits(X[static_cast<size_t>(rv) * ldx + l], e[rv], d);
+      oz_digits(xr[l], e[rv], d0);
     } else {
 #pragma unroll
-      for (int i = 0; i < kOzDigits; ++i) d[i] = 0;
+      for (int i = 0; i < kOzDigits; ++i) d0[i] = 0;
+    }
+    if (l + 1 < L) {
+      oz_digits(xr[l + 1], e[rv], d1);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kOzDigits; ++i) d1[i] = 0;
     }
     if (tn && l < Lp) {
 #pragma unroll
-      for (int i = 0; i < kOzDigits; ++i)
-        tn[(static_cast<size_t>(tn_r0 + rv) * kOzDigits + i) * Lp + l] = static_cast<oz_t>(digit_bits(d[i]));
+      for (int i = 0; i < kOzDigits; ++i) {
+        const uint32_t two = static_cast<uint32_t>(digit_bits(d0[i])) | (static_cast<uint32_t>(digit_bits(d1[i])) << 16);
+        *reinterpret_cast<uint32_t*>(tn + (static_cast<size_t>(tn_r0 + rv) * kOzDigits + i) * Lp + l) = two;
+      }
     }
-    if (nn) tile[r][li] = pack8(d);
+    if (nn) {
+      tile[r][li] = pack8(d0);
+      tile[r][li + 1] = pack8(d1);
+    }
   }
   if (!nn) return;
   __syncthreads();

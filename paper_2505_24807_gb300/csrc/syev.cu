@@ -258,20 +258,33 @@ __global__ void __launch_bounds__(1024) syevk_kernel(int S, int k, const double*
       const double x = a[(r0 + tid) * ld + j];
       part = x * x;
     }
-    const double sigma = active_sum(part, red, m);
-    // the step's scalars in one thread (float64 instructions in every warp
-    // would cost 32 times as much), broadcast through shared memory
-    if (tid == 0) {
-      const double x0 = a[r0 * ld + j];
-      const double nx = sqrt(sigma);
-      const double scale_ref = fabs(a[j * ld + j]) + nx;
-      const bool sk = !(nx > 1e-300) || nx <= 1e-300 * scale_ref;
-      const double al = sk ? x0 : ((x0 > 0.0) ? -nx : nx);
-      scal[0] = al;
-      scal[1] = sk ? 0.0 : rsqrt(2.0 * (sigma - x0 * al));
-      scal[2] = sk ? 1.0 : 0.0;
+    // column norm; the final reduction's lane forms the step's scalars (in
+    // one thread: float64 instructions in every warp would cost 32 times as
+    // much) and broadcasts them through shared memory
+    {
+      const int nw = (m + 31) >> 5;
+      if (warp < nw) {
+        part = warp_sum(part);
+        if (lane == 0) red[warp] = part;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double y = lane < nw ? red[lane] : 0.0;
+        if (nw > 1) y = warp_sum(y);
+        if (lane == 0) {
+          const double sigma = y;
+          const double x0 = a[r0 * ld + j];
+          const double nx = sqrt(sigma);
+          const double scale_ref = fabs(a[j * ld + j]) + nx;
+          const bool sk = !(nx > 1e-300) || nx <= 1e-300 * scale_ref;
+          const double al = sk ? x0 : ((x0 > 0.0) ? -nx : nx);
+          scal[0] = al;
+          scal[1] = sk ? 0.0 : rsqrt(2.0 * (sigma - x0 * al));
+          scal[2] = sk ? 1.0 : 0.0;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
     const bool skip = scal[2] != 0.0;
     const double alpha = scal[0];
     double* Rj = R + (size_t)j * S;
@@ -283,12 +296,7 @@ __global__ void __launch_bounds__(1024) syevk_kernel(int S, int k, const double*
         v[tid] = vi;
         Rj[tid] = vi;
       }
-    } else if (tid < m) {
-      v[tid] = 0.0;
-      Rj[tid] = 0.0;
-    }
-    __syncthreads();
-    if (!skip) {
+      __syncthreads();
       // p = B v, B symmetric and held as its lower triangle (B[i][l] read
       // from row max(i, l)), split over nseg row segments summed in order
       const int nseg = min(kSeg, nt / m);
@@ -318,6 +326,9 @@ __global__ void __launch_bounds__(1024) syevk_kernel(int S, int k, const double*
         double* row = a + (r0 + i) * ld + r0;
         for (int l = lane; l <= i; l += 32) row[l] = fma(-vi, p[l], fma(-wi, v[l], row[l]));
       }
+    } else if (tid < m) {
+      v[tid] = 0.0;
+      Rj[tid] = 0.0;
     }
     if (tid == 0) {
       d[j] = a[j * ld + j];

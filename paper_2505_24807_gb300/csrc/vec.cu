@@ -25,24 +25,28 @@ __global__ void diag_term_kernel(int nvec, int o, int v, const double* __restric
 // The preconditioned residual is only a search direction (it is
 // re-orthogonalised in float64 afterwards), so the denominator and its
 // reciprocal are formed in float32: the float64 divide costs ~640 cycles on
-// this part.  Orbital energies are staged as float32 in shared memory.
-__global__ void precond_kernel(int n, int o, int v, const double* __restrict__ eps,
+// this part.  Orbital energies and the nvec Ritz values are staged as float32
+// in shared memory once per CTA; each thread forms its amplitude's gap and
+// shift once and serves every vector (a few CTAs per SM, grid-stride).
+__global__ void precond_kernel(int n, int o, int v, int nvec, const double* __restrict__ eps,
                                const double* __restrict__ omega, const double* __restrict__ R,
                                double* __restrict__ Tt, const double* __restrict__ shift) {
-  extern __shared__ float epsf[];
+  extern __shared__ float epsf[];   // n orbital energies, then nvec Ritz values
+  float* omf = epsf + n;
   for (int p = threadIdx.x; p < n; p += blockDim.x) epsf[p] = static_cast<float>(eps[p]);
+  for (int k = threadIdx.x; k < nvec; k += blockDim.x) omf[k] = static_cast<float>(omega[k]);
   __syncthreads();
-  const int k = blockIdx.y;
-  const int ov = o * v;
-  const float om = static_cast<float>(omega[k]);
-  const double* Rk = R + (long long)k * ov;
-  double* Tk = Tt + (long long)k * ov;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ov; e += gridDim.x * blockDim.x) {
-    const int i = e / v, a = e - i * v;
-    float d = om - (epsf[o + a] - epsf[i]);
-    if (shift) d -= static_cast<float>(shift[e]);
-    if (fabsf(d) < 1e-4f) d = (d < 0.0f) ? -1e-4f : 1e-4f;
-    Tk[e] = Rk[e] * static_cast<double>(__frcp_rn(d));
+  const long long ov = (long long)o * v;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ov; e += (long long)gridDim.x * blockDim.x) {
+    const int i = static_cast<int>(e / v), a = static_cast<int>(e - (long long)i * v);
+    const float gap = epsf[o + a] - epsf[i];
+    const float sh = shift ? static_cast<float>(shift[e]) : 0.0f;
+    for (int k = 0; k < nvec; ++k) {
+      float d = omf[k] - gap;
+      if (shift) d -= sh;
+      if (fabsf(d) < 1e-4f) d = (d < 0.0f) ? -1e-4f : 1e-4f;
+      Tt[(long long)k * ov + e] = R[(long long)k * ov + e] * static_cast<double>(__frcp_rn(d));
+    }
   }
 }
 
@@ -166,9 +170,15 @@ void precondition(cudaStream_t s, int nvec, int o, int v, const double* eps, con
   long long n = (long long)nvec * o * v;
   if (n == 0) return;
   const int nao = o + v;
-  if (nao > 12000) throw Error(XS_EINVAL, "precondition: more than 12000 orbitals");
-  const int bx = static_cast<int>(std::min<long long>(1024, ((long long)o * v + 255) / 256));
-  precond_kernel<<<dim3(bx, nvec), 256, sizeof(float) * nao, s>>>(nao, o, v, eps, omega, R, T, shift);
+  if (nao + nvec > 12000) throw Error(XS_EINVAL, "precondition: more than 12000 orbitals and vectors");
+  static const int nsm = [] {
+    int dev = 0, count = 0;
+    XS_CUDA(cudaGetDevice(&dev));
+    XS_CUDA(cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev));
+    return count;
+  }();
+  const int bx = static_cast<int>(std::min<long long>(4LL * nsm, ((long long)o * v + 255) / 256));
+  precond_kernel<<<bx, 256, sizeof(float) * (nao + nvec), s>>>(nao, o, v, nvec, eps, omega, R, T, shift);
   XS_CHECK_LAUNCH();
 }
 
