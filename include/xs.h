@@ -254,8 +254,12 @@ int xs_subspace_combine(xs_ctx* ctx, int nb, int S, int nout, long long L, const
  * the launching stream; xs_profile(ctx, 0) disables it.  xs_profile_read
  * synchronises the context's stream and copies up to max_entries entries
  * (one per kernel name: launches, summed device milliseconds, summed
- * algorithmic bytes and flops) and the number of entries into *count.  No
- * counterpart in the paper (measurement plumbing). */
+ * algorithmic bytes and flops) and the number of entries into *count.
+ * Entries named "host:<phase>" hold host wall milliseconds of the excited-
+ * state solver's phases instead (setup, learned_guess, loop, finish; fetch_wait and
+ * sync_wait: time blocked on the device; launches = times entered), and
+ * "all_launches" counts every kernel launch of the library.  No counterpart
+ * in the paper (measurement plumbing). */
 typedef struct {
   char name[32];
   int launches;

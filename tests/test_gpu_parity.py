@@ -111,6 +111,28 @@ def test_roots_match_bruteforce(small_case, method, precision):
     assert out["info"]["converged"] == 1
 
 
+@pytest.mark.parametrize("method", ["CIS", "RPA"])
+def test_many_roots_match_bruteforce(small_case, method):
+    """33 roots: the new-block Gram matrices (up to 66 x 66 for TDHF) take the
+    global-memory Jacobi, the subspace (up to 16 x 33) the global-memory
+    eigensolver and Cholesky -- the paths beyond the shared-memory sizes."""
+    from oracle import excited, nddo
+    c = small_case
+    mol, res = c["mol"], c["res"]
+    eri = nddo.full_eri(mol, c["ints"])
+    A, B = excited.explicit_AB(res.eps, res.C, mol.nocc, eri)
+    k = 33
+    w = excited.cis_bruteforce(A, k)[0] if method == "CIS" else excited.rpa_bruteforce(A, B, k)[0]
+    ctx = context(c["params"])
+    try:
+        xs.xs_ground_state(ctx.h, [(c["Z"], c["xyz"])])
+        out = xs.xs_excited(ctx.h, method=xs.XS_CIS if method == "CIS" else xs.XS_TDHF, nroots=k, tol=1e-6)
+    finally:
+        ctx.close()
+    assert np.abs(out["omega"][0] - w).max() < 1e-6
+    assert out["info"]["converged"] == 1
+
+
 def test_amplitudes_normalised(small_case):
     c = small_case
     ctx = context(c["params"])
