@@ -32,7 +32,9 @@ struct TcEpilogue {
 
 // D[b] (M x N) = A[b] B[b]^T from TF32 pairs: hi*hi + hi*lo + lo*hi, float32
 // accumulation.  d_err: device int set to a nonzero code when a bounded
-// device-side wait timed out.
+// device-side wait timed out.  The first call of a new problem class runs the
+// product several times (tile-width timing), so the output must not alias an
+// input.
 void tc_gemm(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, int N, int Kpad, int batch,
              const TcEpilogue& e, int* d_err);
 

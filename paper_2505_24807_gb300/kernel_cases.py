@@ -1,6 +1,6 @@
 """Small, self-contained invocations of single libxs kernel families through
 the public API, sized for profiling one or a few launches (Nsight Compute
-captures of the full workload would hold ~15 GB on the device):
+captures of the full workload would hold ~12 GB on the device):
 
   python -m paper_2505_24807_gb300.kernel_cases oz      # digit-product kernel: combination, then Gram
   python -m paper_2505_24807_gb300.kernel_cases tc      # TF32 transforms: one TDHF product, large molecule
