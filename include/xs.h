@@ -100,6 +100,11 @@ typedef struct {
                         float64 pipe) or XS_SUBSPACE_EMULATED (2, exact digit splitting on the tensor
                         cores, see xs_subspace_gram); AUTO = EMULATED for XS_MIXED solves of
                         molecules with nocc * nvir >= 32768, else FP64 */
+  double memory_limit; /* bytes the subspace arrays of one molecule may occupy (V and its products in
+                          float64, their digit operands when emulated); the subspace cap is lowered to
+                          fit.  0: the device's free memory at the call, plus the context's reusable
+                          subspace buffers, less a reserve for the other work buffers.  XS_ENOMEM when
+                          not even the initial guess block and one block of new vectors fit */
 } xs_ex_opts;
 
 typedef struct {
@@ -111,6 +116,7 @@ typedef struct {
   int fallback;         /* 1 if the learned shift was dropped because a residual stalled */
   double seconds;       /* wall time of the call */
   double seconds_products;  /* of which in A*X products */
+  int max_subspace_used;    /* subspace cap in effect (largest over the molecules) */
 } xs_solve_info;
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t to
@@ -248,6 +254,18 @@ int xs_subspace_gram(xs_ctx* ctx, int M, int N, long long L, const double* A, co
 /* Y (nout x L) = sum_{b<nb} coef_b^T X_b, X: nb x S x L, coef: nb x S x nout, 1 <= nb <= 3 */
 int xs_subspace_combine(xs_ctx* ctx, int nb, int S, int nout, long long L, const double* X, const double* coef,
                         double* Y, int emulated);
+
+/* Absorption spectrum (paper, Section "Results and discussion": the computed
+ * states' oscillator strengths broadened by Gaussians of width 0.1 eV):
+ *   out[g] = sum_{i<n} f[i] exp(-(grid[g] - omega[i])^2 / (2 width^2)) / (width sqrt(2 pi))
+ * omega, grid and width in eV; width is the Gaussian's standard deviation
+ * (each line has unit area, so the spectrum integrates to sum f).  omega and
+ * f (n values), grid and out (ngrid values) may be host or device memory,
+ * owned by the caller; n = 0 gives zeros.  XS_EINVAL for negative counts,
+ * null arrays with positive counts, or a width that is not positive and
+ * finite.  Synchronous. */
+int xs_spectrum(xs_ctx* ctx, int n, const double* omega, const double* f, double width, int ngrid,
+                const double* grid, double* out);
 
 /* Per-kernel timing.  xs_profile(ctx, 1) clears and enables it: every
  * instrumented kernel launch of later calls is bracketed by CUDA events on

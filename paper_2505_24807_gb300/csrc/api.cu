@@ -1,6 +1,7 @@
 // C ABI of libxs (declared and documented in include/xs.h).
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -351,6 +352,7 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
       inf.polished = inf.polished || st.polished;
       inf.learned = inf.learned || st.learned;
       inf.fallback = inf.fallback || st.fallback;
+      inf.max_subspace_used = st.smax > inf.max_subspace_used ? st.smax : inf.max_subspace_used;
       tprod += st.seconds_products;
       const int kk = m.nroots;
       std::vector<double> pad(K, 0.0);
@@ -375,6 +377,31 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
     if (info) *info = inf;
     if (status == XS_ENOCONV) c.err = "Davidson did not converge within max_iter";
     return status;
+  });
+}
+
+int xs_spectrum(xs_ctx* ctx, int n, const double* omega, const double* f, double width, int ngrid,
+                const double* grid, double* out) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (n < 0 || ngrid < 0) throw Error(XS_EINVAL, "negative count");
+    if (!(width > 0.0) || !std::isfinite(width)) throw Error(XS_EINVAL, "width must be positive and finite");
+    if ((n > 0 && (!omega || !f)) || (ngrid > 0 && (!grid || !out))) throw Error(XS_EINVAL, "null array");
+    if (ngrid == 0) return XS_OK;
+    cudaStream_t s = c.stream;
+    DevBuf<double> buf((size_t)2 * n + 2 * (size_t)ngrid);
+    double* dw = buf.get();
+    double* df = dw + n;
+    double* dg = df + n;
+    double* dout = dg + ngrid;
+    if (n > 0) {
+      copy_any(s, dw, omega, sizeof(double) * n);
+      copy_any(s, df, f, sizeof(double) * n);
+    }
+    copy_any(s, dg, grid, sizeof(double) * ngrid);
+    xs::absorption_spectrum(s, n, dw, df, width, ngrid, dg, dout);
+    copy_any(s, out, dout, sizeof(double) * ngrid);
+    XS_CUDA(cudaStreamSynchronize(s));
+    return XS_OK;
   });
 }
 

@@ -336,8 +336,38 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   Smax = std::min(Smax, 1000);
   const int max_iter = opt.max_iter > 0 ? opt.max_iter : 200;
   const int nguess = static_cast<int>(std::min<long long>(ov, std::max(2 * kk, kk + 2)));
-  if (Smax < nguess + (rpa ? 2 : 1) * kk) Smax = static_cast<int>(std::min<long long>(ov, nguess + 2 * kk));
+  const int Smin = static_cast<int>(std::min<long long>(ov, nguess + 2 * kk));
+  if (Smax < nguess + (rpa ? 2 : 1) * kk) Smax = Smin;
   const int maxnew = rpa ? 2 * kk : kk;
+  // memory bound on the subspace: V and its products in float64 (and their
+  // digit operands for the tensor-core subspace) take per_vec bytes per
+  // stored vector; the cap is lowered to fit the budget (more restarts, same
+  // roots), and a budget below the guess block plus one new block is an error
+  {
+    const double nstore = rpa ? 3.0 : 2.0;
+    const double per_vec = 8.0 * nstore * ov + (use_oz ? 16.0 * (double)oz_lp(ov) + 16.0 * nstore * ov : 0.0);
+    double budget = opt.memory_limit;
+    if (!(budget > 0.0)) {
+      size_t free_b = 0, total_b = 0;
+      XS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+      double held = 0.0;   // this context's subspace buffers are reused
+      if (c.dav_cache) {
+        const Work& w0 = *static_cast<const Work*>(c.dav_cache.get());
+        held = 8.0 * (double)(w0.V.n + w0.S1.n + w0.S2.n) + 2.0 * (double)(w0.Vtn.n + w0.Vnn.n + w0.S1nn.n + w0.S2nn.n);
+      }
+      // reserve: Ritz vectors, residuals, new directions and their digit
+      // scratch (a few 2k-row blocks of amplitudes), product scratch, headroom
+      const double reserve = 8.0 * ov * (8.0 * kk + 8.0) + 32.0 * ov * (2.0 * kk + 2.0) + 4.0 * 1073741824.0;
+      budget = (double)free_b + held - reserve;
+    }
+    const double cap = std::floor(budget / per_vec);
+    if (cap < Smin)
+      throw Error(XS_ENOMEM, "subspace needs " + std::to_string(static_cast<long long>(Smin * per_vec)) +
+                                 " bytes for its first " + std::to_string(Smin) + " vectors; budget " +
+                                 std::to_string(static_cast<long long>(budget)));
+    if (cap < Smax) Smax = static_cast<int>(cap);
+  }
+  st.smax = Smax;
   // Mixed-precision products carry rounding noise of ~1e-6 relative, so their
   // residuals cannot fall much below 1e-5 eV; the energies, quadratic in the
   // residual, are still converged far below 1e-5 eV at a 1e-4 eV residual.

@@ -14,6 +14,7 @@ struct SolveStats {
   bool learned = false;    // learned guess and shift were used
   bool fallback = false;   // the learned shift was dropped for a stalled residual
   double seconds_products = 0.0;
+  int smax = 0;            // subspace cap in effect
 };
 
 // Solves molecule m; stores roots, oscillator strengths, residuals and

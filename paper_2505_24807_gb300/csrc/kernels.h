@@ -74,6 +74,12 @@ void transpose(cudaStream_t s, int rows, int cols, const double* a, double* b);
 // non-finite value (the error word c.tc_err).
 void check_device_error(Ctx& c);
 
+// ---- absorption spectrum (spectrum.cu) -----------------------------------
+// out[g] = sum_n f_n exp(-(grid_g - omega_n)^2 / (2 width^2)) / (width sqrt(2 pi)),
+// all arrays on the device.
+void absorption_spectrum(cudaStream_t s, int n, const double* omega, const double* f, double width, int ngrid,
+                         const double* grid, double* out);
+
 // ---- small dense eigenproblems (small.cu) -----------------------------------
 // Symmetric eigen-decomposition (n <= 1024) by cyclic Jacobi in one CTA
 // (shared-memory resident for n <= 64): A (n x n, lda) may be overwritten, V

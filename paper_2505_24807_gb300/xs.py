@@ -41,13 +41,13 @@ class xs_gs_info(C.Structure):
 class xs_ex_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("nroots", C.c_int), ("tol", C.c_double), ("precision", C.c_int),
                 ("guess", C.c_int), ("max_subspace", C.c_int), ("max_iter", C.c_int), ("batched", C.c_int),
-                ("subspace", C.c_int)]
+                ("subspace", C.c_int), ("memory_limit", C.c_double)]
 
 
 class xs_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("products", C.c_longlong), ("converged", C.c_int),
                 ("polished", C.c_int), ("learned", C.c_int), ("fallback", C.c_int), ("seconds", C.c_double),
-                ("seconds_products", C.c_double)]
+                ("seconds_products", C.c_double), ("max_subspace_used", C.c_int)]
 
 
 class xs_prof_entry(C.Structure):
@@ -83,6 +83,7 @@ def load():
         "xs_gbuild_noalloc": (i, [vp, i, i, vp, vp]),
         "xs_subspace_gram": (i, [vp, i, i, C.c_longlong, vp, vp, vp, i]),
         "xs_subspace_combine": (i, [vp, i, i, i, C.c_longlong, vp, vp, vp, i]),
+        "xs_spectrum": (i, [vp, i, vp, vp, d, i, vp, vp]),
         "xs_mlp_nparams": (i, []),
         "xs_mlp_init": (i, [vp, C.c_ulonglong]),
         "xs_mlp_get_weights": (i, [vp, vp]),
@@ -188,10 +189,10 @@ def xs_apply(ctx, mol, kind, x, precision=XS_FP64, out=None):
 
 
 def xs_excited(ctx, method=XS_CIS, nroots=5, tol=1e-6, precision=XS_FP64, guess=XS_GUESS_PLAIN, max_subspace=0,
-               max_iter=0, batched=0, n_mol=1, outputs=None, allow=(), subspace=0):
+               max_iter=0, batched=0, n_mol=1, outputs=None, allow=(), subspace=0, memory_limit=0.0):
     """Returns dict(omega, osc, iters, resid, info, status); arrays of shape (n_mol, nroots)."""
     o = xs_ex_opts(int(method), int(nroots), float(tol), int(precision), int(guess), int(max_subspace),
-                   int(max_iter), int(batched), int(subspace))
+                   int(max_iter), int(batched), int(subspace), float(memory_limit))
     if outputs is None:
         outputs = dict(omega=np.zeros((n_mol, nroots)), osc=np.zeros((n_mol, nroots)),
                        iters=np.zeros(n_mol, dtype=np.int32), resid=np.zeros((n_mol, nroots)))
@@ -242,6 +243,21 @@ def xs_subspace_combine(ctx, X, coef, emulated=True):
     Y = np.empty((nout, L))
     _check(ctx, load().xs_subspace_combine(ctx, nb, S, nout, L, _ptr(X), _ptr(coef), _ptr(Y), int(bool(emulated))))
     return Y
+
+
+def xs_spectrum(ctx, omega, f, grid, width=0.1):
+    """Absorption spectrum on the energy grid (eV): the oscillator strengths f
+    of the states at omega (eV) broadened by unit-area Gaussians of standard
+    deviation width (eV)."""
+    omega = np.ascontiguousarray(omega, dtype=np.float64).ravel()
+    f = np.ascontiguousarray(f, dtype=np.float64).ravel()
+    grid = np.ascontiguousarray(grid, dtype=np.float64).ravel()
+    if omega.shape != f.shape:
+        raise ValueError("omega and f differ in length")
+    out = np.empty_like(grid)
+    _check(ctx, load().xs_spectrum(ctx, len(omega), _ptr(omega), _ptr(f), float(width), len(grid), _ptr(grid),
+                                   _ptr(out)))
+    return out
 
 
 def xs_mlp_nparams():

@@ -203,3 +203,77 @@ def test_unstable_reference_reported():
         assert np.abs(out["omega"][0] - w).max() < 1e-6
     finally:
         ctx.close()
+
+
+def test_spectrum_matches_oracle():
+    """Gaussian-broadened absorption spectrum (paper width 0.1 eV) against the
+    oracle on seeded lines, and on a solved molecule's own roots."""
+    from oracle.spectrum import absorption_spectrum
+    rng = np.random.default_rng(4)
+    omega = rng.uniform(3.0, 8.0, 37)
+    f = rng.uniform(0.0, 1.5, 37)
+    grid = np.linspace(2.0, 9.0, 3001)
+    ctx = context(molgen.make_params(0))
+    try:
+        got = xs.xs_spectrum(ctx.h, omega, f, grid, 0.1)
+        ref = absorption_spectrum(omega, f, grid, 0.1)
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+        assert np.all(xs.xs_spectrum(ctx.h, [], [], grid, 0.1) == 0.0)
+        with pytest.raises(xs.XSError):
+            xs.xs_spectrum(ctx.h, omega, f, grid, 0.0)
+    finally:
+        ctx.close()
+
+
+def test_spectrum_of_solved_molecule(small_case):
+    """The library's spectrum of its own CIS roots equals the oracle's spectrum
+    of the brute-force roots within what the 1e-6 eV root tolerance allows."""
+    from oracle import excited, nddo
+    from oracle.spectrum import absorption_spectrum
+    c = small_case
+    mol, res = c["mol"], c["res"]
+    eri = nddo.full_eri(mol, c["ints"])
+    A, _ = excited.explicit_AB(res.eps, res.C, mol.nocc, eri)
+    k = 5
+    w, V = excited.cis_bruteforce(A, k)
+    fo = excited.oscillator_strengths(mol, res.C, mol.nocc, w, V.T.reshape(k, mol.nocc, mol.nvir))
+    grid = np.linspace(w[0] - 1.0, w[-1] + 1.0, 2001)
+    ref = absorption_spectrum(w, fo, grid)
+    ctx = context(c["params"])
+    try:
+        xs.xs_ground_state(ctx.h, [(c["Z"], c["xyz"])])
+        out = xs.xs_excited(ctx.h, method=xs.XS_CIS, nroots=k, tol=1e-6)
+        got = xs.xs_spectrum(ctx.h, out["omega"][0], out["osc"][0], grid)
+    finally:
+        ctx.close()
+    # |dS| <= sum_n (|df_n| peak + f_n |d omega_n| max slope), peak = 1/(sigma sqrt(2 pi))
+    peak = 1.0 / (0.1 * np.sqrt(2 * np.pi))
+    bound = k * (1e-4 * peak + fo.max() * 1e-6 * peak / (0.1 * np.sqrt(np.e)))
+    assert np.abs(got - ref).max() <= bound
+
+
+def test_memory_bounded_subspace(small_case):
+    """A memory budget lowers the subspace cap (more restarts, same roots); a
+    budget below the guess block plus one new block is XS_ENOMEM."""
+    from oracle import excited, nddo
+    c = small_case
+    mol, res = c["mol"], c["res"]
+    eri = nddo.full_eri(mol, c["ints"])
+    A, _ = excited.explicit_AB(res.eps, res.C, mol.nocc, eri)
+    k = 5
+    w = excited.cis_bruteforce(A, k)[0]
+    per_vec = 8.0 * 2 * mol.nocc * mol.nvir   # V and A V in float64
+    ctx = context(c["params"])
+    try:
+        xs.xs_ground_state(ctx.h, [(c["Z"], c["xyz"])])
+        free = xs.xs_excited(ctx.h, method=xs.XS_CIS, nroots=k, tol=1e-6)
+        tight = xs.xs_excited(ctx.h, method=xs.XS_CIS, nroots=k, tol=1e-6, memory_limit=20.5 * per_vec)
+        assert free["info"]["max_subspace_used"] == 50
+        assert tight["info"]["max_subspace_used"] == 20
+        assert np.abs(tight["omega"][0] - w).max() < 1e-6
+        assert tight["info"]["converged"] == 1
+        with pytest.raises(xs.XSError) as e:
+            xs.xs_excited(ctx.h, method=xs.XS_CIS, nroots=k, tol=1e-6, memory_limit=10 * per_vec)
+        assert e.value.status == xs.XS_ENOMEM
+    finally:
+        ctx.close()
