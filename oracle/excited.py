@@ -59,6 +59,24 @@ def g_minus(mol, ints, R):
     return -2.0 * K
 
 
+# Triplet excitations (not computed in the paper, which treats closed-shell
+# singlets; the spin-adapted triplet combinations are the textbook ones, e.g.
+# Dreuw and Head-Gordon, Chem. Rev. 105, 4009 (2005)): the Coulomb-type
+# 2(ia|jb) terms drop out, A_T = de - (ij|ab), B_T = -(ib|ja).  Through the AO
+# transition density: A_T X uses -K(R), (A+B)_T X uses -2K(R_s), and
+# (A-B)_T = (A-B) (the same -2K(R_a) as the singlet).
+
+def g_cis_triplet(mol, ints, R):
+    _, K = coulomb_exchange(mol, ints, R)
+    return -K
+
+
+def g_plus_triplet(mol, ints, R):
+    Rs = 0.5 * (R + R.T)
+    _, K = coulomb_exchange(mol, ints, Rs)
+    return -2.0 * K
+
+
 def delta_eps(eps, nocc):
     """(eps_a - eps_i) as an (nocc, nvir) matrix."""
     return eps[None, nocc:] - eps[:nocc, None]
@@ -67,7 +85,8 @@ def delta_eps(eps, nocc):
 def apply_kind(mol, ints, C, eps, nocc, X, kind):
     """Products for a stack of amplitude matrices X (k, nocc, nvir).
 
-    kind: 'A' (CIS), 'ApB' (A + B), 'AmB' (A - B), or 'G' (returns the
+    kind: 'A' (CIS), 'ApB' (A + B), 'AmB' (A - B), their triplet forms
+    'A_T', 'ApB_T', 'AmB_T' (the last equal to 'AmB'), or 'G' (returns the
     AO matrix G_CIS(R) for each R = X given directly as an n x n matrix).
     """
     X = np.asarray(X, dtype=np.float64)
@@ -82,8 +101,12 @@ def apply_kind(mol, ints, C, eps, nocc, X, kind):
             G = g_cis(mol, ints, R)
         elif kind == "ApB":
             G = g_plus(mol, ints, R)
-        elif kind == "AmB":
+        elif kind in ("AmB", "AmB_T"):
             G = g_minus(mol, ints, R)
+        elif kind == "A_T":
+            G = g_cis_triplet(mol, ints, R)
+        elif kind == "ApB_T":
+            G = g_plus_triplet(mol, ints, R)
         else:
             raise ValueError(kind)
         out[k] = de * X[k] + Co.T @ G @ Cv
@@ -108,6 +131,20 @@ def explicit_AB(eps, C, nocc, eri):
     de = delta_eps(eps, nocc).reshape(-1)
     A = np.diag(de) + (2.0 * ov_ov - oo_vv).reshape(o * v, o * v)
     B = (2.0 * ov_ov - ib_ja).reshape(o * v, o * v)
+    return A, B
+
+
+def explicit_AB_triplet(eps, C, nocc, eri):
+    """Triplet A and B as (ov, ov) matrices: A_T = de - (ij|ab), B_T = -(ib|ja)."""
+    n = C.shape[0]
+    o, v = nocc, n - nocc
+    mo = mo_eri(eri, C)
+    ov_ov = mo[:o, o:, :o, o:]
+    oo_vv = mo[:o, :o, o:, o:].transpose(0, 2, 1, 3)
+    ib_ja = ov_ov.transpose(0, 3, 2, 1)
+    de = delta_eps(eps, nocc).reshape(-1)
+    A = np.diag(de) - oo_vv.reshape(o * v, o * v)
+    B = -ib_ja.reshape(o * v, o * v)
     return A, B
 
 
@@ -309,8 +346,14 @@ def oscillator_strengths(mol, C, nocc, omega, U):
 # ---------------------------------------------------------------------------
 # the whole excited-state solve for one molecule
 
-def solve(mol, ints, scf_result, method="CIS", nroots=5, tol=1e-6, max_sub=None):
-    """Davidson solve on top of a converged SCF; returns omega (eV), f, amplitudes."""
+def solve(mol, ints, scf_result, method="CIS", nroots=5, tol=1e-6, max_sub=None, spin="singlet"):
+    """Davidson solve on top of a converged SCF; returns omega (eV), f, amplitudes.
+
+    spin: 'singlet' or 'triplet' (triplets are dipole-forbidden: f = 0).
+    """
+    if spin not in ("singlet", "triplet"):
+        raise ValueError(spin)
+    sfx = "_T" if spin == "triplet" else ""
     C, eps = scf_result.C, scf_result.eps
     o, v = mol.nocc, mol.nvir
     diag = delta_eps(eps, o).reshape(-1)
@@ -322,20 +365,20 @@ def solve(mol, ints, scf_result, method="CIS", nroots=5, tol=1e-6, max_sub=None)
         return Xs.reshape(Xs.shape[0], -1).T
 
     if method == "CIS":
-        res = davidson_cis(lambda Vc: flat(apply_kind(mol, ints, C, eps, o, unflat(Vc), "A")),
+        res = davidson_cis(lambda Vc: flat(apply_kind(mol, ints, C, eps, o, unflat(Vc), "A" + sfx)),
                            diag, nroots, tol=tol, max_sub=max_sub)
         Xs = unflat(res["X"])
-        f = oscillator_strengths(mol, C, o, res["omega"], Xs)
+        f = oscillator_strengths(mol, C, o, res["omega"], Xs) if not sfx else np.zeros(len(res["omega"]))
         return dict(omega=res["omega"], f=f, X=Xs, Y=None, residual=res["residual"],
                     iterations=res["iterations"], products=res["products"], converged=res["converged"])
     if method in ("RPA", "TDHF"):
         def apm(Vc):
             Xs = unflat(Vc)
-            return (flat(apply_kind(mol, ints, C, eps, o, Xs, "ApB")),
-                    flat(apply_kind(mol, ints, C, eps, o, Xs, "AmB")))
+            return (flat(apply_kind(mol, ints, C, eps, o, Xs, "ApB" + sfx)),
+                    flat(apply_kind(mol, ints, C, eps, o, Xs, "AmB" + sfx)))
         res = davidson_rpa(apm, diag, nroots, tol=tol, max_sub=max_sub)
         U, W = unflat(res["U"]), unflat(res["W"])
-        f = oscillator_strengths(mol, C, o, res["omega"], U)
+        f = oscillator_strengths(mol, C, o, res["omega"], U) if not sfx else np.zeros(len(res["omega"]))
         return dict(omega=res["omega"], f=f, X=0.5 * (U + W), Y=0.5 * (U - W), residual=res["residual"],
                     iterations=res["iterations"], products=res["products"], converged=res["converged"])
     raise ValueError(method)

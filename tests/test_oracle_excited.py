@@ -202,3 +202,67 @@ def test_generator_sizes():
     assert molgen.n_orbitals(Z) == 600
     Z2, xyz2 = molgen.config_medium(0)
     assert np.array_equal(Z, Z2) and np.array_equal(xyz, xyz2)
+
+
+# ---- triplets (spin-adapted A_T = de - (ij|ab), B_T = -(ib|ja)) -------------
+
+@pytest.fixture(scope="module")
+def small_triplet(small):
+    mol, ints, res, eri, A, B = small
+    At, Bt = excited.explicit_AB_triplet(res.eps, res.C, mol.nocc, eri)
+    return At, Bt
+
+
+def test_triplet_products_equal_explicit_matrices(small, small_triplet):
+    mol, ints, res, eri, A, B = small
+    At, Bt = small_triplet
+    o, v = mol.nocc, mol.nvir
+    X = np.random.default_rng(2).uniform(-1, 1, size=(3, o, v))
+    flat = X.reshape(3, -1).T
+    for kind, M in (("A_T", At), ("ApB_T", At + Bt), ("AmB_T", At - Bt)):
+        Y = excited.apply_kind(mol, ints, res.C, res.eps, o, X, kind).reshape(3, -1).T
+        ref = M @ flat
+        assert np.abs(Y - ref).max() <= 1e-12 * np.abs(ref).max(), kind
+
+
+def test_triplet_matrix_structure(small, small_triplet):
+    mol, ints, res, eri, A, B = small
+    At, Bt = small_triplet
+    # A - B is spin-independent; A - A_T = 2 (ia|jb) and B - B_T = 2 (ia|jb)
+    # (the model's two-electron matrix need not be positive semidefinite, so no
+    # ordering of singlets and triplets is implied)
+    assert np.abs((A - B) - (At - Bt)).max() < 1e-12
+    assert np.abs((A - At) - (B - Bt)).max() < 1e-12
+    assert np.abs(At - At.T).max() < 1e-12 and np.abs(Bt - Bt.T).max() < 1e-12
+
+
+def test_davidson_triplets_equal_bruteforce(small, small_triplet):
+    mol, ints, res, eri, A, B = small
+    At, Bt = small_triplet
+    w, _ = excited.cis_bruteforce(At, 5)
+    out = excited.solve(mol, ints, res, "CIS", 5, tol=1e-6, spin="triplet")
+    assert out["converged"]
+    assert np.abs(out["omega"] - w).max() < 1e-8
+    assert np.all(out["f"] == 0.0)
+    if np.linalg.eigvalsh(At + Bt)[0] > 0:   # triplet-stable reference
+        om, _, _ = excited.rpa_bruteforce(At, Bt, 5)
+        out = excited.solve(mol, ints, res, "RPA", 5, tol=1e-6, spin="triplet")
+        assert np.abs(out["omega"] - om).max() < 1e-8
+
+
+def test_h2_triplet_closed_form(params0):
+    # two-site H2: (ii|aa) = (gss + gamma)/2, (ia|ia) = (gss - gamma)/2, so
+    # A_T = de - (gss + gamma)/2 and B_T = -(gss - gamma)/2
+    R = 0.9
+    mol, ints = _h2(params0, R)
+    res = scf.scf(mol, ints, min_gap=0.0)
+    gss = params0[1]["gss"]
+    gamma = ints.pair_block(0, 1)[0, 0, 0, 0]
+    de = res.eps[1] - res.eps[0]
+    At = de - 0.5 * (gss + gamma)
+    Bt = -0.5 * (gss - gamma)
+    cis = excited.solve(mol, ints, res, "CIS", 1, tol=1e-10, spin="triplet")
+    assert abs(cis["omega"][0] - At) < 1e-10
+    if (At - Bt) > 0 and (At + Bt) > 0:
+        rpa = excited.solve(mol, ints, res, "RPA", 1, tol=1e-10, spin="triplet")
+        assert abs(rpa["omega"][0] - math.sqrt(At ** 2 - Bt ** 2)) < 1e-10
