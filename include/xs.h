@@ -65,6 +65,14 @@ extern "C" {
 #define XS_KIND_APB 1  /* (A + B) X    (TDHF) */
 #define XS_KIND_AMB 2  /* (A - B) X    (TDHF) */
 #define XS_KIND_G 3    /* G_CIS(R) = 2 J(R) - K(R) of an n x n AO matrix R */
+#define XS_KIND_A_TRIPLET 4    /* A_T X = de X - C_occ^T K(R) C_vir (triplet CIS) */
+#define XS_KIND_APB_TRIPLET 5  /* (A_T + B_T) X (triplet TDHF); (A_T - B_T) = (A - B): XS_KIND_AMB */
+
+/* Spin of the computed states (xs_ex_opts.spin).  The paper computes
+ * closed-shell singlets; triplets use the spin-adapted A_T = de - (ij|ab),
+ * B_T = -(ib|ja) (no Coulomb terms in G) and have zero oscillator strength. */
+#define XS_SINGLET 0
+#define XS_TRIPLET 1
 
 #define XS_GUESS_PLAIN 0    /* unit vectors on the lowest orbital-energy gaps */
 #define XS_GUESS_LEARNED 1  /* MLP-predicted guess and diagonal shift (plain fallback) */
@@ -105,6 +113,7 @@ typedef struct {
                           fit.  0: the device's free memory at the call, plus the context's reusable
                           subspace buffers, less a reserve for the other work buffers.  XS_ENOMEM when
                           not even the initial guess block and one block of new vectors fit */
+  int spin;            /* XS_SINGLET (0) or XS_TRIPLET (1); triplet solves use the plain guess */
 } xs_ex_opts;
 
 typedef struct {
@@ -156,7 +165,7 @@ int xs_set_orbitals(xs_ctx* ctx, int mol, const double* C, const double* eps);
 
 /* Apply a response product to nvec vectors of molecule `mol`
  * (Eqs. cis_matrix_vector and ftilde):
- *   kind XS_KIND_A / APB / AMB: in and out are nvec x (nocc*nvir);
+ *   kind XS_KIND_A / APB / AMB / A_TRIPLET / APB_TRIPLET: in and out are nvec x (nocc*nvir);
  *   kind XS_KIND_G: in and out are nvec x (n*n) AO matrices, out = 2J(R) - K(R).
  * `precision` selects XS_FP64 or XS_MIXED.  Host or device pointers. */
 int xs_apply(xs_ctx* ctx, int mol, int kind, int nvec, const double* in, double* out, int precision);

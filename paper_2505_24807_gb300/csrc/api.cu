@@ -258,18 +258,20 @@ int xs_apply(xs_ctx* ctx, int mol, int kind, int nvec, const double* in, double*
       copy_any(s, R.get(), in, sizeof(double) * nvec * nn);
       xs::gmatrix(c, m, precision, nvec, R.get(), G.get());
       copy_any(s, out, G.get(), sizeof(double) * nvec * nn);
-    } else if (kind == XS_KIND_A || kind == XS_KIND_APB || kind == XS_KIND_AMB) {
+    } else if (kind == XS_KIND_A || kind == XS_KIND_APB || kind == XS_KIND_AMB || kind == XS_KIND_A_TRIPLET ||
+               kind == XS_KIND_APB_TRIPLET) {
+      const bool triplet = kind == XS_KIND_A_TRIPLET || kind == XS_KIND_APB_TRIPLET;
       DevBuf<double> X((size_t)nvec * ov), Y1((size_t)nvec * ov), Y2;
       copy_any(s, X.get(), in, sizeof(double) * nvec * ov);
-      if (kind == XS_KIND_A) {
-        xs::products(c, m, XS_CIS, precision, nvec, X.get(), Y1.get(), nullptr);
+      if (kind == XS_KIND_A || kind == XS_KIND_A_TRIPLET) {
+        xs::products(c, m, XS_CIS, precision, nvec, X.get(), Y1.get(), nullptr, triplet);
         xs::check_device_error(c);
         copy_any(s, out, Y1.get(), sizeof(double) * nvec * ov);
       } else {
         Y2.alloc((size_t)nvec * ov);
-        xs::products(c, m, XS_TDHF, precision, nvec, X.get(), Y1.get(), Y2.get());
+        xs::products(c, m, XS_TDHF, precision, nvec, X.get(), Y1.get(), Y2.get(), triplet);
         xs::check_device_error(c);
-        copy_any(s, out, (kind == XS_KIND_APB ? Y1 : Y2).get(), sizeof(double) * nvec * ov);
+        copy_any(s, out, (kind == XS_KIND_AMB ? Y2 : Y1).get(), sizeof(double) * nvec * ov);
       }
     } else {
       throw Error(XS_EINVAL, "unknown product kind");
@@ -291,6 +293,8 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
     if (o.precision != XS_FP64 && o.precision != XS_MIXED) throw Error(XS_EINVAL, "bad precision");
     if (o.subspace < XS_SUBSPACE_AUTO || o.subspace > XS_SUBSPACE_EMULATED)
       throw Error(XS_EINVAL, "bad subspace option");
+    if (o.spin != XS_SINGLET && o.spin != XS_TRIPLET) throw Error(XS_EINVAL, "spin must be XS_SINGLET or XS_TRIPLET");
+    if (!(o.memory_limit >= 0.0)) throw Error(XS_EINVAL, "memory_limit must be >= 0");
     if (c.mols.empty()) throw Error(XS_ESTATE, "xs_ground_state must come first");
     const int K = o.nroots;
     int status = XS_OK;

@@ -325,6 +325,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   const int o = m.o, v = m.v;
   const long long ov = (long long)o * v;
   const bool rpa = opt.method == XS_TDHF;
+  const bool triplet = opt.spin == XS_TRIPLET;
   const int kk = static_cast<int>(std::min<long long>(opt.nroots, ov));
   const bool use_oz = opt.subspace == XS_SUBSPACE_EMULATED ||
                       (opt.subspace == XS_SUBSPACE_AUTO && opt.precision == XS_MIXED && ov >= kOzMinLength);
@@ -445,7 +446,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     prod_events.emplace_back(e0, e1);
     XS_CUDA(cudaEventRecord(e0, s));
     products(c, m, opt.method, prod_prec, count, w.V.get() + first * ov, w.S1.get() + first * ov,
-             rpa ? w.S2.get() + first * ov : nullptr);
+             rpa ? w.S2.get() + first * ov : nullptr, triplet);
     XS_CUDA(cudaEventRecord(e1, s));
     st.products += count;
   };
@@ -475,7 +476,8 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   // learned guess and diagonal shift: MLP outputs on the lowest-gap pairs
   const double* shift = nullptr;
   std::vector<long long> learned_pairs;
-  if (opt.guess == XS_GUESS_LEARNED && c.mlp && c.mlp->ready) {
+  // (the network was trained on singlet roots and shifts: triplets take the plain guess)
+  if (opt.guess == XS_GUESS_LEARNED && !triplet && c.mlp && c.mlp->ready) {
     HostScope h_learned("host:learned_guess");
     const int npairs = static_cast<int>(std::min<long long>(ov, kLearnedPairs));
     std::vector<long long> pairs = lowest_gap_pairs(c, m, npairs);
@@ -800,12 +802,14 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   XS_CUDA(cudaMemcpyAsync(m.U.get(), w.X.get(), sizeof(double) * kk * ov, cudaMemcpyDeviceToDevice, s));
   XS_CUDA(cudaMemcpyAsync(m.Wv.get(), rpa ? w.AX : w.X.get(), sizeof(double) * kk * ov,
                           cudaMemcpyDeviceToDevice, s));
-  w.fdev.ensure(kk);
-  oscillator_strengths(c, m, kk, m.U.get(), w.omega.get(), w.fdev.get());
   m.omega.assign(hw.begin(), hw.begin() + kk);
   m.resid.assign(hn.begin(), hn.begin() + kk);
-  m.osc.resize(kk);
-  sync_copy(s, m.osc.data(), w.fdev.get(), sizeof(double) * kk);
+  m.osc.assign(kk, 0.0);   // triplets: dipole-forbidden
+  if (!triplet) {
+    w.fdev.ensure(kk);
+    oscillator_strengths(c, m, kk, m.U.get(), w.omega.get(), w.fdev.get());
+    sync_copy(s, m.osc.data(), w.fdev.get(), sizeof(double) * kk);
+  }
   m.iterations = st.iterations;
   st.converged = converged;
   return converged ? XS_OK : XS_ENOCONV;

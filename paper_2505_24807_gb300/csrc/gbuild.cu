@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
   // double-buffered groups: group g is read from one buffer while group g + 1
   // is stored into the other from registers loaded before the compute
   constexpr int GV = gv_for<T>();
+  constexpr bool kRpa = MODE == G_RPA || MODE == G_RPA_T;       // G+ and G- outputs, R^T tiles
+  constexpr bool kTriplet = MODE == G_CIS_T || MODE == G_RPA_T;  // no Coulomb terms
   __shared__ T Ws[kGP][kGQ + 1];
   __shared__ T Rt[2][GV][kGR + 4][kGC + 4];
   __shared__ T Rtt[2][GV][kGC + 4][kGR + 5];   // odd row stride: the rows of different atoms hit different banks
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
           wv[nu * 4 + sg] = Ws[pA + ((nA == 4) ? pidx(a, nu) : 0)][pB + ((nB == 4) ? pidx(b, sg) : 0)];
   }
   const int tr = tid % kGR, tc = tid / kGR;   // transpose tile: 4 consecutive threads per row
-  const bool tact = (MODE == G_RPA) && tr < nr && tc < nc;
+  const bool tact = kRpa && tr < nr && tc < nc;
   const long long nn = (long long)n * n;
   const long long at_r = (long long)mu * n + lam, at_t = (long long)(cb + tc) * n + ra + tr;
   __syncthreads();
@@ -241,13 +243,19 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
           for (int i = 0; i < XS_NPARAM; ++i) p[i] = (i >= 4 && i <= 8) ? T(pd[i]) : T(0);
           one_centre<T>(p, a, b, Rd, J1, K1ab, K1ba);
         }
-        const int pab = (nA == 4) ? pidx(a, b) : 0;
-        const T J = J1 + J2[(long long)(PA + pab) * nvec + v];
-        if (MODE == G_CIS) {
-          g = T(2) * J - K1ab;
+        if constexpr (kTriplet) {
+          (void)J1;
+          g = kRpa ? -(K1ab + K1ba) : -K1ab;
+          if (kRpa) gm = -(K1ab - K1ba);
         } else {
-          g = T(4) * J - (K1ab + K1ba);
-          gm = -(K1ab - K1ba);
+          const int pab = (nA == 4) ? pidx(a, b) : 0;
+          const T J = J1 + J2[(long long)(PA + pab) * nvec + v];
+          if (!kRpa) {
+            g = T(2) * J - K1ab;
+          } else {
+            g = T(4) * J - (K1ab + K1ba);
+            gm = -(K1ab - K1ba);
+          }
         }
       } else {
         // K(R)_{mu lam} = sum_{nu in A, sig in B} (mu nu|lam sig) R_{nu sig},
@@ -263,25 +271,25 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
 #pragma unroll
             for (int sg = 0; sg < 4; ++sg) {
               kr = fma(wv[nu * 4 + sg], Rt[buf][q][rA + nu][rB + sg], kr);
-              if (MODE == G_RPA) krt = fma(wv[nu * 4 + sg], Rtt[buf][q][rB + sg][rA + nu], krt);
+              if (kRpa) krt = fma(wv[nu * 4 + sg], Rtt[buf][q][rB + sg][rA + nu], krt);
             }
         } else if (nA == 4) {
 #pragma unroll
           for (int nu = 0; nu < 4; ++nu) {
             kr = fma(wv[nu * 4], Rt[buf][q][rA + nu][rB], kr);
-            if (MODE == G_RPA) krt = fma(wv[nu * 4], Rtt[buf][q][rB][rA + nu], krt);
+            if (kRpa) krt = fma(wv[nu * 4], Rtt[buf][q][rB][rA + nu], krt);
           }
         } else if (nB == 4) {
 #pragma unroll
           for (int sg = 0; sg < 4; ++sg) {
             kr = fma(wv[sg], Rt[buf][q][rA][rB + sg], kr);
-            if (MODE == G_RPA) krt = fma(wv[sg], Rtt[buf][q][rB + sg][rA], krt);
+            if (kRpa) krt = fma(wv[sg], Rtt[buf][q][rB + sg][rA], krt);
           }
         } else {
           kr = fma(wv[0], Rt[buf][q][rA][rB], kr);
-          if (MODE == G_RPA) krt = fma(wv[0], Rtt[buf][q][rB][rA], krt);
+          if (kRpa) krt = fma(wv[0], Rtt[buf][q][rB][rA], krt);
         }
-        if (MODE == G_CIS) {
+        if (!kRpa) {
           g = -kr;
         } else {
           g = -(kr + krt);
@@ -294,14 +302,14 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
         tf32_pair(static_cast<float>(g), h, l);
         out.Gh[at] = h;
         out.Gl[at] = l;
-        if (MODE == G_RPA) {
+        if (kRpa) {
           tf32_pair(static_cast<float>(gm), h, l);
           out.Gmh[at] = h;
           out.Gml[at] = l;
         }
       } else {
         out.G[v * nn + at_r] = g;
-        if (MODE == G_RPA) out.Gm[v * nn + at_r] = gm;
+        if (kRpa) out.Gm[v * nn + at_r] = gm;
       }
     }
     if (v0 + GV < nvec) {
@@ -316,22 +324,31 @@ __global__ void __launch_bounds__(256, 4) gtile_kernel(int n, int np, int nvec, 
   }
 }
 
-template <typename T, bool SPLIT>
-void launch_tiles(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* W, const T* J2,
-                  const T* R, const GOut<T>& out) {
+template <typename T, GMode MODE, bool SPLIT>
+void launch_mode(cudaStream_t s, const DevMol& m, const double* d_par, int nvec, const T* W, const T* J2, const T* R,
+                 const GOut<T>& out) {
   dim3 grid(m.gb_ncols, m.gb_nrows);
   const int4* rows = reinterpret_cast<const int4*>(m.gb_rows.get());
   const int4* cols = reinterpret_cast<const int4*>(m.gb_cols.get());
-  if (mode == G_CIS)
-    gtile_kernel<T, G_CIS, SPLIT><<<grid, 256, 0, s>>>(m.n, m.np, nvec, rows, cols, m.ao_atom.get(),
-                                                       m.ao_local.get(), m.atom_ao_off.get(), m.atom_nao.get(),
-                                                       m.atom_prod_off.get(), m.atom_elem.get(), d_par, W, J2, R, out);
-  else
-    gtile_kernel<T, G_RPA, SPLIT><<<grid, 256, 0, s>>>(m.n, m.np, nvec, rows, cols, m.ao_atom.get(),
-                                                       m.ao_local.get(), m.atom_ao_off.get(), m.atom_nao.get(),
-                                                       m.atom_prod_off.get(), m.atom_elem.get(), d_par, W, J2, R, out);
+  gtile_kernel<T, MODE, SPLIT><<<grid, 256, 0, s>>>(m.n, m.np, nvec, rows, cols, m.ao_atom.get(), m.ao_local.get(),
+                                                    m.atom_ao_off.get(), m.atom_nao.get(), m.atom_prod_off.get(),
+                                                    m.atom_elem.get(), d_par, W, J2, R, out);
+}
+
+template <typename T, bool SPLIT>
+void launch_tiles(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* W, const T* J2,
+                  const T* R, const GOut<T>& out) {
+  switch (mode) {
+    case G_CIS: launch_mode<T, G_CIS, SPLIT>(s, m, d_par, nvec, W, J2, R, out); break;
+    case G_RPA: launch_mode<T, G_RPA, SPLIT>(s, m, d_par, nvec, W, J2, R, out); break;
+    case G_CIS_T: launch_mode<T, G_CIS_T, SPLIT>(s, m, d_par, nvec, W, J2, R, out); break;
+    case G_RPA_T: launch_mode<T, G_RPA_T, SPLIT>(s, m, d_par, nvec, W, J2, R, out); break;
+  }
   XS_CHECK_LAUNCH();
 }
+
+inline bool has_coulomb(GMode mode) { return mode == G_CIS || mode == G_RPA; }
+inline bool has_minus(GMode mode) { return mode == G_RPA || mode == G_RPA_T; }
 
 // zero columns [n, ldo) of rows x ldo matrices (batch stride rows * ldo)
 __global__ void zero_pad_cols_kernel(int rows, int n, int ldo, int nvec, float* a, float* b) {
@@ -354,22 +371,22 @@ void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, in
   ws.ensure((size_t)2 * np * nvec);
   T* rT = ws.get();
   T* J2 = ws.get() + (size_t)np * nvec;
-  {
+  const T* W = nullptr;
+  if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(m.W.get());
+  else W = reinterpret_cast<const T*>(m.Wf.get());
+  if (has_coulomb(mode)) {
     dim3 block(8, 32);
     dim3 grid((m.L.natoms + 31) / 32);
     pack_diag_kernel<T, true><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(), m.atom_nao.get(),
                                                      m.atom_prod_off.get(), R, rT);
     XS_CHECK_LAUNCH();
+    // two-centre Coulomb J2 = W r: W streamed once, split over its columns so
+    // that the skinny product fills the GPU
+    static thread_local DevBuf<T> split_ws;
+    gram<T>(s, np, nvec, np, W, np, rT, np, J2, nvec, T(1), T(0), split_ws);
   }
-  const T* W = nullptr;
-  if constexpr (sizeof(T) == 8) W = reinterpret_cast<const T*>(m.W.get());
-  else W = reinterpret_cast<const T*>(m.Wf.get());
-  // two-centre Coulomb J2 = W r: W streamed once, split over its columns so
-  // that the skinny product fills the GPU
-  static thread_local DevBuf<T> split_ws;
-  gram<T>(s, np, nvec, np, W, np, rT, np, J2, nvec, T(1), T(0), split_ws);
   // algorithmic traffic: read R, write G (and G-), read the pair integrals once
-  const double outs = (mode == G_CIS) ? 1.0 : 2.0;
+  const double outs = has_minus(mode) ? 2.0 : 1.0;
   ProfScope ps(s, sizeof(T) == 8 ? "gbuild_assemble_f64" : "gbuild_assemble_f32",
                sizeof(T) * ((double)nvec * n * n * (1.0 + outs) + (double)np * np), 0.0);
   launch_tiles<T, false>(s, m, d_par, mode, nvec, W, J2, R, GOut<T>{G, Gm, nullptr, nullptr, nullptr, nullptr, 0});
@@ -383,24 +400,24 @@ void gbuild_split(cudaStream_t s, const DevMol& m, const double* d_par, GMode mo
   ws.ensure((size_t)2 * np * nvec);
   float* rT = ws.get();
   float* J2 = ws.get() + (size_t)np * nvec;
-  {
+  const float* W = m.Wf.get();
+  if (has_coulomb(mode)) {
     dim3 block(8, 32);
     dim3 grid((m.L.natoms + 31) / 32);
     pack_diag_kernel<float, true><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(),
                                                          m.atom_nao.get(), m.atom_prod_off.get(), R, rT);
     XS_CHECK_LAUNCH();
+    static thread_local DevBuf<float> split_ws;
+    gram<float>(s, np, nvec, np, W, np, rT, np, J2, nvec, 1.0f, 0.0f, split_ws);
   }
-  const float* W = m.Wf.get();
-  static thread_local DevBuf<float> split_ws;
-  gram<float>(s, np, nvec, np, W, np, rT, np, J2, nvec, 1.0f, 0.0f, split_ws);
   if (ldo > n) {
     const long long cnt = (long long)nvec * n * (ldo - n);
     zero_pad_cols_kernel<<<grid1(cnt, 256), 256, 0, s>>>(n, n, ldo, nvec, Gh, Gl);
-    if (mode != G_CIS) zero_pad_cols_kernel<<<grid1(cnt, 256), 256, 0, s>>>(n, n, ldo, nvec, Gmh, Gml);
+    if (has_minus(mode)) zero_pad_cols_kernel<<<grid1(cnt, 256), 256, 0, s>>>(n, n, ldo, nvec, Gmh, Gml);
     XS_CHECK_LAUNCH();
   }
   // algorithmic traffic: read R, write the G (and G-) TF32 pairs, read the pair integrals once
-  const double outs = (mode == G_CIS) ? 1.0 : 2.0;
+  const double outs = has_minus(mode) ? 2.0 : 1.0;
   ProfScope ps(s, "gbuild_assemble_f32", 4.0 * ((double)nvec * n * n * (1.0 + 2.0 * outs) + (double)np * np), 0.0);
   launch_tiles<float, true>(s, m, d_par, mode, nvec, W, J2, R, GOut<float>{nullptr, nullptr, Gh, Gl, Gmh, Gml, ldo});
 }

@@ -31,7 +31,13 @@ void gram(cudaStream_t s, int M, int N, int L, const T* A, int lda, const T* B, 
           int ldc, T alpha, T beta, DevBuf<T>& ws);
 
 // ---- G(R) build (gbuild.cu) -------------------------------------------------
-enum GMode { G_CIS = 0, G_RPA = 1 };
+// G(R) variants: singlet CIS 2J(R) - K(R); singlet TDHF G+ = 4J(R_s) - 2K(R_s)
+// with G- = -2K(R_a); triplets drop the Coulomb terms: CIS -K(R), TDHF
+// G+ = -2K(R_s) with the same G- (A - B does not depend on the spin).
+enum GMode { G_CIS = 0, G_RPA = 1, G_CIS_T = 2, G_RPA_T = 3 };
+inline GMode gmode(bool rpa, bool triplet) {
+  return rpa ? (triplet ? G_RPA_T : G_RPA) : (triplet ? G_CIS_T : G_CIS);
+}
 // nvec AO matrices R (n x n each, row-major, consecutive) -> G (CIS/Fock:
 // 2J(R) - K(R)) or G+ = 4J(Rs) - 2K(Rs) and G- = -2K(Ra) (RPA).
 // Gm is unused for G_CIS.  ws: scratch of at least 2 * np * nvec.

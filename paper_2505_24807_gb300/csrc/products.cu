@@ -58,7 +58,8 @@ int product_batch(const DevMol& m) {
   return nb;
 }
 
-void products_fp64(Ctx& c, const DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2) {
+void products_fp64(Ctx& c, const DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2,
+                   bool triplet) {
   cudaStream_t s = c.stream;
   const int n = m.n, o = m.o, v = m.v;
   const long long ov = (long long)o * v, nn = (long long)n * n;
@@ -73,11 +74,11 @@ void products_fp64(Ctx& c, const DevMol& m, int method, int nvec, const double* 
     const double* Xk = X + k0 * ov;
     pbuild<double>(s, n, o, v, k, m.CT.get(), Xk, c.ws1.get(), c.ws4.get());
     if (method == XS_CIS) {
-      gbuild<double>(s, m, c.d_par.get(), G_CIS, k, c.ws1.get(), c.ws2.get(), nullptr, c.ws0);
+      gbuild<double>(s, m, c.d_par.get(), gmode(false, triplet), k, c.ws1.get(), c.ws2.get(), nullptr, c.ws0);
       backtransform<double>(s, n, o, v, k, m.CT.get(), c.ws2.get(), Y1 + k0 * ov, c.ws4.get());
       add_diag_term<double>(s, k, o, v, m.eps.get(), Xk, Y1 + k0 * ov);
     } else {
-      gbuild<double>(s, m, c.d_par.get(), G_RPA, k, c.ws1.get(), c.ws2.get(), c.ws3.get(), c.ws0);
+      gbuild<double>(s, m, c.d_par.get(), gmode(true, triplet), k, c.ws1.get(), c.ws2.get(), c.ws3.get(), c.ws0);
       backtransform<double>(s, n, o, v, k, m.CT.get(), c.ws2.get(), Y1 + k0 * ov, c.ws4.get());
       add_diag_term<double>(s, k, o, v, m.eps.get(), Xk, Y1 + k0 * ov);
       backtransform<double>(s, n, o, v, k, m.CT.get(), c.ws3.get(), Y2 + k0 * ov, c.ws4.get());
@@ -89,7 +90,7 @@ void products_fp64(Ctx& c, const DevMol& m, int method, int nvec, const double* 
 // float32 SIMT products: float32 coefficients, R, G and integrals, float32
 // accumulation with round-to-nearest (no tensor cores); the accurate
 // reference for the final Rayleigh-Ritz step of a mixed-precision solve.
-void products_f32(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2) {
+void products_f32(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2, bool triplet) {
   cudaStream_t s = c.stream;
   const int n = m.n, o = m.o, v = m.v;
   const long long ov = (long long)o * v, nn = (long long)n * n;
@@ -117,7 +118,7 @@ void products_f32(Ctx& c, DevMol& m, int method, int nvec, const double* X, doub
     convert_d2f(s, k * ov, Xk, Xf);
     pbuild<float>(s, n, o, v, k, m.CTf.get(), Xf, R, tmp);
     const bool rpa = method != XS_CIS;
-    gbuild<float>(s, m, c.d_par.get(), rpa ? G_RPA : G_CIS, k, R, G, rpa ? Gm : nullptr, c.fs1);
+    gbuild<float>(s, m, c.d_par.get(), gmode(rpa, triplet), k, R, G, rpa ? Gm : nullptr, c.fs1);
     for (int pass = 0; pass < (rpa ? 2 : 1); ++pass) {
       double* Y = (pass == 0 ? Y1 : Y2) + k0 * ov;
       backtransform<float>(s, n, o, v, k, m.CTf.get(), pass == 0 ? G : Gm, Yf, tmp);
@@ -127,17 +128,18 @@ void products_f32(Ctx& c, DevMol& m, int method, int nvec, const double* X, doub
   }
 }
 
-void products(Ctx& c, DevMol& m, int method, int precision, int nvec, const double* X, double* Y1, double* Y2) {
+void products(Ctx& c, DevMol& m, int method, int precision, int nvec, const double* X, double* Y1, double* Y2,
+              bool triplet) {
   if (nvec <= 0) return;
   if (precision == XS_MIXED) {
-    products_mixed(c, m, method, nvec, X, Y1, Y2);
+    products_mixed(c, m, method, nvec, X, Y1, Y2, triplet);
     return;
   }
   if (precision == kPrecF32) {
-    products_f32(c, m, method, nvec, X, Y1, Y2);
+    products_f32(c, m, method, nvec, X, Y1, Y2, triplet);
     return;
   }
-  products_fp64(c, m, method, nvec, X, Y1, Y2);
+  products_fp64(c, m, method, nvec, X, Y1, Y2, triplet);
 }
 
 void gmatrix(Ctx& c, const DevMol& m, int precision, int nvec, const double* R, double* G) {

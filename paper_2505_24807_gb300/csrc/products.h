@@ -10,8 +10,11 @@ constexpr int kPrecF32 = 2;
 
 // Y1 = A X (CIS) or Y1 = (A+B) X, Y2 = (A-B) X (TDHF) for nvec vectors
 // X (nvec x nocc x nvir, float64, device).  precision: XS_FP64 or XS_MIXED.
-void products(Ctx& c, DevMol& m, int method, int precision, int nvec, const double* X, double* Y1, double* Y2);
-void products_fp64(Ctx& c, const DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2);
+// triplet: the spin-adapted triplet matrices (no Coulomb terms in G).
+void products(Ctx& c, DevMol& m, int method, int precision, int nvec, const double* X, double* Y1, double* Y2,
+              bool triplet = false);
+void products_fp64(Ctx& c, const DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2,
+                   bool triplet = false);
 // G_CIS(R) of nvec AO matrices (float64 device arrays)
 void gmatrix(Ctx& c, const DevMol& m, int precision, int nvec, const double* R, double* G);
 // vectors per pass of the AO work arrays

@@ -19,7 +19,7 @@
 
 namespace xs {
 
-void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2) {
+void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2, bool triplet) {
   cudaStream_t s = c.stream;
   const int n = m.n, o = m.o, v = m.v;
   const int np_ = pad32(n), op = pad32(o), vp = pad32(v);
@@ -128,7 +128,7 @@ void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, do
       }
     }
     // G (and G-) written directly as the back-transform's TF32 pairs
-    gbuild_split(s, m, c.d_par.get(), rpa ? G_RPA : G_CIS, k, R, Gh, Gl, Gmh, Gml, np_, c.fs1);
+    gbuild_split(s, m, c.d_par.get(), gmode(rpa, triplet), k, R, Gh, Gl, Gmh, Gml, np_, c.fs1);
     for (int pass = 0; pass < (rpa ? 2 : 1); ++pass) {
       const float* Gph = pass == 0 ? Gh : Gmh;
       const float* Gpl = pass == 0 ? Gl : Gml;

@@ -6,6 +6,7 @@
 
 namespace xs {
 
-void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2);
+void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2,
+                    bool triplet = false);
 
 }  // namespace xs

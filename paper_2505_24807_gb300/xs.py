@@ -18,7 +18,8 @@ XS_OK, XS_EINVAL, XS_ENOMEM, XS_ESCF, XS_EUNSTABLE, XS_ENOCONV, XS_ECUDA, XS_ETI
     0, -1, -2, -3, -4, -5, -6, -7, -8
 XS_CIS, XS_TDHF = 0, 1
 XS_FP64, XS_MIXED = 0, 1
-XS_KIND_A, XS_KIND_APB, XS_KIND_AMB, XS_KIND_G = 0, 1, 2, 3
+XS_KIND_A, XS_KIND_APB, XS_KIND_AMB, XS_KIND_G, XS_KIND_A_TRIPLET, XS_KIND_APB_TRIPLET = 0, 1, 2, 3, 4, 5
+XS_SINGLET, XS_TRIPLET = 0, 1
 XS_GUESS_PLAIN, XS_GUESS_LEARNED = 0, 1
 XS_SUBSPACE_AUTO, XS_SUBSPACE_FP64, XS_SUBSPACE_EMULATED = 0, 1, 2
 XS_NPARAM, XS_NELEM = 13, 4
@@ -41,7 +42,7 @@ class xs_gs_info(C.Structure):
 class xs_ex_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("nroots", C.c_int), ("tol", C.c_double), ("precision", C.c_int),
                 ("guess", C.c_int), ("max_subspace", C.c_int), ("max_iter", C.c_int), ("batched", C.c_int),
-                ("subspace", C.c_int), ("memory_limit", C.c_double)]
+                ("subspace", C.c_int), ("memory_limit", C.c_double), ("spin", C.c_int)]
 
 
 class xs_solve_info(C.Structure):
@@ -189,10 +190,11 @@ def xs_apply(ctx, mol, kind, x, precision=XS_FP64, out=None):
 
 
 def xs_excited(ctx, method=XS_CIS, nroots=5, tol=1e-6, precision=XS_FP64, guess=XS_GUESS_PLAIN, max_subspace=0,
-               max_iter=0, batched=0, n_mol=1, outputs=None, allow=(), subspace=0, memory_limit=0.0):
+               max_iter=0, batched=0, n_mol=1, outputs=None, allow=(), subspace=0, memory_limit=0.0,
+               spin=0):
     """Returns dict(omega, osc, iters, resid, info, status); arrays of shape (n_mol, nroots)."""
     o = xs_ex_opts(int(method), int(nroots), float(tol), int(precision), int(guess), int(max_subspace),
-                   int(max_iter), int(batched), int(subspace), float(memory_limit))
+                   int(max_iter), int(batched), int(subspace), float(memory_limit), int(spin))
     if outputs is None:
         outputs = dict(omega=np.zeros((n_mol, nroots)), osc=np.zeros((n_mol, nroots)),
                        iters=np.zeros(n_mol, dtype=np.int32), resid=np.zeros((n_mol, nroots)))

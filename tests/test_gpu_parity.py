@@ -277,3 +277,38 @@ def test_memory_bounded_subspace(small_case):
         assert e.value.status == xs.XS_ENOMEM
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("kind,okind", [(4, "A_T"), (5, "ApB_T")])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_triplet_products_match_oracle(small_case, kind, okind, precision):
+    from oracle import excited
+    c = small_case
+    mol, res = c["mol"], c["res"]
+    xs.xs_set_orbitals(c["ctx"].h, 0, res.C, res.eps)
+    X = molgen.trial_vectors(8, 4, mol.nocc, mol.nvir)
+    Y = xs.xs_apply(c["ctx"].h, 0, kind, X.reshape(4, -1), precision=precision).reshape(X.shape)
+    ref = excited.apply_kind(mol, c["ints"], res.C, res.eps, mol.nocc, X, okind)
+    assert rel_err(Y, ref) < (1e-11 if precision == 0 else 3e-5)
+
+
+@pytest.mark.parametrize("method", ["CIS", "RPA"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_triplet_roots_match_bruteforce(small_case, method, precision):
+    from oracle import excited, nddo
+    c = small_case
+    mol, res = c["mol"], c["res"]
+    eri = nddo.full_eri(mol, c["ints"])
+    At, Bt = excited.explicit_AB_triplet(res.eps, res.C, mol.nocc, eri)
+    k = 5
+    w = excited.cis_bruteforce(At, k)[0] if method == "CIS" else excited.rpa_bruteforce(At, Bt, k)[0]
+    ctx = context(c["params"])
+    try:
+        xs.xs_ground_state(ctx.h, [(c["Z"], c["xyz"])])
+        out = xs.xs_excited(ctx.h, method=xs.XS_CIS if method == "CIS" else xs.XS_TDHF, nroots=k, tol=1e-6,
+                            precision=precision, spin=xs.XS_TRIPLET, guess=xs.XS_GUESS_LEARNED)
+    finally:
+        ctx.close()
+    assert np.abs(out["omega"][0] - w).max() < (1e-6 if precision == 0 else 1e-5)
+    assert np.all(out["osc"][0] == 0.0)
+    assert out["info"]["converged"] == 1 and out["info"]["learned"] == 0
