@@ -344,8 +344,6 @@ void split_pad_t(cudaStream_t s, int rows, int cols, int ld_dst, const double* s
   split_pad_t_kernel<<<grid, dim3(32, 8), 0, s>>>(rows, cols, ld_dst, src, ld_src, sstride, dstride, hi, lo);
   XS_CHECK_LAUNCH();
 }
-template void split_pad<float>(cudaStream_t, int, int, int, const float*, int, long long, long long, int, bool,
-                               float*, float*);
 
 namespace {
 
