@@ -14,7 +14,11 @@ implementation"):
 * ``excited``  -- explicit A and B (Eq. A_matrix_elem), brute-force CIS and
                   RPA (Eqs. rpa_eqn, cis_eqn), the A*V product through the AO
                   transition density (Eqs. cis_matrix_vector, ftilde), block
-                  Davidson for CIS and for RPA, oscillator strengths.
+                  Davidson for CIS and for RPA, oscillator strengths, and the
+                  spin-adapted triplet forms (beyond the paper's singlets).
+* ``spectrum`` -- the absorption spectrum: oscillator strengths broadened by
+                  Gaussians (Section "Results and discussion").
+* ``mlp``      -- the learned guess network's forward and backward pass.
 
 Everything is float64, written for clarity rather than speed.  Where the
 paper is silent (spin adaptation, the NDDO parameters and integral formulas,
