@@ -1,9 +1,10 @@
 /*
  * xs.h -- C ABI of libxs, the GB300 (sm_103a) semiempirical excited-state library.
  *
- * The library computes the lowest singlet excitations of closed-shell
- * molecules at the CIS (Tamm-Dancoff) and TDHF/RPA level on top of an NDDO
- * ground state, following arXiv:2505.24807 ("PySEQM 2.0"):
+ * The library computes the lowest singlet excitations (and, beyond the paper,
+ * the spin-adapted triplets) of closed-shell molecules at the CIS
+ * (Tamm-Dancoff) and TDHF/RPA level on top of an NDDO ground state, following
+ * arXiv:2505.24807 ("PySEQM 2.0"):
  *   - ground state: F C = C eps with S = I, restricted closed shell (Eq. 1);
  *   - RPA eigenproblem [[A,B],[B,A]][X;Y] = omega diag(I,-I)[X;Y] (Eq. rpa_eqn),
  *     CIS A X = omega X (Eq. cis_eqn);
@@ -14,8 +15,8 @@
  *     diagonal atom blocks and exchange called with the symmetric and
  *     antisymmetric parts of R (Section "GPU Implementation");
  *   - the batched Davidson steps 1-6 of the same section;
- *   - transition dipoles and oscillator strengths (Section "Results and
- *     discussion").
+ *   - transition dipoles and oscillator strengths, and the absorption
+ *     spectrum by Gaussian broadening (Section "Results and discussion").
  * Spin: singlet adaptation, A = d eps + 2(ia|jb) - (ij|ab),
  * B = 2(ia|jb) - (ib|ja) (the paper omits spin indices).
  *
