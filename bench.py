@@ -53,14 +53,26 @@ def peaks():
     return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_sustained=1700.0, source="fallback")
 
 
-# float64 and float32 SIMT FMA throughput of this GB300 measured by the
-# project's own probe kernel (paper_2505_24807_gb300/probe_peaks.cu): 1.195
-# and 72.99 TFLOP/s.
-FP64_SIMT_TFLOPS = 1.195
-FP32_SIMT_TFLOPS = 72.99
+# SIMT peaks from unit counts and the maximum clock: 152 SMs x 128 float32
+# lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s; float64: NVIDIA's 1.25 TFLOP/s
+# for the part (a warp-wide DFMA holds a sub-partition's float64 unit for 64
+# cycles: 152 x 4 x 32 / 64 x 2 x 2.07 GHz = 1.26 TFLOP/s).
+FP64_SIMT_TFLOPS = 1.25
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean over the captured launches of one solve of the
+# workload), from the ncu summaries named in "source"; a kernel absent here
+# (or changed since its capture) reports traffic null.
+TRAFFIC = {}
 
 
-def kernel_roofline(name, t, pk):
+def traffic_of(name, workload):
+    t = TRAFFIC.get((name, workload))
+    return (t["bytes_per_launch"], t["source"]) if t else (None, None)
+
+
+def kernel_roofline(name, t, pk, workload=None):
     """Achieved rate of one profiled kernel family against its bound: digit
     products, digit splits and the G build stream HBM (algorithmic bytes);
     tensor-core GEMMs against the TF32 peak; SIMT kernels against the float64
@@ -68,17 +80,21 @@ def kernel_roofline(name, t, pk):
     per_launch_s = t["ms"] / 1e3 / t["launches"]
     if name.startswith(("oz_", "gbuild")) and t["bytes"] > 0:
         ach = t["bytes"] / t["launches"] / per_launch_s / 1e9
+        traffic, tsrc = traffic_of(name, workload)
         return dict(kernel=name, bound="hbm", achieved=ach, peak=pk["hbm_gbs"], unit="GB/s",
-                    frac=ach / pk["hbm_gbs"], traffic=None, peak_source=pk["source"] + " hbm_gbs",
+                    frac=ach / pk["hbm_gbs"], traffic=traffic, traffic_source=tsrc,
+                    peak_source=pk["source"] + " hbm_gbs",
                     bytes_per_launch=t["bytes"] / t["launches"], ms_per_launch=per_launch_s * 1e3)
     ach = t["flops"] / t["launches"] / per_launch_s / 1e12
     if name.startswith("tc_"):
         peak, src, bound = pk["bf16_sustained"] / 2.0, pk["source"] + " bf16 sustained x 1/2 (tf32)", "tensor"
     elif "f64" in name:
-        peak, src, bound = FP64_SIMT_TFLOPS, "measured fp64 FMA probe", "alu"
+        peak, src, bound = FP64_SIMT_TFLOPS, "float64 SIMT, nominal 1.25 TFLOP/s", "alu"
     else:
-        peak, src, bound = FP32_SIMT_TFLOPS, "measured fp32 FMA probe", "alu"
-    return dict(kernel=name, bound=bound, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None,
+        peak, src, bound = FP32_SIMT_TFLOPS, "float32 SIMT, 152 SMs x 128 lanes x 2 x 2.07 GHz", "alu"
+    traffic, tsrc = traffic_of(name, workload)
+    return dict(kernel=name, bound=bound, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=traffic,
+                traffic_source=tsrc,
                 peak_source=src, flops_per_launch=t["flops"] / t["launches"], ms_per_launch=per_launch_s * 1e3)
 
 
@@ -166,28 +182,48 @@ def throughput(world, roots_per_solve, steps, seconds):
     return world * roots_per_solve * steps / seconds
 
 
-def cpu_sample(wl, seconds_budget=20.0):
-    """Oracle (A+B)X and (A-B)X products on the same molecule, seeded orbitals."""
-    from oracle import excited, nddo
-    params = molgen.make_params(0)
-    Z, xyz = wl["gen"](0)
-    mol = nddo.Molecule(Z, xyz, params)
-    t0 = time.perf_counter()
-    ints = nddo.Integrals(mol)
-    t_ints = time.perf_counter() - t0
-    Cm = molgen.orthonormal_matrix(11, mol.nao)
-    eps = np.sort(np.random.default_rng(3).uniform(-40.0, 10.0, mol.nao))
-    X = molgen.trial_vectors(5, 1, mol.nocc, mol.nvir)
-    n = 0
-    t0 = time.perf_counter()
-    while True:
-        excited.apply_kind(mol, ints, Cm, eps, mol.nocc, X, "ApB")
-        excited.apply_kind(mol, ints, Cm, eps, mol.nocc, X, "AmB")
-        n += 1
-        if time.perf_counter() - t0 > seconds_budget or n >= 64:
-            break
-    per_vector = (time.perf_counter() - t0) / n
-    return per_vector, n, t_ints
+def blas_threads():
+    """Threads of the BLAS that numpy uses (the oracle's products run there)."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d["num_threads"] for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except ImportError:
+        pass
+    import ctypes
+    import glob
+    libdir = os.path.join(os.path.dirname(np.__file__), "..", "numpy.libs")
+    for path in glob.glob(os.path.join(libdir, "*openblas*")):
+        lib = ctypes.CDLL(path)
+        for fn in ("scipy_openblas_get_num_threads64_", "openblas_get_num_threads64_", "openblas_get_num_threads"):
+            if hasattr(lib, fn):
+                return int(getattr(lib, fn)())
+    return None
+
+
+class OracleSample:
+    """The oracle's (A+B)X and (A-B)X products of one trial vector on the
+    workload's molecule with seeded orthonormal orbitals: the unit of work of
+    an oracle Davidson solve (its stored run counts these vectors)."""
+
+    def __init__(self, wl):
+        from oracle import excited, nddo
+        self.excited = excited
+        params = molgen.make_params(0)
+        Z, xyz = wl["gen"](0)
+        self.mol = nddo.Molecule(Z, xyz, params)
+        self.ints = nddo.Integrals(self.mol)
+        self.C = molgen.orthonormal_matrix(11, self.mol.nao)
+        self.eps = np.sort(np.random.default_rng(3).uniform(-40.0, 10.0, self.mol.nao))
+        self.X = molgen.trial_vectors(5, 1, self.mol.nocc, self.mol.nvir)
+
+    def product(self):
+        m = self.mol
+        t0 = time.perf_counter()
+        self.excited.apply_kind(m, self.ints, self.C, self.eps, m.nocc, self.X, "ApB")
+        self.excited.apply_kind(m, self.ints, self.C, self.eps, m.nocc, self.X, "AmB")
+        return time.perf_counter() - t0
 
 
 def oracle_products(workload, method):
@@ -204,25 +240,49 @@ def oracle_products(workload, method):
     return 200, "no stored oracle run: 200 products"
 
 
+def cpu_baseline_leg(wl, workload, seconds_budget=20.0):
+    """Oracle roots/s on the host cores, extrapolated from a bounded sample:
+    products timed for ~seconds_budget, times the oracle's own product count
+    per solve (its stored Davidson run of this molecule)."""
+    smp = OracleSample(wl)
+    times = []
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds_budget and len(times) < 64:
+        times.append(smp.product())
+    per_vector = float(np.mean(times))
+    prods, source = oracle_products(workload, "RPA" if wl["method"] == "TDHF" else "CIS")
+    value = wl["nroots"] / (per_vector * prods)
+    return dict(value=value, unit="roots/s", cores=os.cpu_count(), blas_threads=blas_threads(), kind="oracle",
+                extrapolated=True, sampled_products=len(times), products_per_solve=prods,
+                sample=f"{len(times)} oracle (A+B)X,(A-B)X trial-vector products on the {workload} molecule "
+                       f"(seeded orbitals), {per_vector:.3f} s each, x {prods} products per solve ({source})")
+
+
 def run_reference(args, wl):
+    """The oracle as the reference arm: every step is one bounded sample of the
+    workload -- the oracle's (A+B)X and (A-B)X products of one trial vector --
+    timed on the host cores; roots/s extrapolates to a whole solve with the
+    oracle's own Davidson product count."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    # each step: the oracle's products for the number of trial vectors the
-    # oracle's own Davidson needs on this workload (its stored run of the same
-    # molecule and method, else of the medium molecule), timed on a sample
-    per_vector, n, _ = cpu_sample(wl, seconds_budget=max(5.0, 20.0 / max(args.steps, 1)))
-    products_per_solve, source = oracle_products(args.workload, "RPA" if wl["method"] == "TDHF" else "CIS")
-    step_s = per_vector * products_per_solve
-    value = wl["nroots"] / step_s
+    smp = OracleSample(wl)
+    for _ in range(args.warmup):
+        smp.product()
+    step_s = [smp.product() for _ in range(max(args.steps, 1))]
+    per_vector = float(np.mean(step_s))
+    prods, source = oracle_products(args.workload, "RPA" if wl["method"] == "TDHF" else "CIS")
+    value = wl["nroots"] / (per_vector * prods)
+    sample = (f"each step: one trial vector's oracle (A+B)X and (A-B)X products on the {args.workload} molecule "
+              f"(seeded orbitals), {per_vector:.3f} s; roots/s = {wl['nroots']} roots / ({prods} products per "
+              f"solve ({source}) x the mean step)")
     line = dict(impl="reference", metric=METRIC, value=value, unit="roots/s", n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=step_s * 1e3, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=args.workload, desc=wl["desc"]),
+                warmup=args.warmup, ms_per_step=per_vector * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", extrapolated=True,
+                config=dict(workload=args.workload, desc=wl["desc"], step="one oracle product pair"),
                 cpu_baseline=dict(kind="oracle", value=value, unit="roots/s", cores=os.cpu_count(),
-                                  sample=f"{n} oracle (A+B)X,(A-B)X products on the {args.workload} molecule "
-                                         f"(seeded orbitals), {per_vector:.3f} s each, x{products_per_solve} "
-                                         f"products per solve ({source})"),
+                                  blas_threads=blas_threads(), extrapolated=True, products_per_solve=prods,
+                                  sample=sample),
                 e2e=dict(value=value, unit="roots/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -376,13 +436,14 @@ def main():
 
     for _ in range(args.warmup):
         solve()
-    # timed region: K solves bracketed by barrier + synchronize, CUDA events on the stream
+    # timed region: K solves bracketed by barrier + synchronize, CUDA events on
+    # the stream; the library only counts its launches here (no per-kernel events)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    xs.xs_profile(ctx, True)
+    xs.xs_profile(ctx, 2)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -391,8 +452,8 @@ def main():
         results.append(solve())
     e1.record(stream)
     torch.cuda.synchronize()
-    prof = xs.xs_profile_read(ctx)
-    xs.xs_profile(ctx, False)
+    counts = xs.xs_profile_read(ctx)
+    xs.xs_profile(ctx, 0)
     clk = clocks.stop()
     dev_ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
     if world > 1:
@@ -416,47 +477,94 @@ def main():
     e2e = dict(value=throughput(world, K, 1, e2e_s), unit="roots/s", h2d_bytes_per_step=8 * (nao * nao + nao),
                d2h_bytes_per_step=8 * 3 * K + 4)
 
-    # plain float64 GPU Davidson on the same molecule (the metric's denominator)
+    # one more solve with per-kernel CUDA events (outside the timed region):
+    # the kernel table and the rooflines
+    xs.xs_profile(ctx, 1)
+    solve()
+    prof = xs.xs_profile_read(ctx)
+    xs.xs_profile(ctx, 0)
+
+    def timed_solve(p, g, tol):
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        f0.record(stream)
+        r = xs.xs_excited(ctx, method=method, nroots=K, tol=tol, precision=p, guess=g)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        return r, f0.elapsed_time(f1) / 1e3
+
+    def record(r, sec):
+        return dict(value=K / sec, unit="roots/s", seconds=sec, iterations=int(r["info"]["iterations"]),
+                    products=int(r["info"]["products"]), tol_used_eV=r["info"]["tol_used"],
+                    converged=int(r["info"]["converged"]))
+
+    # the same mixed solve with the plain guess: the learned guess's own gain
+    plain_mixed = None
+    if prec == xs.XS_MIXED and guess == xs.XS_GUESS_LEARNED and not args.no_fp64_baseline:
+        rp, sp = timed_solve(prec, xs.XS_GUESS_PLAIN, wl["tol"])
+        plain_mixed = record(rp, sp)
+        plain_mixed["roots"] = rp
+
+    # plain float64 GPU Davidson on the same molecule (the metric's
+    # denominator), plain guess, stopping at the residual threshold the mixed
+    # solve applied (same stopping rule), and at the requested tolerance
     fp64 = None
     if not args.no_fp64_baseline and prec == xs.XS_MIXED:
         # a short untimed float64 solve first: the float64 path's GEMM shape
         # classes are autotuned on first use, as the mixed path's were in warm-up
         xs.xs_excited(ctx, method=method, nroots=K, tol=wl["tol"], precision=xs.XS_FP64,
                       guess=xs.XS_GUESS_PLAIN, max_iter=25, allow=(xs.XS_ENOCONV,))
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        r64 = solve(xs.XS_FP64, xs.XS_GUESS_PLAIN)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        s64 = f0.elapsed_time(f1) / 1e3
-        err = float(np.abs(last["omega"][0] - r64["omega"][0]).max())
-        fp64 = dict(value=K / s64, unit="roots/s", seconds=s64, iterations=int(r64["info"]["iterations"]),
-                    products=int(r64["info"]["products"]), max_abs_domega_vs_mixed_eV=err,
-                    speedup_of_chosen_form=(K / (ms_per_step / 1e3)) / (K / s64))
+        tol_same = float(last["info"]["tol_used"])
+        r64, s64 = timed_solve(xs.XS_FP64, xs.XS_GUESS_PLAIN, tol_same)
+        fp64 = record(r64, s64)
+        fp64["roots"] = r64
+        fp64["stopping_rule"] = f"residual <= {tol_same:g} eV (the mixed solve's)"
+        fp64["speedup_of_chosen_form"] = (K / (ms_per_step / 1e3)) / fp64["value"]
+        r64t, s64t = timed_solve(xs.XS_FP64, xs.XS_GUESS_PLAIN, wl["tol"])
+        fp64["at_requested_tol"] = record(r64t, s64t)
+        fp64["at_requested_tol"]["roots"] = r64t
 
-    # parity against the oracle's stored roots for this workload, when present
-    oracle_err = None
+    # per-root errors against the oracle's stored roots for this workload
+    golden = None
     gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}.json")
     if os.path.exists(gpath) and rank == 0:
         with open(gpath) as f:
             g = json.load(f)
         key = "RPA" if wl["method"] == "TDHF" else "CIS"
         if key in g["roots"]:
-            ref = np.array(g["roots"][key]["omega"])
-            oracle_err = float(np.abs(last["omega"][0][: len(ref)] - ref).max())
+            golden = (np.array(g["roots"][key]["omega"]), np.array(g["roots"][key]["f"]))
 
-    # roofline of the dominant kernel, from the library's CUDA-event profile
+    def per_root(r):
+        if golden is None or r is None:
+            return None
+        w, f = golden
+        n = min(len(w), K)
+        dw = np.abs(r["omega"][0][:n] - w[:n])
+        df = np.abs(r["osc"][0][:n] - f[:n])
+        return dict(abs_domega_eV=[float(x) for x in dw], abs_df=[float(x) for x in df],
+                    max_abs_domega_eV=float(dw.max()), max_abs_df=float(df.max()))
+
+    errors = dict(chosen=per_root(last))
+    for name, rec in (("mixed_plain_guess", plain_mixed), ("fp64_gpu", fp64),
+                      ("fp64_gpu_requested_tol", fp64["at_requested_tol"] if fp64 else None)):
+        if rec is not None:
+            errors[name] = per_root(rec.pop("roots"))
+    oracle_err = errors["chosen"]["max_abs_domega_eV"] if errors["chosen"] else None
+
+    # roofline of the dominant kernel, from the profiled solve
     pk = peaks()
     kernels = {k: v for k, v in prof.items()
                if k != "all_launches" and not k.startswith("host:") and v["launches"] > 0}
-    # host wall time of the solver's phases (setup, iteration loop, time spent
-    # waiting for the device at the per-iteration read-back), per step
-    host_phases = {k[5:]: round(v["ms"] / args.steps, 2) for k, v in prof.items() if k.startswith("host:")}
+    # host wall time of the solver's phases in the timed region (setup, iteration
+    # loop, time spent waiting for the device at the per-iteration read-back), per step
+    host_phases = {k[5:]: round(v["ms"] / args.steps, 2) for k, v in counts.items() if k.startswith("host:")}
     top_name = max(kernels, key=lambda k: kernels[k]["ms"]) if kernels else None
-    roof = kernel_roofline(top_name, kernels[top_name], pk) if top_name else None
+    roof = kernel_roofline(top_name, kernels[top_name], pk, args.workload) if top_name else None
     # the A.X product itself: its transforms (tensor cores) and G build (HBM)
-    ax = {k: kernel_roofline(k, kernels[k], pk) for k in kernels if k.startswith(("tc_gemm", "gbuild"))}
+    ax = {k: kernel_roofline(k, kernels[k], pk, args.workload) for k in kernels
+          if k.startswith(("tc_gemm", "gbuild", "coulomb"))}
+
     def _rate(v):
         sec = v["ms"] / 1e3
         out = {}
@@ -466,18 +574,14 @@ def main():
             out["TFLOPps"] = round(v["flops"] / sec / 1e12, 2)
         return out
 
-    kernel_table = {k: dict(launches=v["launches"], ms=round(v["ms"], 3),
-                            share=round(v["ms"] / max(sum(x["ms"] for x in kernels.values()), 1e-9), 4), **_rate(v))
+    total_ms = max(sum(x["ms"] for x in kernels.values()), 1e-9)
+    kernel_table = {k: dict(launches=v["launches"], ms=round(v["ms"], 3), share=round(v["ms"] / total_ms, 4),
+                            **_rate(v))
                     for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["ms"])}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        per_vector, n, _ = cpu_sample(wl, seconds_budget=20.0)
-        prods = int(last["info"]["products"])
-        cpu_value = K / (per_vector * max(prods, 1))
-        cpu = dict(value=cpu_value, unit="roots/s", cores=os.cpu_count(), kind="oracle",
-                   sample=f"{n} oracle (A+B)X,(A-B)X product pairs on the {args.workload} molecule with seeded "
-                          f"orbitals ({per_vector:.3f} s each) x {prods} products of the GPU solve")
+        cpu = cpu_baseline_leg(wl, args.workload, seconds_budget=20.0)
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="roots/s", n_gpus=world, steps=args.steps,
@@ -487,15 +591,18 @@ def main():
                     data="synthetic",
                     config=dict(workload=args.workload, desc=wl["desc"], precision=args.precision,
                                 guess="learned" if guess == xs.XS_GUESS_LEARNED else "plain",
-                                nao=nao, nocc=nocc, tol_eV=wl["tol"], l2="working set > L2 (V, (A+B)V, (A-B)V)",
+                                nao=nao, nocc=nocc, tol_eV=wl["tol"], tol_used_eV=last["info"]["tol_used"],
+                                l2="inputs larger than L2 (V, (A+B)V, (A-B)V: ~12 GB working set)",
                                 setup_seconds=round(setup_s, 3), scf_iterations=gs["max_scf_iter_used"]),
                     iterations=int(last["info"]["iterations"]), products=int(last["info"]["products"]),
                     converged=int(last["info"]["converged"]),
-                    max_abs_err_vs_oracle_eV=oracle_err,
-                    roofline=roof, ax_product=ax, kernels=kernel_table, host_ms_per_step=host_phases,
+                    max_abs_err_vs_oracle_eV=oracle_err, errors_vs_oracle=errors,
+                    roofline=roof, ax_product=ax, kernels=kernel_table,
+                    kernels_note="per-kernel CUDA events from one extra untimed solve",
+                    host_ms_per_step=host_phases,
                     cpu_baseline=cpu, e2e=e2e,
-                    gpu_launches=int(prof.get("all_launches", {}).get("launches", 0)),
-                    clocks=clk, fp64_gpu=fp64)
+                    gpu_launches=int(counts.get("all_launches", {}).get("launches", 0)),
+                    clocks=clk, mixed_plain_guess=plain_mixed, fp64_gpu=fp64)
         print(json.dumps(line), flush=True)
     xs.xs_destroy(ctx)
     if world > 1:

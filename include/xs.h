@@ -99,7 +99,11 @@ typedef struct {
 typedef struct {
   int method;        /* XS_CIS or XS_TDHF */
   int nroots;        /* roots per molecule (>= 1) */
-  double tol;        /* residual 2-norm threshold in eV */
+  double tol;        /* residual 2-norm threshold in eV.  XS_MIXED solves apply max(tol, 1e-4 eV):
+                        their products carry ~1e-6 relative rounding, so residuals stall near 1e-5 eV,
+                        while the energies (quadratic in the residual, then refined by a float32
+                        Rayleigh-Ritz step) still land within ~5e-6 eV.  The threshold applied is
+                        returned in xs_solve_info.tol_used */
   int precision;     /* XS_FP64 or XS_MIXED */
   int guess;         /* XS_GUESS_PLAIN or XS_GUESS_LEARNED */
   int max_subspace;  /* subspace cap per molecule (0: library default) */
@@ -127,6 +131,7 @@ typedef struct {
   double seconds;       /* wall time of the call */
   double seconds_products;  /* of which in A*X products */
   int max_subspace_used;    /* subspace cap in effect (largest over the molecules) */
+  double tol_used;          /* residual threshold applied (eV): opts->tol, or its mixed-precision floor */
 } xs_solve_info;
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t to
@@ -225,11 +230,11 @@ int xs_mlp_train(xs_ctx* ctx, int rows, const float* features, const float* targ
                  float lr, float* loss);
 
 /* Allocation-free G(R) build: the same G = 2J(R) - K(R) as
- * xs_apply(ctx, mol, XS_KIND_G, nvec, R, G, XS_FP64), for callers that must not
- * allocate device memory during the call -- work recorded inside CUDA stream
- * capture, or a process whose device memory belongs to another allocator's
- * pool, where a cudaMalloc would fail or break the capture.  No counterpart in
- * the paper.
+ * xs_apply(ctx, mol, XS_KIND_G, nvec, R, G, XS_FP64), for callers that cannot
+ * call cudaMalloc during the call: a process whose device memory is reserved
+ * up front by another allocator's pool (a framework's caching allocator), or
+ * a latency-critical loop that must not meet cudaMalloc's implicit device
+ * synchronisation.  No counterpart in the paper.
  *   R, G: DEVICE pointers to nvec n x n row-major float64 matrices, owned by
  *   the caller (molecule `mol` must have its ground state already).
  * Scratch comes from one fixed device array of 2^18 doubles (2 MiB) compiled
@@ -279,7 +284,10 @@ int xs_spectrum(xs_ctx* ctx, int n, const double* omega, const double* f, double
 
 /* Per-kernel timing.  xs_profile(ctx, 1) clears and enables it: every
  * instrumented kernel launch of later calls is bracketed by CUDA events on
- * the launching stream; xs_profile(ctx, 0) disables it.  xs_profile_read
+ * the launching stream; xs_profile(ctx, 2) clears and enables counting only
+ * (launches, algorithmic bytes and flops, host phases; no CUDA events, ms = 0
+ * for kernels), which leaves device timings undisturbed; xs_profile(ctx, 0)
+ * disables it.  xs_profile_read
  * synchronises the context's stream and copies up to max_entries entries
  * (one per kernel name: launches, summed device milliseconds, summed
  * algorithmic bytes and flops) and the number of entries into *count.

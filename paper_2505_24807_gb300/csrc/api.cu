@@ -357,6 +357,7 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
       inf.learned = inf.learned || st.learned;
       inf.fallback = inf.fallback || st.fallback;
       inf.max_subspace_used = st.smax > inf.max_subspace_used ? st.smax : inf.max_subspace_used;
+      inf.tol_used = st.tol_used > inf.tol_used ? st.tol_used : inf.tol_used;
       tprod += st.seconds_products;
       const int kk = m.nroots;
       std::vector<double> pad(K, 0.0);
@@ -590,8 +591,10 @@ int xs_mlp_train(xs_ctx* ctx, int rows, const float* features, const float* targ
 
 int xs_profile(xs_ctx* ctx, int enable) {
   return guarded(ctx, [&](Ctx& c) {
+    if (enable < 0 || enable > 2) throw Error(XS_EINVAL, "xs_profile: enable must be 0, 1 or 2");
     c.prof.reset();
     c.prof.on = enable != 0;
+    c.prof.events = enable == 1;
     return XS_OK;
   });
 }

@@ -373,6 +373,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   // residuals cannot fall much below 1e-5 eV; the energies, quadratic in the
   // residual, are still converged far below 1e-5 eV at a 1e-4 eV residual.
   const double tol_eff = (opt.precision == XS_MIXED) ? std::max(opt.tol, kMixedResidualFloor) : opt.tol;
+  st.tol_used = tol_eff;
 
   HostScope h_setup("host:setup");
   // the workspace persists in the context between solves (buffers only grow):

@@ -15,6 +15,7 @@ struct SolveStats {
   bool fallback = false;   // the learned shift was dropped for a stalled residual
   double seconds_products = 0.0;
   int smax = 0;            // subspace cap in effect
+  double tol_used = 0.0;   // residual threshold applied (eV)
 };
 
 // Solves molecule m; stores roots, oscillator strengths, residuals and

@@ -1,11 +1,12 @@
 // Allocation-free G(R) build (declared in include/xs.h as xs_gbuild_noalloc).
 //
-// For callers that cannot allocate device memory while they call into the
-// library -- work recorded inside CUDA stream capture, or processes whose
-// device memory belongs to another allocator's pool -- the two scratch
-// vectors of the G build (packed diagonal blocks r and the Coulomb products
-// J2) come from one fixed array compiled into the library instead of from
-// cudaMalloc.  The kernels are the ones the allocating path launches.
+// For callers that cannot call cudaMalloc while they call into the library --
+// a process whose device memory is reserved up front by another allocator's
+// pool, or a latency-critical loop that must not meet cudaMalloc's implicit
+// device synchronisation -- the two scratch vectors of the G build (packed
+// diagonal blocks r and the Coulomb products J2) come from one fixed array
+// compiled into the library instead of from cudaMalloc.  The kernels are the
+// ones the allocating path launches.
 #include <mutex>
 #include <vector>
 

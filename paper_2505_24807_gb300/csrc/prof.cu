@@ -46,6 +46,10 @@ ProfScope::ProfScope(cudaStream_t stream, const char* name, double bytes, double
   ent->launches += 1;
   ent->bytes += bytes;
   ent->flops += flops;
+  if (!g_prof->events) {
+    ent = nullptr;
+    return;
+  }
   s = stream;
   a = g_prof->get();
   b = g_prof->get();

@@ -22,6 +22,7 @@ struct ProfEntry {
 
 struct Profiler {
   bool on = false;
+  bool events = true;       // false: count launches, bytes and flops only
   long long launches = 0;   // every kernel launch of the library while on
   std::map<std::string, ProfEntry> e;
   std::vector<cudaEvent_t> pool;

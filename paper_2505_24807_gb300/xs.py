@@ -48,7 +48,8 @@ class xs_ex_opts(C.Structure):
 class xs_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("products", C.c_longlong), ("converged", C.c_int),
                 ("polished", C.c_int), ("learned", C.c_int), ("fallback", C.c_int), ("seconds", C.c_double),
-                ("seconds_products", C.c_double), ("max_subspace_used", C.c_int)]
+                ("seconds_products", C.c_double), ("max_subspace_used", C.c_int),
+                ("tol_used", C.c_double)]
 
 
 class xs_prof_entry(C.Structure):
@@ -322,7 +323,8 @@ def xs_mlp_train(ctx, features, targets, epochs=10, batch=4096, lr=1e-3):
 
 
 def xs_profile(ctx, enable=True):
-    return _check(ctx, load().xs_profile(ctx, int(bool(enable))))
+    """enable: True / 1 (CUDA-event timing), 2 (counts only), False / 0 (off)."""
+    return _check(ctx, load().xs_profile(ctx, int(enable)))
 
 
 def xs_profile_read(ctx):

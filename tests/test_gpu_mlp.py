@@ -106,4 +106,34 @@ def test_learned_guess_keeps_roots_and_cuts_iterations():
     assert learned["info"]["learned"] == 1
     assert np.abs(learned["omega"] - plain["omega"]).max() < 1e-6
     print("iterations plain", plain["iters"], "learned", learned["iters"], "loss", loss[0], loss[-1])
+    # a 16-molecule network trained in seconds: it must not cost iterations;
+    # the committed network's gain is asserted below
     assert learned["iters"].mean() <= plain["iters"].mean()
+
+
+def test_committed_network_cuts_iterations_on_held_out_molecules():
+    """The committed network (paper_2505_24807_gb300/guess_weights.f32, trained
+    on molecules of 20-120 atoms with seeds 1000-5095) on 16 held-out
+    molecules of 20-300 atoms (seeds 9000-9015, the first of the benchmark's
+    held-out set), batched TDHF, 8 roots: the same roots as the plain
+    Davidson, and at least 10 % fewer mean iterations."""
+    import os
+    path = os.path.join(os.path.dirname(xs.__file__), "guess_weights.f32")
+    weights = np.fromfile(path, dtype=np.float32)
+    assert weights.size == xs.xs_mlp_nparams()
+    params = molgen.make_params(0)
+    mols = [molgen.config_sized(9000 + s, 20 + (s * 4099) % 281) for s in range(16)]
+    ctx = context(params)
+    try:
+        xs.xs_mlp_set_weights(ctx.h, weights)
+        xs.xs_ground_state(ctx.h, mols)
+        run = dict(method=xs.XS_TDHF, nroots=8, tol=1e-5, precision=xs.XS_FP64, batched=1, n_mol=len(mols))
+        plain = xs.xs_excited(ctx.h, guess=xs.XS_GUESS_PLAIN, **run)
+        learned = xs.xs_excited(ctx.h, guess=xs.XS_GUESS_LEARNED, **run)
+    finally:
+        ctx.close()
+    assert learned["info"]["learned"] == 1
+    assert plain["info"]["converged"] == 1 and learned["info"]["converged"] == 1
+    assert np.abs(learned["omega"] - plain["omega"]).max() < 1e-6
+    print("mean iterations plain", plain["iters"].mean(), "learned", learned["iters"].mean())
+    assert learned["iters"].mean() <= 0.9 * plain["iters"].mean()

@@ -145,3 +145,34 @@ def test_overlap_rotational_covariance(params0):
     # antisymmetry of the s-p part under exchange of the atoms
     S21 = nddo.sk_overlap_block(mol, 1, 0)
     assert np.allclose(S21, S.T, atol=1e-14)
+
+
+def test_one_centre_dipole_term_is_the_product_density_dipole(params0):
+    # <s|r_j|p_i> of the dipole integrals must be the dipole moment of the
+    # model density rho_{s p_i}, whose Coulomb field defines the two-centre
+    # integrals: far from atom A, (s p_i | s_B s_B) -> kappa d_i . (R_B - R_A) / R^3
+    # (erf(aR) = 1 to ~1e-40 at R = 12 Angstrom).  A flipped sign or a wrong
+    # scale of the one-centre term in dipole_integrals fails here.
+    rng = np.random.default_rng(17)
+    dirs = rng.normal(size=(4, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    RA = np.array([0.3, -0.2, 0.1])
+    for z in (6, 7, 8):
+        Z = np.array([z] + [1] * len(dirs) + ([1] if (nddo.CORE_CHARGE[z] + len(dirs)) % 2 else []))
+        far = [RA + 12.0 * d for d in dirs]
+        extra = [RA + np.array([0.0, 0.0, 40.0])] if len(Z) > 1 + len(dirs) else []
+        xyz = np.array([RA] + far + extra)
+        mol = nddo.Molecule(Z, xyz, params0)
+        ints = nddo.Integrals(mol)
+        dip = nddo.dipole_integrals(mol)
+        o = mol.ao_offset[0]
+        for B in range(1, 1 + len(dirs)):
+            Rv = mol.xyz[B] - mol.xyz[0]
+            R = np.linalg.norm(Rv)
+            w = ints.pair_block(0, B)          # (mu nu | s_B s_B), mu nu on the heavy atom
+            for i in range(3):
+                d_si = dip[:, o, o + 1 + i]    # <s| r |p_i>, Angstrom
+                expected = nddo.KAPPA * float(d_si @ Rv) / R ** 3
+                assert w[0, 1 + i, 0, 0] == pytest.approx(expected, rel=1e-9, abs=1e-12), (z, B, i)
+                # and the matrix is symmetric in s, p_i
+                assert np.allclose(dip[:, o + 1 + i, o], d_si, atol=0.0)
