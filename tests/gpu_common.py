@@ -23,3 +23,33 @@ def rel_err(a, b):
     a = np.asarray(a)
     b = np.asarray(b)
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def mixed_product_tol(n):
+    """Bound on max|Y - ref| / max|ref - de X| for the mixed-precision product
+    (split-TF32 tensor-core transforms, float32 G build) of an n-AO molecule.
+
+    The product chains four split-TF32 GEMMs, each contracting over at most n
+    terms.  The tensor cores add every 8-term MMA step into a float32
+    accumulator with truncation, which biases each output by about
+    (K / 8) steps x half an ulp (2^-24) x 2/3 of the final magnitude (the
+    mean running sum of random-signed terms): (K / 12) 2^-24 relative per GEMM.
+    Each GEMM also drops lo*lo (2^-22 relative) and reads lo rounded to TF32
+    (2 x 2^-22), and stores its output in float32.  Summed over the four
+    GEMMs, with a factor 2 of headroom.  The exact float64 term de*X carries
+    no rounding, so the error is measured against the rest of the product
+    (C_occ^T G C_vir).  Measured on a GB300: 1.9e-6 at n = 62, 5.8e-6 at
+    n = 220, 1.3e-5 at n = 600, 4.7e-5 at n = 2200 (this bound: 8.2e-6,
+    1.4e-5, 3.0e-5, 9.3e-5)."""
+    per_gemm = (n / 12.0) * 2.0 ** -24 + 3.0 * 2.0 ** -22
+    return 2.0 * 4.0 * per_gemm
+
+
+def mixed_product_err(Y, ref, X, eps, nocc):
+    """max|Y - ref| / max|ref - de X| (see mixed_product_tol)."""
+    from oracle import excited
+    Y = np.asarray(Y).reshape(len(X), -1)
+    ref = np.asarray(ref).reshape(len(X), -1)
+    de = excited.delta_eps(eps, nocc).reshape(-1)
+    g_part = ref - de[None, :] * np.asarray(X).reshape(len(X), -1)
+    return float(np.abs(Y - ref).max() / np.abs(g_part).max())

@@ -6,13 +6,14 @@ given to both sides (the library receives them through xs_set_orbitals, so no
 input of the oracle comes from the GPU path).
 
 Tolerances as in the small-size parity tests: float64 products to 1e-10
-relative to the largest element (rounding order only), mixed products to 3e-5.
+relative to the largest element (rounding order only), mixed products within
+mixed_product_tol(2200) of the non-diagonal part (tests/gpu_common.py).
 """
 import numpy as np
 import pytest
 
 import molgen
-from tests.gpu_common import context, rel_err
+from tests.gpu_common import context, mixed_product_err, mixed_product_tol, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +34,7 @@ def large_case():
     ctx = context(params)
     xs.xs_ground_state(ctx.h, [(Z, xyz)])
     xs.xs_set_orbitals(ctx.h, 0, Cm, eps)
-    yield dict(ctx=ctx, X=X.reshape(2, -1), ref=ref, nocc=mol.nocc, nao=mol.nao)
+    yield dict(ctx=ctx, X=X.reshape(2, -1), ref=ref, nocc=mol.nocc, nao=mol.nao, eps=eps)
     ctx.close()
 
 
@@ -46,4 +47,7 @@ def test_large_products_match_oracle(large_case, kind, okind, precision):
     prec = xs.XS_MIXED if precision == "mixed" else xs.XS_FP64
     got = xs.xs_apply(c["ctx"].h, 0, okind, c["X"], precision=prec)
     ref = c["ref"][kind].reshape(2, -1)
-    assert rel_err(got, ref) < (3e-5 if precision == "mixed" else 1e-10)
+    if precision == "mixed":
+        assert mixed_product_err(got, ref, c["X"], c["eps"], c["nocc"]) < mixed_product_tol(c["nao"])
+    else:
+        assert rel_err(got, ref) < 1e-10
