@@ -108,7 +108,14 @@ typedef struct {
   int guess;         /* XS_GUESS_PLAIN or XS_GUESS_LEARNED */
   int max_subspace;  /* subspace cap per molecule (0: library default) */
   int max_iter;      /* Davidson iteration cap (0: library default) */
-  int batched;       /* 1: all molecules advance together, one launch per step */
+  int batched;       /* 0: molecules one after another (each with its own launch sequence);
+                        1: lock-step batch -- every molecule of the last xs_ground_state call advances
+                        one Davidson iteration per replay of one captured CUDA graph whose kernels walk
+                        device-side work lists over all molecules (no zero padding; converged molecules
+                        retire on the device); up to 16 roots, subspaces of at most 64 vectors, products
+                        in float32 SIMT (XS_MIXED) or float64 (XS_FP64), float64 subspace; with the
+                        learned guess it runs as form 2;
+                        2: molecules concurrently, each on its own stream and host thread */
   int subspace;      /* float64 subspace products: XS_SUBSPACE_AUTO (0), XS_SUBSPACE_FP64 (1, the
                         float64 pipe) or XS_SUBSPACE_EMULATED (2, exact digit splitting on the tensor
                         cores, see xs_subspace_gram); AUTO = EMULATED for XS_MIXED solves of
@@ -132,6 +139,7 @@ typedef struct {
   double seconds_products;  /* of which in A*X products */
   int max_subspace_used;    /* subspace cap in effect (largest over the molecules) */
   double tol_used;          /* residual threshold applied (eV): opts->tol, or its mixed-precision floor */
+  long long graph_launches; /* lock-step batched solves (batched = 1): CUDA graph replays, one per iteration */
 } xs_solve_info;
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t to

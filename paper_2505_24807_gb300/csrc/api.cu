@@ -6,6 +6,7 @@
 #include <thread>
 #include <vector>
 
+#include "batch.h"
 #include "davidson.h"
 #include "mlp.h"
 #include "ozaki.h"
@@ -304,7 +305,14 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
     const int nmol = static_cast<int>(c.mols.size());
     std::vector<xs::SolveStats> stats(nmol);
     std::vector<int> rcs(nmol, XS_OK);
-    if (o.batched && nmol > 1) {
+    if (o.batched < 0 || o.batched > 2) throw Error(XS_EINVAL, "batched must be 0, 1 or 2");
+    // the lock-step form takes the plain guess; learned-guess batches run concurrently
+    const int form = (o.batched == 1 && o.guess == XS_GUESS_LEARNED && c.mlp && c.mlp->ready) ? 2 : o.batched;
+    if (form == 1) {
+      long long replays = 0;
+      xs::davidson_batched(c, o, stats, rcs, &replays);
+      inf.graph_launches = replays;
+    } else if (form == 2 && nmol > 1) {
       // molecules advance concurrently: one host thread per worker context,
       // each launching on its own stream; the GPU overlaps their kernels
       unsigned hw = std::thread::hardware_concurrency();

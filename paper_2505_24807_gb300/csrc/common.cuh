@@ -108,6 +108,7 @@ struct Ctx {
   Profiler prof;
   DevBuf<int> tc_err;   // error word of the tensor-core kernels' bounded waits
   std::shared_ptr<void> dav_cache;  // Davidson workspace kept between solves (davidson.cu)
+  std::shared_ptr<void> batch_cache;  // lock-step batched solver's arenas (batch.cu)
   // batched solves: worker contexts (own stream and scratch), reused across calls
   std::vector<std::unique_ptr<Ctx>> workers;
   // learned guess / preconditioner network (shared by the workers)

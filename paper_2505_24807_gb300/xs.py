@@ -49,7 +49,7 @@ class xs_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("products", C.c_longlong), ("converged", C.c_int),
                 ("polished", C.c_int), ("learned", C.c_int), ("fallback", C.c_int), ("seconds", C.c_double),
                 ("seconds_products", C.c_double), ("max_subspace_used", C.c_int),
-                ("tol_used", C.c_double)]
+                ("tol_used", C.c_double), ("graph_launches", C.c_longlong)]
 
 
 class xs_prof_entry(C.Structure):
