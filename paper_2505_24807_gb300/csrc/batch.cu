@@ -60,13 +60,14 @@ enum StField {
   F_NKEEP,      // directions kept by the Loewdin step
   F_KQ,         // eigenvectors kept by the eigensolver (CIS)
   F_PROD,       // trial vectors multiplied so far
+  F_GS2,        // 1: a second Gram-Schmidt pass is needed
   kSt = 16
 };
 enum Status { BS_ACTIVE = 0, BS_CONVERGED = 1, BS_STALLED = 2, BS_MAXITER = 3, BS_UNSTABLE = 4 };
 
 constexpr double kLowdinThresh = 1e-14;
 constexpr double kMixedResidualFloor = 1e-4;
-constexpr int kGramChunk = 4096;   // amplitudes per partial Gram block
+constexpr int kGramChunk = 1024;   // amplitudes per partial Gram block
 constexpr int kCombChunk = 256;    // amplitudes per combination work unit
 
 // ---- per-molecule descriptor (device) ----------------------------------------
@@ -98,6 +99,7 @@ struct BCfg {
   int rpa, triplet, coulomb, mode;    // GMode of the G build
   int max_iter;
   double tol;
+  int pass;                           // Gram-Schmidt pass of the launch (0 or 1)
 };
 
 __device__ __forceinline__ double de_of(const BMol& d, long long l) {
@@ -511,6 +513,7 @@ __device__ __forceinline__ bool gr_live(const int* st, int m, const BCfg& cfg) {
   if (ROLE == GR_OSC) return sf(st, m, F_STATUS) != BS_UNSTABLE && !cfg.triplet;
   if (!active(st, m)) return false;
   if (ROLE == GR_PROJ) return sf(st, m, F_NNEW) > 0;
+  if (ROLE == GR_GS && cfg.pass == 1) return sf(st, m, F_NDIR) > 0 && sf(st, m, F_GS2);
   return sf(st, m, F_NDIR) > 0;
 }
 template <int ROLE>
@@ -541,56 +544,61 @@ __device__ __forceinline__ const double* gr_b(const BMol& d, const int* st, int 
   return d.T + (size_t)c * d.ov;
 }
 
+// The float64 pipe of this part issues one warp instruction per 64 cycles
+// per sub-partition whatever the number of active lanes, so only the live
+// rows x cols outputs are computed: with P outputs, f = 256 / P threads (a
+// power of two, at most 32) share each output over interleaved amplitudes and
+// combine by warp shuffles; above 256 outputs each thread takes up to 16.
 template <int ROLE>
 __global__ void __launch_bounds__(256) bgram_kernel(const BMol* __restrict__ mols, const int* __restrict__ st,
                                                     BCfg cfg) {
   __shared__ double As[32][65];
   __shared__ double Bs[32][65];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x;
   RAGGED_PROLOGUE([&](int m) { return gr_live<ROLE>(st, m, cfg) ? mols[m].nch : 0; }) {
     const int m = find_mol(pref, cfg.nmol, u);
     const BMol& d = mols[m];
     const int ch = u - pref[m];
     const int rows = gr_rows<ROLE>(d, st, m), cols = gr_cols<ROLE>(d, st, m, cfg);
+    const int P = rows * cols;
+    int f = 1;
+    while (f < 32 && P * (2 * f) <= 256) f <<= 1;
+    const int ln = tid & (f - 1), og = tid / f, npo = 256 / f;
+    int ai[16], bc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int o = og + q * npo;
+      ai[q] = o < P ? o / cols : -1;
+      bc[q] = o < P ? o - (o / cols) * cols : 0;
+    }
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
     const long long l0 = (long long)ch * kGramChunk, l1 = min(d.ov, l0 + kGramChunk);
-    double acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
     for (long long lb = l0; lb < l1; lb += 32) {
       __syncthreads();
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int e = tid + 256 * q;
-        const int i = e >> 5, ll = e & 31;
+      for (int e = tid; e < (rows + cols) * 32; e += 256) {
+        const int r = e >> 5, ll = e & 31;
         const long long l = lb + ll;
-        As[ll][i] = (i < rows && l < l1) ? gr_a<ROLE>(d, i)[l] : 0.0;
-        Bs[ll][i] = (i < cols && l < l1) ? gr_b<ROLE>(d, st, m, i)[l] : 0.0;
+        if (r < rows) As[ll][r] = l < l1 ? gr_a<ROLE>(d, r)[l] : 0.0;
+        else Bs[ll][r - rows] = l < l1 ? gr_b<ROLE>(d, st, m, r - rows)[l] : 0.0;
       }
       __syncthreads();
-#pragma unroll 8
-      for (int ll = 0; ll < 32; ++ll) {
-        double a[4], b[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          a[q] = As[ll][ty + 16 * q];
-          b[q] = Bs[ll][tx + 16 * q];
-        }
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+      for (int q = 0; q < 16; ++q) {
+        if (ai[q] < 0) break;
+        double a = acc[q];
+        for (int ll = ln; ll < 32; ll += f) a = fma(As[ll][ai[q]], Bs[ll][bc[q]], a);
+        acc[q] = a;
       }
     }
     double* part = d.gpart + (size_t)ch * 4096;
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = ty + 16 * p, c = tx + 16 * q;
-        if (i < rows && c < cols) part[i * 64 + c] = acc[p][q];
-      }
+    for (int q = 0; q < 16; ++q) {
+      double a = acc[q];
+      for (int o = 1; o < f; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (ai[q] >= 0 && ln == 0) part[ai[q] * 64 + bc[q]] = a;
+    }
   }
 }
 
@@ -643,9 +651,9 @@ __device__ __forceinline__ int cb_which(const BCfg& cfg) {
   return ROLE == CB_COLL ? (cfg.rpa ? 3 : 2) : 1;
 }
 template <int ROLE>
-__device__ __forceinline__ bool cb_live(const int* st, int m) {
+__device__ __forceinline__ bool cb_live(const int* st, int m, int pass) {
   if (!active(st, m)) return false;
-  if (ROLE == CB_GS) return sf(st, m, F_NDIR) > 0;
+  if (ROLE == CB_GS) return sf(st, m, F_NDIR) > 0 && (pass == 0 || sf(st, m, F_GS2));
   if (ROLE == CB_APPEND) return sf(st, m, F_NKEEP) > 0;
   if (ROLE == CB_COLL) return sf(st, m, F_COLL) != 0;
   return true;
@@ -714,16 +722,16 @@ __device__ __forceinline__ void cb_column(const CbJob& j, const double* cs, long
 template <int ROLE>
 __global__ void __launch_bounds__(256) bcombine_kernel(const BMol* __restrict__ mols, const int* __restrict__ st,
                                                        BCfg cfg) {
-  extern __shared__ double cs[];   // nb x rows x NOUT coefficients (NOUT = 8, 16 or 32)
+  extern __shared__ double cs[];   // nb x rows x NOUT coefficients (NOUT: nout rounded up to a power of two)
   RAGGED_PROLOGUE([&](int m) {
-    return cb_live<ROLE>(st, m) ? cb_which<ROLE>(cfg) * cdiv(mols[m].ov, kCombChunk) : 0;
+    return cb_live<ROLE>(st, m, cfg.pass) ? cb_which<ROLE>(cfg) * cdiv(mols[m].ov, kCombChunk) : 0;
   }) {
     const int m = find_mol(pref, cfg.nmol, u);
     const BMol& d = mols[m];
     const int nchk = cdiv(d.ov, kCombChunk);
     const int lu = u - pref[m], which = lu / nchk, ch = lu - which * nchk;
     const CbJob j = cb_job<ROLE>(d, st, m, which, cfg);
-    const int NO = j.nout <= 8 ? 8 : (j.nout <= 16 ? 16 : 32);
+    const int NO = j.nout <= 1 ? 1 : j.nout <= 2 ? 2 : j.nout <= 4 ? 4 : j.nout <= 8 ? 8 : (j.nout <= 16 ? 16 : 32);
     __syncthreads();   // the previous unit's reads of cs are done
     for (int idx = threadIdx.x; idx < j.nb * j.rows * NO; idx += blockDim.x) {
       const int b = idx / (j.rows * NO), r = idx - b * (j.rows * NO);
@@ -733,10 +741,108 @@ __global__ void __launch_bounds__(256) bcombine_kernel(const BMol* __restrict__ 
     __syncthreads();
     const long long l = (long long)ch * kCombChunk + threadIdx.x;
     if (l >= d.ov) continue;
-    if (NO == 8) cb_column<8>(j, cs, d.ov, l);
-    else if (NO == 16) cb_column<16>(j, cs, d.ov, l);
-    else cb_column<32>(j, cs, d.ov, l);
+    switch (NO) {
+      case 1: cb_column<1>(j, cs, d.ov, l); break;
+      case 2: cb_column<2>(j, cs, d.ov, l); break;
+      case 4: cb_column<4>(j, cs, d.ov, l); break;
+      case 8: cb_column<8>(j, cs, d.ov, l); break;
+      case 16: cb_column<16>(j, cs, d.ov, l); break;
+      default: cb_column<32>(j, cs, d.ov, l); break;
+    }
   }
+}
+
+// Ritz vectors and residuals, one thread per amplitude with the subspace
+// coefficients in shared memory; only the products that are not zero are
+// formed (the float64 pipe is the limit).
+//   CIS:  X_j = V q_j, R_j = (A V) q_j - omega_j X_j        -> Xb rows [X | R]
+//   TDHF: p_j = V cu_j (X+Y), q_j = V cw_j (X-Y), r1_j = (A+B)V cu_j - omega_j q_j,
+//         r2_j = (A-B)V cw_j - omega_j p_j                   -> Xb [p | q], Rb [r1 | r2]
+template <int KK, bool RPA>
+__device__ __forceinline__ void ritz_column(const BMol& d, int S, const double* cq, const double* om, long long l) {
+  const long long ov = d.ov;
+  double p[KK], q[KK], a[KK], b[KK];
+#pragma unroll
+  for (int j = 0; j < KK; ++j) { p[j] = 0.0; q[j] = 0.0; a[j] = 0.0; b[j] = 0.0; }
+  for (int s = 0; s < S; ++s) {
+    const double v = d.V[(size_t)s * ov + l];
+    const double y = d.S1[(size_t)s * ov + l];
+    const double* c = cq + (size_t)s * (RPA ? 2 * KK : KK);
+    if (RPA) {
+      const double z = d.S2[(size_t)s * ov + l];
+#pragma unroll
+      for (int j = 0; j < KK; ++j) {
+        p[j] = fma(c[j], v, p[j]);
+        q[j] = fma(c[KK + j], v, q[j]);
+        a[j] = fma(c[j], y, a[j]);
+        b[j] = fma(c[KK + j], z, b[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < KK; ++j) {
+        p[j] = fma(c[j], v, p[j]);
+        a[j] = fma(c[j], y, a[j]);
+      }
+    }
+  }
+  const int kk = d.kk;
+#pragma unroll
+  for (int j = 0; j < KK; ++j) {
+    if (j >= kk) break;
+    if (RPA) {
+      d.Xb[(size_t)j * ov + l] = p[j];
+      d.Xb[(size_t)(kk + j) * ov + l] = q[j];
+      d.Rb[(size_t)j * ov + l] = a[j] - om[j] * q[j];
+      d.Rb[(size_t)(kk + j) * ov + l] = b[j] - om[j] * p[j];
+    } else {
+      d.Xb[(size_t)j * ov + l] = p[j];
+      d.Xb[(size_t)(kk + j) * ov + l] = a[j] - om[j] * p[j];
+    }
+  }
+}
+
+template <bool RPA>
+__global__ void __launch_bounds__(256) britz_kernel(const BMol* __restrict__ mols, const int* __restrict__ st,
+                                                    BCfg cfg) {
+  __shared__ double cq[kBatchMaxSub * 2 * kBatchMaxRoots];
+  __shared__ double om[kBatchMaxRoots];
+  RAGGED_PROLOGUE([&](int m) { return active(st, m) ? cdiv(mols[m].ov, kCombChunk) : 0; }) {
+    const int m = find_mol(pref, cfg.nmol, u);
+    const BMol& d = mols[m];
+    const int S = sf(st, m, F_S), kk = d.kk, k = min(kk, S);
+    const int KK = kk <= 1 ? 1 : kk <= 2 ? 2 : kk <= 4 ? 4 : kk <= 8 ? 8 : 16;
+    const int w = RPA ? 2 * KK : KK;
+    __syncthreads();   // the previous unit's reads of cq are done
+    for (int idx = threadIdx.x; idx < S * w; idx += blockDim.x) {
+      const int s = idx / w, c = idx - s * w;
+      const int j = RPA ? (c < KK ? c : c - KK) : c;
+      const int col = (RPA && c >= KK) ? kk + j : j;   // cu in Q[:, j], cw in Q[:, kk + j]
+      cq[idx] = j < k ? d.Q[(size_t)s * 2 * kk + col] : 0.0;
+    }
+    for (int j = threadIdx.x; j < KK; j += blockDim.x) om[j] = j < k ? d.omega[j] : 0.0;
+    __syncthreads();
+    const long long l = (long long)(u - pref[m]) * kCombChunk + threadIdx.x;
+    if (l >= d.ov) continue;
+    switch (KK) {
+      case 1: ritz_column<1, RPA>(d, S, cq, om, l); break;
+      case 2: ritz_column<2, RPA>(d, S, cq, om, l); break;
+      case 4: ritz_column<4, RPA>(d, S, cq, om, l); break;
+      case 8: ritz_column<8, RPA>(d, S, cq, om, l); break;
+      default: ritz_column<16, RPA>(d, S, cq, om, l); break;
+    }
+  }
+}
+
+// second Gram-Schmidt pass only where the first removed more than half of a
+// direction's norm^2 (unit rows in, norms below 0.7 out): "twice is enough"
+__global__ void bgs_check_kernel(const BMol* __restrict__ mols, int* __restrict__ st, BCfg cfg) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= cfg.nmol || !active(st, m)) return;
+  const BMol& d = mols[m];
+  const int nd = sf(st, m, F_NDIR);
+  int need = 0;
+  for (int j = 0; j < nd; ++j) need |= !(d.tn[j] >= 0.7);
+  st[m * kSt + F_GS2] = need;
 }
 
 // Row 2-norms, one CTA per row (fixed reduction order): residual rows (CIS:
@@ -1260,10 +1366,9 @@ int enqueue_iteration(cudaStream_t s, const BMol* mols, int* st, const BCfg& cfg
   bgram_reduce_kernel<GR_PROJ><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   beig_kernel<<<cfg.nmol, 1024, sizeof(double) * syevk_work_doubles(kBatchMaxSub), s>>>(mols, st, cfg); L();
   if (!cfg.rpa) {
-    bcombine_kernel<CB_RITZ_CIS><<<kGridCTAs, 256, kCombSmem, s>>>(mols, st, cfg); L();
+    britz_kernel<false><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   } else {
-    bcombine_kernel<CB_RITZ_RPA_R><<<kGridCTAs, 256, kCombSmem, s>>>(mols, st, cfg); L();
-    bcombine_kernel<CB_RITZ_RPA_X><<<kGridCTAs, 256, kCombSmem, s>>>(mols, st, cfg); L();
+    britz_kernel<true><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   }
   bnorm_kernel<RN_RES><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   bdecide_kernel<<<cfg.nmol, 256, 0, s>>>(mols, st, cfg); L();
@@ -1275,9 +1380,15 @@ int enqueue_iteration(cudaStream_t s, const BMol* mols, int* st, const BCfg& cfg
   bnorm_kernel<RN_T><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   bprecond_kernel<true><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   for (int pass = 0; pass < 2; ++pass) {
-    bgram_kernel<GR_GS><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
-    bgram_reduce_kernel<GR_GS><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
-    bcombine_kernel<CB_GS><<<kGridCTAs, 256, kCombSmem, s>>>(mols, st, cfg); L();
+    BCfg cp = cfg;
+    cp.pass = pass;
+    bgram_kernel<GR_GS><<<kGridCTAs, 256, 0, s>>>(mols, st, cp); L();
+    bgram_reduce_kernel<GR_GS><<<kGridCTAs, 256, 0, s>>>(mols, st, cp); L();
+    bcombine_kernel<CB_GS><<<kGridCTAs, 256, kCombSmem, s>>>(mols, st, cp); L();
+    if (pass == 0) {
+      bnorm_kernel<RN_T><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
+      bgs_check_kernel<<<cdiv(cfg.nmol, 256), 256, 0, s>>>(mols, st, cfg); L();
+    }
   }
   bgram_kernel<GR_LOW><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   bgram_reduce_kernel<GR_LOW><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
