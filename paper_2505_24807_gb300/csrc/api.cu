@@ -190,6 +190,7 @@ int xs_ground_state(xs_ctx* ctx, int n_mol, const int* natoms, const int* Z, con
       upload(s, m.atom_elem, m.L.elem);
       upload(s, m.xyz, m.L.xyz);
       xs::build_gtiles(s, m);
+      xs::build_gpairs(s, m);
       int it = xs::run_scf(c, m, scf_tol, max_iter);
       maxit = it > maxit ? it : maxit;
       m.ready = true;

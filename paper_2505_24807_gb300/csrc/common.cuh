@@ -83,6 +83,8 @@ struct DevMol {
   DevBuf<double> dip;            // MO dipole integrals <i|r_x|a>, 3 x nocc x nvir (lazily)
   DevBuf<int> gb_rows, gb_cols;  // atom-aligned G tiles (first AO, count, first atom, end atom)
   int gb_nrows = 0, gb_ncols = 0;
+  DevBuf<int> gp_sa, gp_pairs;   // super-atoms (int4) and unordered super-atom pairs (int2) of the float32 G build
+  int gp_nsa = 0, gp_npairs = 0;
   bool ready = false;
   int scf_iterations = 0;
   // last excited-state solution

@@ -308,19 +308,30 @@ void gbuild(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, in
   if (has_coulomb(mode)) {
     dim3 block(8, 32);
     dim3 grid((m.L.natoms + 31) / 32);
-    pack_diag_kernel<T, true><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(), m.atom_nao.get(),
-                                                     m.atom_prod_off.get(), R, rT);
-    XS_CHECK_LAUNCH();
-    // two-centre Coulomb J2 = W r: W streamed once, split over its columns so
-    // that the skinny product fills the GPU
-    static thread_local DevBuf<T> split_ws;
-    gram<T>(s, np, nvec, np, W, np, rT, np, J2, nvec, T(1), T(0), split_ws);
+    if constexpr (sizeof(T) == 4) {
+      pack_diag_kernel<T, false><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(),
+                                                        m.atom_nao.get(), m.atom_prod_off.get(), R, rT);
+      XS_CHECK_LAUNCH();
+      static thread_local DevBuf<float> j2_ws;
+      coulomb_j2(s, np, nvec, W, rT, J2, j2_ws);
+    } else {
+      pack_diag_kernel<T, true><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(),
+                                                       m.atom_nao.get(), m.atom_prod_off.get(), R, rT);
+      XS_CHECK_LAUNCH();
+      // two-centre Coulomb J2 = W r: W streamed once, split over its columns so
+      // that the skinny product fills the GPU
+      static thread_local DevBuf<T> split_ws;
+      gram<T>(s, np, nvec, np, W, np, rT, np, J2, nvec, T(1), T(0), split_ws);
+    }
   }
   // algorithmic traffic: read R, write G (and G-), read the pair integrals once
   const double outs = has_minus(mode) ? 2.0 : 1.0;
   ProfScope ps(s, sizeof(T) == 8 ? "gbuild_assemble_f64" : "gbuild_assemble_f32",
                sizeof(T) * ((double)nvec * n * n * (1.0 + outs) + (double)np * np), 0.0);
-  launch_tiles<T, false>(s, m, d_par, mode, nvec, W, J2, R, GOut<T>{G, Gm, nullptr, nullptr, nullptr, nullptr, 0});
+  if constexpr (sizeof(T) == 4)
+    gpair_build(s, m, d_par, mode, nvec, W, J2, nvec, R, G, Gm);
+  else
+    launch_tiles<T, false>(s, m, d_par, mode, nvec, W, J2, R, GOut<T>{G, Gm, nullptr, nullptr, nullptr, nullptr, 0});
 }
 
 void gbuild_split(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const float* R,
@@ -335,11 +346,11 @@ void gbuild_split(cudaStream_t s, const DevMol& m, const double* d_par, GMode mo
   if (has_coulomb(mode)) {
     dim3 block(8, 32);
     dim3 grid((m.L.natoms + 31) / 32);
-    pack_diag_kernel<float, true><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(),
-                                                         m.atom_nao.get(), m.atom_prod_off.get(), R, rT);
+    pack_diag_kernel<float, false><<<grid, block, 0, s>>>(m.L.natoms, n, np, nvec, m.atom_ao_off.get(),
+                                                          m.atom_nao.get(), m.atom_prod_off.get(), R, rT);
     XS_CHECK_LAUNCH();
-    static thread_local DevBuf<float> split_ws;
-    gram<float>(s, np, nvec, np, W, np, rT, np, J2, nvec, 1.0f, 0.0f, split_ws);
+    static thread_local DevBuf<float> j2_ws;
+    coulomb_j2(s, np, nvec, W, rT, J2, j2_ws);
   }
   if (ldo > n) {
     const long long cnt = (long long)nvec * n * (ldo - n);
@@ -350,7 +361,7 @@ void gbuild_split(cudaStream_t s, const DevMol& m, const double* d_par, GMode mo
   // algorithmic traffic: read R, write the G (and G-) TF32 pairs, read the pair integrals once
   const double outs = has_minus(mode) ? 2.0 : 1.0;
   ProfScope ps(s, "gbuild_assemble_f32", 4.0 * ((double)nvec * n * n * (1.0 + 2.0 * outs) + (double)np * np), 0.0);
-  launch_tiles<float, true>(s, m, d_par, mode, nvec, W, J2, R, GOut<float>{nullptr, nullptr, Gh, Gl, Gmh, Gml, ldo});
+  gpair_build_split(s, m, d_par, mode, nvec, W, J2, nvec, R, Gh, Gl, Gmh, Gml, ldo);
 }
 
 template <typename T>

@@ -52,6 +52,21 @@ void gbuild_split(cudaStream_t s, const DevMol& m, const double* d_par, GMode mo
 // Atom-aligned tiling of G used by gbuild (rows: one heavy atom or up to 4
 // hydrogens; columns: whole atoms, at most 64 AOs); built once per molecule.
 void build_gtiles(cudaStream_t s, DevMol& m);
+// Super-atoms (a heavy atom, or up to 4 consecutive hydrogens) and their
+// unordered pairs in warp blocks (gpair.cu); built once per molecule.
+void build_gpairs(cudaStream_t s, DevMol& m);
+// Float32 G build over super-atom pairs (gpair.cu): every R element read and
+// every G element written once per matrix.  J2 (np x nvec, row stride ldj) is
+// the two-centre Coulomb of the diagonal blocks.  Plain outputs with row
+// stride n, or TF32 pairs with row stride ldo (split).
+// J2 = W r for symmetric float32 W (np x np), r and J2 np x nvec (row stride
+// nvec); ws: partial sums (grown as needed)
+void coulomb_j2(cudaStream_t s, int np, int nvec, const float* W, const float* r, float* J2, DevBuf<float>& ws);
+void gpair_build(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const float* W,
+                 const float* J2, int ldj, const float* R, float* G, float* Gm);
+void gpair_build_split(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const float* W,
+                       const float* J2, int ldj, const float* R, float* Gh, float* Gl, float* Gmh, float* Gml,
+                       int ldo);
 // The same with caller-provided scratch: r and J2 of np * nvec elements each.
 template <typename T>
 void gbuild_raw(cudaStream_t s, const DevMol& m, const double* d_par, GMode mode, int nvec, const T* R, T* G,
