@@ -38,6 +38,7 @@
 
 #include "batch.h"
 #include "gbuild_dev.cuh"
+#include "gpair_dev.cuh"
 #include "jacobi.cuh"
 #include "kernels.h"
 #include "mlp.h"
@@ -78,6 +79,9 @@ struct BMol {
   int ntr, ntc;                       // G tiles: row groups, column tiles
   const int4* gb_rows;
   const int4* gb_cols;
+  const int2* gp_pairs;               // super-atom pairs of the float32 G build
+  const int4* gp_sa;
+  int gp_npairs;
   const int *ao_atom, *ao_local, *atom_ao_off, *atom_nao, *atom_prod_off, *atom_elem;
   const double* eps;
   const double* dip;                  // MO dipole integrals 3 x ov
@@ -499,6 +503,27 @@ __global__ void __launch_bounds__(256) bgtile_kernel(const BMol* __restrict__ mo
       Gp[j * nn + at_r] = g;
       if (kRpa) Gq[j * nn + at_r] = gm;
     }
+  }
+}
+
+// float32 G build of the batch over each molecule's super-atom pairs (the
+// single-molecule pair build, gpair.cu): a work unit is 256 pairs of one
+// molecule, every pair through all of the molecule's new matrices
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) bgpair_kernel(const BMol* __restrict__ mols, const int* __restrict__ st,
+                                                        BCfg cfg, const double* __restrict__ par) {
+  extern __shared__ float wsm[];   // 100 integrals per thread
+  RAGGED_PROLOGUE([&](int m) {
+    return (active(st, m) && sf(st, m, F_NNEW) > 0) ? cdiv(mols[m].gp_npairs, 256) : 0;
+  }) {
+    const int m = find_mol(pref, cfg.nmol, u);
+    const BMol& d = mols[m];
+    const int t = (u - pref[m]) * 256 + threadIdx.x;
+    if (t >= d.gp_npairs) continue;
+    PairOut o{static_cast<float*>(d.Gp), static_cast<float*>(d.Gq), nullptr, nullptr, nullptr, nullptr, 0};
+    gpair_one<static_cast<GMode>(MODE), false>(d.n, d.np, sf(st, m, F_NNEW), d.gp_pairs[t], d.gp_sa, par,
+                                                static_cast<const float*>(d.W), static_cast<const float*>(d.J2),
+                                                d.pmax, static_cast<const float*>(d.Rm), o, wsm + threadIdx.x * 100);
   }
 }
 
@@ -1358,7 +1383,11 @@ int enqueue_iteration(cudaStream_t s, const BMol* mols, int* st, const BCfg& cfg
     bpack_kernel<T><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
     bgemm_kernel<T, R_J2><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   }
-  bgtile_kernel<T, MODE><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg, par); L();
+  if (sizeof(T) == 4) {
+    bgpair_kernel<MODE><<<kGridCTAs, 256, sizeof(float) * 100 * 256, s>>>(mols, st, cfg, par); L();
+  } else {
+    bgtile_kernel<T, MODE><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg, par); L();
+  }
   bgemm_kernel<T, R_B1><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   bgemm_kernel<T, R_B2><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   // projected matrices and the Rayleigh-Ritz step
@@ -1401,6 +1430,16 @@ int enqueue_iteration(cudaStream_t s, const BMol* mols, int* st, const BCfg& cfg
 
 void set_attributes() {
   constexpr int kCombSmem = 3 * kBatchMaxSub * 32 * 8;
+  static const bool pair_attr = [] {
+    for (const void* f : {reinterpret_cast<const void*>(bgpair_kernel<G_CIS>),
+                          reinterpret_cast<const void*>(bgpair_kernel<G_RPA>),
+                          reinterpret_cast<const void*>(bgpair_kernel<G_CIS_T>),
+                          reinterpret_cast<const void*>(bgpair_kernel<G_RPA_T>)})
+      XS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(sizeof(float) * 100 * 256)));
+    return true;
+  }();
+  (void)pair_attr;
   set_smem_attr<CB_RITZ_CIS>(reinterpret_cast<const void*>(bcombine_kernel<CB_RITZ_CIS>), kCombSmem);
   set_smem_attr<CB_RITZ_RPA_R>(reinterpret_cast<const void*>(bcombine_kernel<CB_RITZ_RPA_R>), kCombSmem);
   set_smem_attr<CB_RITZ_RPA_X>(reinterpret_cast<const void*>(bcombine_kernel<CB_RITZ_RPA_X>), kCombSmem);
@@ -1537,6 +1576,9 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     d.Rm = takep(pm * n * n); d.Gp = takep(pm * n * n); d.Gq = rpa ? takep(pm * n * n) : nullptr;
     d.r = takep((size_t)d.np * pm); d.J2 = takep((size_t)d.np * pm);
     d.slot = bw.islot.get() + off_slot[q];
+    d.gp_pairs = reinterpret_cast<const int2*>(m.gp_pairs.get());
+    d.gp_sa = reinterpret_cast<const int4*>(m.gp_sa.get());
+    d.gp_npairs = m.gp_npairs;
     d.gb_rows = reinterpret_cast<const int4*>(m.gb_rows.get());
     d.gb_cols = reinterpret_cast<const int4*>(m.gb_cols.get());
     d.ao_atom = m.ao_atom.get(); d.ao_local = m.ao_local.get(); d.atom_ao_off = m.atom_ao_off.get();
