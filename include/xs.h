@@ -170,6 +170,17 @@ int xs_ground_state(xs_ctx* ctx, int n_mol, const int* natoms, const int* Z, con
 /* Sizes of molecule `mol` after xs_ground_state. */
 int xs_get_sizes(const xs_ctx* ctx, int mol, int* nao, int* nocc, int* natoms);
 
+/* The model of molecule `mol` as the library built it (on the device): the
+ * two-centre product supermatrix W (nprod x nprod, nprod = 10 per heavy atom +
+ * 1 per hydrogen; rows and columns are the on-atom AO products mu <= nu in
+ * atom order, (s,s), (s,px), (s,py), (s,pz), (px,px), (px,py), (px,pz),
+ * (py,py), (py,pz), (pz,pz) on a heavy atom; W[p][q] = (mu nu|lam sig) for
+ * products on different atoms, zero inside an atom's own block) and the core
+ * Hamiltonian H (n x n): paper, Section "Ground-state wavefunction
+ * calculation".  Either pointer may be NULL; host or device memory; nprod is
+ * returned in *nprod when it is not NULL. */
+int xs_get_model(const xs_ctx* ctx, int mol, double* W, double* H, int* nprod);
+
 /* Read (get) or replace (set) the MO coefficients C (n x n, row-major, MOs in
  * columns) and orbital energies eps (n, eV) of molecule `mol`; host or
  * device pointers.  Replacing them lets a caller run the products on its own
@@ -294,8 +305,10 @@ int xs_spectrum(xs_ctx* ctx, int n, const double* omega, const double* f, double
  * instrumented kernel launch of later calls is bracketed by CUDA events on
  * the launching stream; xs_profile(ctx, 2) clears and enables counting only
  * (launches, algorithmic bytes and flops, host phases; no CUDA events, ms = 0
- * for kernels), which leaves device timings undisturbed; xs_profile(ctx, 0)
- * disables it.  xs_profile_read
+ * for kernels), which leaves device timings undisturbed; xs_profile(ctx, 3)
+ * is mode 1 plus entries "gap:<kernel>" holding the device idle time between
+ * the previous instrumented launch and each launch of <kernel> (a timeline of
+ * the launching stream); xs_profile(ctx, 0) disables it.  xs_profile_read
  * synchronises the context's stream and copies up to max_entries entries
  * (one per kernel name: launches, summed device milliseconds, summed
  * algorithmic bytes and flops) and the number of entries into *count.

@@ -177,11 +177,6 @@ int xs_ground_state(xs_ctx* ctx, int n_mol, const int* natoms, const int* Z, con
       m.v = m.n - m.o;
       m.np = m.L.nprod;
       if (m.v <= 0) throw Error(XS_EINVAL, "no virtual orbitals");
-      std::vector<double> W, H;
-      xs::two_centre_supermatrix(m.L, c.par, W);
-      xs::core_hamiltonian(m.L, c.par, W, H);
-      upload(s, m.W, W);
-      upload(s, m.H, H);
       upload(s, m.ao_atom, m.L.ao_atom);
       upload(s, m.ao_local, m.L.ao_local);
       upload(s, m.atom_ao_off, m.L.ao_off);
@@ -189,6 +184,7 @@ int xs_ground_state(xs_ctx* ctx, int n_mol, const int* natoms, const int* Z, con
       upload(s, m.atom_prod_off, m.L.prod_off);
       upload(s, m.atom_elem, m.L.elem);
       upload(s, m.xyz, m.L.xyz);
+      xs::build_model(s, m, c.d_par.get());   // two-centre supermatrix and core Hamiltonian
       xs::build_gtiles(s, m);
       xs::build_gpairs(s, m);
       int it = xs::run_scf(c, m, scf_tol, max_iter);
@@ -211,6 +207,18 @@ int xs_get_sizes(const xs_ctx* cctx, int mol, int* nao, int* nocc, int* natoms) 
     if (nao) *nao = m.n;
     if (nocc) *nocc = m.o;
     if (natoms) *natoms = m.L.natoms;
+    return XS_OK;
+  });
+}
+
+int xs_get_model(const xs_ctx* cctx, int mol, double* W, double* H, int* nprod) {
+  xs_ctx* ctx = const_cast<xs_ctx*>(cctx);
+  return guarded(ctx, [&](Ctx& c) {
+    DevMol& m = molecule(c, mol);
+    if (nprod) *nprod = m.np;
+    if (W) copy_any(c.stream, W, m.W.get(), sizeof(double) * m.np * m.np);
+    if (H) copy_any(c.stream, H, m.H.get(), sizeof(double) * m.n * m.n);
+    XS_CUDA(cudaStreamSynchronize(c.stream));
     return XS_OK;
   });
 }
@@ -600,10 +608,11 @@ int xs_mlp_train(xs_ctx* ctx, int rows, const float* features, const float* targ
 
 int xs_profile(xs_ctx* ctx, int enable) {
   return guarded(ctx, [&](Ctx& c) {
-    if (enable < 0 || enable > 2) throw Error(XS_EINVAL, "xs_profile: enable must be 0, 1 or 2");
+    if (enable < 0 || enable > 3) throw Error(XS_EINVAL, "xs_profile: enable must be 0, 1, 2 or 3");
     c.prof.reset();
     c.prof.on = enable != 0;
-    c.prof.events = enable == 1;
+    c.prof.events = enable == 1 || enable == 3;
+    c.prof.timeline = enable == 3;
     return XS_OK;
   });
 }

@@ -52,6 +52,9 @@ void gbuild_split(cudaStream_t s, const DevMol& m, const double* d_par, GMode mo
 // Atom-aligned tiling of G used by gbuild (rows: one heavy atom or up to 4
 // hydrogens; columns: whole atoms, at most 64 AOs); built once per molecule.
 void build_gtiles(cudaStream_t s, DevMol& m);
+// Two-centre product supermatrix m.W (np x np) and core Hamiltonian m.H
+// (n x n) on the device from the uploaded layout and parameters (integrals.cu).
+void build_model(cudaStream_t s, DevMol& m, const double* d_par);
 // Super-atoms (a heavy atom, or up to 4 consecutive hydrogens) and their
 // unordered pairs in warp blocks (gpair.cu); built once per molecule.
 void build_gpairs(cudaStream_t s, DevMol& m);

@@ -1,5 +1,6 @@
-// Host-side NDDO model of libxs: per-element parameters, AO layout, the
-// two-centre integral supermatrix and the core Hamiltonian.
+// Host-side NDDO model of libxs: per-element parameters and the AO layout
+// (the integrals and the core Hamiltonian are built on the device,
+// integrals.cu).
 //
 // Paper, Section "Ground-state wavefunction calculation": minimal valence
 // basis, three- and four-centre integrals dropped, two-centre integrals as
@@ -52,17 +53,6 @@ struct MolLayout {
 
 // Builds the layout; returns false for odd electron counts or unknown elements.
 bool build_layout(int natoms, const int* Z, const double* xyz, MolLayout& out);
-
-// Dense nprod x nprod supermatrix W: for atoms A != B the block at rows
-// prod_off[A].., columns prod_off[B].. holds (p|q) for products p on A and q
-// on B; diagonal atom blocks are zero (one-centre terms use the parameters).
-void two_centre_supermatrix(const MolLayout& m, const ElemParams* par, std::vector<double>& W);
-
-// Core Hamiltonian H (n x n, row-major): U on the diagonal, core attraction
-// -Z_B (mu nu|s_B s_B) on the diagonal atom blocks, resonance
-// (beta_mu + beta_lam)/2 S_mu lam on the off-diagonal blocks.
-void core_hamiltonian(const MolLayout& m, const ElemParams* par, const std::vector<double>& W,
-                      std::vector<double>& H);
 
 // Product index of AOs (a, b) on one heavy atom, AO order s, px, py, pz.
 int prod_index(int a, int b);

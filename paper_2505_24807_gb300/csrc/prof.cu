@@ -17,6 +17,28 @@ cudaEvent_t Profiler::get() {
 }
 
 void Profiler::flush() {
+  // timeline: the device idle time before each launch (end of the previous
+  // launch to its start, same stream), charged to "gap:<kernel>"
+  if (!spans.empty()) {
+    std::map<const ProfEntry*, std::string> names;
+    for (auto& kv : e) names[&kv.second] = kv.first;
+    std::map<std::string, std::pair<int, double>> gaps;
+    for (size_t i = 1; i < spans.size(); ++i) {
+      cudaEventSynchronize(spans[i].a);
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, spans[i - 1].b, spans[i].a) == cudaSuccess && ms > 0.0f) {
+        auto& g = gaps["gap:" + names[spans[i].ent]];
+        g.first += 1;
+        g.second += ms;
+      }
+    }
+    spans.clear();
+    for (auto& kv : gaps) {
+      ProfEntry& ge = e[kv.first];
+      ge.launches += kv.second.first;
+      ge.ms += kv.second.second;
+    }
+  }
   for (auto& kv : e) {
     for (auto& pr : kv.second.pending) {
       cudaEventSynchronize(pr.second);
@@ -54,6 +76,7 @@ ProfScope::ProfScope(cudaStream_t stream, const char* name, double bytes, double
   a = g_prof->get();
   b = g_prof->get();
   cudaEventRecord(a, s);
+  if (g_prof->timeline) g_prof->spans.push_back({ent, a, b});
 }
 
 ProfScope::~ProfScope() {

@@ -23,6 +23,12 @@ struct ProfEntry {
 struct Profiler {
   bool on = false;
   bool events = true;       // false: count launches, bytes and flops only
+  bool timeline = false;    // also attribute the device idle time between launches
+  struct Span {
+    const ProfEntry* ent;
+    cudaEvent_t a, b;
+  };
+  std::vector<Span> spans;  // launch order (timeline mode)
   long long launches = 0;   // every kernel launch of the library while on
   std::map<std::string, ProfEntry> e;
   std::vector<cudaEvent_t> pool;

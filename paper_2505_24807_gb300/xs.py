@@ -77,6 +77,7 @@ def load():
         "xs_ground_state": (i, [vp, i, vp, vp, vp, d, i, C.POINTER(xs_gs_info)]),
         "xs_get_sizes": (i, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
         "xs_get_orbitals": (i, [vp, i, vp, vp]),
+        "xs_get_model": (i, [vp, i, vp, vp, C.POINTER(i)]),
         "xs_set_orbitals": (i, [vp, i, vp, vp]),
         "xs_apply": (i, [vp, i, i, i, vp, vp, i]),
         "xs_excited": (i, [vp, C.POINTER(xs_ex_opts), vp, vp, vp, vp, C.POINTER(xs_solve_info)]),
@@ -161,6 +162,17 @@ def xs_get_sizes(ctx, mol=0):
     nao, nocc, nat = C.c_int(), C.c_int(), C.c_int()
     _check(ctx, load().xs_get_sizes(ctx, int(mol), C.byref(nao), C.byref(nocc), C.byref(nat)))
     return nao.value, nocc.value, nat.value
+
+
+def xs_get_model(ctx, mol=0):
+    """Two-centre product supermatrix W (nprod x nprod) and core Hamiltonian H (n x n)."""
+    n, _, _ = xs_get_sizes(ctx, mol)
+    npr = C.c_int()
+    _check(ctx, load().xs_get_model(ctx, int(mol), None, None, C.byref(npr)))
+    W = np.empty((npr.value, npr.value))
+    H = np.empty((n, n))
+    _check(ctx, load().xs_get_model(ctx, int(mol), _ptr(W), _ptr(H), None))
+    return W, H
 
 
 def xs_get_orbitals(ctx, mol=0):
