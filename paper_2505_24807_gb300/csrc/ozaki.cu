@@ -520,6 +520,7 @@ constexpr int kMaxCols = 256 / kOzDigits;   // vectors (gram) or outputs (combin
 void oz_exponents(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, int* e, OzWork& w,
                   int* err) {
   if (nvec <= 0) return;
+  ProfScope ps(s, "oz_exponents", 8.0 * nvec * L, 0.0);
   w.mx.ensure(nvec);
   XS_CUDA(cudaMemsetAsync(w.mx.get(), 0, sizeof(unsigned long long) * nvec, s));
   if (L > 0) {

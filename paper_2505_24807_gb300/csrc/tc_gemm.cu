@@ -330,6 +330,7 @@ void split_pad(cudaStream_t s, int rows, int cols, int ld_dst, const S* src, int
                long long dstride, int batch, bool transpose, float* hi, float* lo) {
   if (rows <= 0 || batch <= 0) return;
   dim3 grid(static_cast<unsigned>(((long long)rows * ld_dst + 255) / 256), 1, batch);
+  ProfScope ps(s, "split_pad", (double)batch * rows * (sizeof(S) * (double)cols + 8.0 * ld_dst), 0.0);
   split_pad_kernel<S><<<grid, 256, 0, s>>>(rows, cols, ld_dst, src, ld_src, sstride, dstride, transpose ? 1 : 0, hi,
                                            lo);
   XS_CHECK_LAUNCH();
@@ -341,6 +342,7 @@ void split_pad_t(cudaStream_t s, int rows, int cols, int ld_dst, const double* s
                  long long dstride, int batch, float* hi, float* lo) {
   if (rows <= 0 || batch <= 0) return;
   dim3 grid(static_cast<unsigned>((ld_dst + 31) / 32), static_cast<unsigned>((rows + 31) / 32), batch);
+  ProfScope ps(s, "split_pad", (double)batch * rows * (8.0 * cols + 8.0 * ld_dst), 0.0);
   split_pad_t_kernel<<<grid, dim3(32, 8), 0, s>>>(rows, cols, ld_dst, src, ld_src, sstride, dstride, hi, lo);
   XS_CHECK_LAUNCH();
 }

@@ -178,6 +178,7 @@ void precondition(cudaStream_t s, int nvec, int o, int v, const double* eps, con
     return count;
   }();
   const int bx = static_cast<int>(std::min<long long>(4LL * nsm, ((long long)o * v + 255) / 256));
+  ProfScope ps(s, "precond", 16.0 * n, 0.0);
   precond_kernel<<<bx, 256, sizeof(float) * (nao + nvec), s>>>(nao, o, v, nvec, eps, omega, R, T, shift);
   XS_CHECK_LAUNCH();
 }
@@ -188,6 +189,7 @@ void residual_norms(cudaStream_t s, int nvec, long long len, const double* A, co
   const int blocks = static_cast<int>(std::min<long long>(256, (len + 255) / 256));
   static thread_local DevBuf<double> part;
   part.ensure((size_t)nvec * blocks);
+  ProfScope ps(s, "resid_norms", 8.0 * nvec * len * (B ? 2.0 : 1.0) + (R ? 8.0 * nvec * len : 0.0), 0.0);
   resid_kernel<<<dim3(blocks, nvec), 256, 0, s>>>(len, A, B, omega, part.get(), R);
   XS_CHECK_LAUNCH();
   sum_sqrt_kernel<<<grid1(nvec, 64), 64, 0, s>>>(nvec, blocks, part.get(), out_norm);
@@ -201,6 +203,7 @@ void row_norms(cudaStream_t s, int nvec, long long len, const double* X, double*
 void scale_rows(cudaStream_t s, int nvec, long long len, double* X, const double* scale) {
   long long n = (long long)nvec * len;
   if (n == 0) return;
+  ProfScope ps(s, "scale_rows", 16.0 * n, 0.0);
   scale_rows_kernel<<<grid1(n, 256), 256, 0, s>>>(nvec, len, X, scale);
   XS_CHECK_LAUNCH();
 }
