@@ -113,8 +113,8 @@ typedef struct {
                         one Davidson iteration per replay of one captured CUDA graph whose kernels walk
                         device-side work lists over all molecules (no zero padding; converged molecules
                         retire on the device); up to 16 roots, subspaces of at most 64 vectors, products
-                        in float32 SIMT (XS_MIXED) or float64 (XS_FP64), float64 subspace; with the
-                        learned guess it runs as form 2;
+                        in float32 SIMT (XS_MIXED) or float64 (XS_FP64), float64 subspace; the learned
+                        guess is scored for all molecules in one network pass;
                         2: molecules concurrently, each on its own stream and host thread */
   int subspace;      /* float64 subspace products: XS_SUBSPACE_AUTO (0), XS_SUBSPACE_FP64 (1, the
                         float64 pipe) or XS_SUBSPACE_EMULATED (2, exact digit splitting on the tensor
@@ -288,6 +288,21 @@ int xs_subspace_gram(xs_ctx* ctx, int M, int N, long long L, const double* A, co
 /* Y (nout x L) = sum_{b<nb} coef_b^T X_b, X: nb x S x L, coef: nb x S x nout, 1 <= nb <= 3 */
 int xs_subspace_combine(xs_ctx* ctx, int nb, int S, int nout, long long L, const double* X, const double* coef,
                         double* Y, int emulated);
+
+/* Parameter derivatives of a CIS excitation energy (paper, Section "Overview
+ * of the capabilities of PySEQM": the semiempirical parameters are learned by
+ * differentiating through the model).  After a singlet CIS xs_excited,
+ * grad (XS_NELEM x XS_NPARAM float64, host or device; rows H, C, N, O, fields
+ * as listed at XS_NPARAM) receives d omega_root / d parameter in eV per unit
+ * of the parameter, including the response of the ground-state orbitals: one
+ * adjoint solve (A+B) Z = L by conjugate gradients on float64 (A+B) products,
+ * then the derivatives of the core Hamiltonian, one-centre and two-centre
+ * integrals contracted with the relaxed difference density.  cg_iterations
+ * (may be NULL) receives the adjoint solve's iteration count.  XS_ESTATE if
+ * the molecule has no singlet CIS solution, XS_EINVAL for a bad root,
+ * XS_EUNSTABLE if A+B is not positive definite, XS_ENOCONV if the adjoint
+ * solve does not converge in 500 iterations. */
+int xs_gradient(xs_ctx* ctx, int mol, int root, double* grad, int* cg_iterations);
 
 /* Absorption spectrum (paper, Section "Results and discussion": the computed
  * states' oscillator strengths broadened by Gaussians of width 0.1 eV):

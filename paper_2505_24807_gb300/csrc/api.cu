@@ -315,8 +315,7 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
     std::vector<xs::SolveStats> stats(nmol);
     std::vector<int> rcs(nmol, XS_OK);
     if (o.batched < 0 || o.batched > 2) throw Error(XS_EINVAL, "batched must be 0, 1 or 2");
-    // the lock-step form takes the plain guess; learned-guess batches run concurrently
-    const int form = (o.batched == 1 && o.guess == XS_GUESS_LEARNED && c.mlp && c.mlp->ready) ? 2 : o.batched;
+    const int form = o.batched;
     if (form == 1) {
       long long replays = 0;
       xs::davidson_batched(c, o, stats, rcs, &replays);
@@ -399,6 +398,23 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
     if (info) *info = inf;
     if (status == XS_ENOCONV) c.err = "Davidson did not converge within max_iter";
     return status;
+  });
+}
+
+int xs_gradient(xs_ctx* ctx, int mol, int root, double* grad, int* cg_iterations) {
+  return guarded(ctx, [&](Ctx& c) {
+    DevMol& m = molecule(c, mol);
+    if (m.nroots <= 0 || m.method != XS_CIS || m.spin != XS_SINGLET || !m.U.get())
+      throw Error(XS_ESTATE, "xs_gradient needs a singlet CIS solution of the molecule");
+    if (root < 0 || root >= m.nroots) throw Error(XS_EINVAL, "root out of range");
+    if (!grad) throw Error(XS_EINVAL, "null gradient array");
+    std::vector<double> g((size_t)XS_NELEM * XS_NPARAM);
+    int its = 0;
+    xs::cis_parameter_gradient(c, m, root, g.data(), &its);
+    copy_any(c.stream, grad, g.data(), sizeof(double) * g.size());
+    XS_CUDA(cudaStreamSynchronize(c.stream));
+    if (cg_iterations) *cg_iterations = its;
+    return XS_OK;
   });
 }
 

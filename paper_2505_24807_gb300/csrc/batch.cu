@@ -62,6 +62,7 @@ enum StField {
   F_KQ,         // eigenvectors kept by the eigensolver (CIS)
   F_PROD,       // trial vectors multiplied so far
   F_GS2,        // 1: a second Gram-Schmidt pass is needed
+  F_NOSHIFT,    // 1: the learned shift was dropped (a residual stalled)
   kSt = 16
 };
 enum Status { BS_ACTIVE = 0, BS_CONVERGED = 1, BS_STALLED = 2, BS_MAXITER = 3, BS_UNSTABLE = 4 };
@@ -94,6 +95,8 @@ struct BMol {
   double *wts, *omega, *nrm, *tn, *dm, *osc, *gpart, *syw;
   int* slot;                          // new direction -> root * 2 + residual kind
   double *U, *Wv;                     // the molecule's kept amplitudes (X+Y and X-Y; CIS: X and X)
+  double* shift;                      // learned diagonal shift (ov) or null
+  double* rhist;                      // largest residual of the last 8 iterations
   // product scratch (product type)
   void *Xf, *Tm, *Rm, *Gp, *Gq, *Sb, *Sq, *r, *J2;
 };
@@ -922,8 +925,10 @@ __global__ void __launch_bounds__(256) bprecond_kernel(const BMol* __restrict__ 
       const int code = d.slot[s], root = code >> 1, kind = code & 1;
       const double* r = cfg.rpa ? d.Rb + (size_t)(kind * d.kk + root) * d.ov : d.Xb + (size_t)(d.kk + root) * d.ov;
       const float w = static_cast<float>(d.omega[root]);
+      const double* sh = sf(st, m, F_NOSHIFT) ? nullptr : d.shift;
       for (long long l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
         float den = w - static_cast<float>(de_of(d, l));
+        if (sh) den -= static_cast<float>(sh[l]);
         if (fabsf(den) < 1e-4f) den = (den < 0.0f) ? -1e-4f : 1e-4f;
         t[l] = r[l] * static_cast<double>(__frcp_rn(den));
       }
@@ -1123,6 +1128,14 @@ __global__ void __launch_bounds__(256) bdecide_kernel(const BMol* __restrict__ m
         if (cfg.rpa) d.slot[nd++] = 2 * j + 1;
       }
     }
+    // learned shift dropped when the largest residual has not fallen by 10 %
+    // over the last five iterations (the plain preconditioner takes over)
+    if (d.shift && !sf(st, m, F_NOSHIFT)) {
+      double mr = 0.0;
+      for (int j = 0; j < k; ++j) mr = fmax(mr, cfg.rpa ? fmax(d.nrm[j], d.nrm[kk + j]) : d.nrm[j]);
+      d.rhist[it & 7] = mr;
+      if (it > 5 && mr > 0.9 * d.rhist[(it - 5) & 7]) st[m * kSt + F_NOSHIFT] = 1;
+    }
     int done = 0;
     if (all) done = BS_CONVERGED;
     else if (it >= cfg.max_iter) done = BS_MAXITER;
@@ -1269,6 +1282,67 @@ __global__ void __launch_bounds__(256) bguess_kernel(const BMol* __restrict__ mo
   }
 }
 
+// learned guess: the nguess scored pairs of highest predicted weight (output
+// 1; ties to the lower gap, i.e. the earlier pair), one CTA per molecule;
+// pairs, rows and out concatenated over the molecules
+__global__ void __launch_bounds__(256) bselect_kernel(const BMol* __restrict__ mols, const int* __restrict__ st,
+                                                      BCfg cfg, const long long* __restrict__ pairs,
+                                                      const int* __restrict__ row0, const int* __restrict__ nrow,
+                                                      const float* __restrict__ out, long long* __restrict__ gidx,
+                                                      int gld) {
+  const int m = blockIdx.x;
+  if (m >= cfg.nmol) return;
+  __shared__ float bv[256];
+  __shared__ int bi[256];
+  __shared__ int taken[32];
+  const int r0 = row0[m], nr = nrow[m], ng = sf(st, m, F_NNEW);
+  for (int j = 0; j < ng; ++j) {
+    float best = -INFINITY;
+    int bq = 0x7fffffff;
+    for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+      bool used = false;
+      for (int t = 0; t < j; ++t) used |= taken[t] == q;
+      if (used) continue;
+      const float v = out[(size_t)(r0 + q) * kMlpOutputs + 1];
+      if (v > best || (v == best && q < bq)) { best = v; bq = q; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = bq;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        const float v2 = bv[threadIdx.x + o];
+        const int i2 = bi[threadIdx.x + o];
+        if (v2 > bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+          bv[threadIdx.x] = v2;
+          bi[threadIdx.x] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      taken[j] = bi[0];
+      gidx[(size_t)m * gld + j] = pairs[r0 + bi[0]];
+    }
+    __syncthreads();
+  }
+}
+
+// learned shift of every scored pair (output 0), zero elsewhere (zeroed before)
+__global__ void __launch_bounds__(256) bshift_kernel(const BMol* __restrict__ mols, const int* __restrict__ st,
+                                                     BCfg cfg, const long long* __restrict__ pairs,
+                                                     const int* __restrict__ row0, const int* __restrict__ nrow,
+                                                     const float* __restrict__ out) {
+  RAGGED_PROLOGUE([&](int m) { return mols[m].shift ? cdiv(nrow[m], 256) : 0; }) {
+    const int m = find_mol(pref, cfg.nmol, u);
+    const BMol& d = mols[m];
+    const int q = (u - pref[m]) * 256 + threadIdx.x;
+    if (q >= nrow[m]) continue;
+    const int r = row0[m] + q;
+    d.shift[pairs[r]] = static_cast<double>(out[(size_t)r * kMlpOutputs]);
+  }
+}
+
 // oscillator strengths from the transition dipoles dm (kk x 3, Angstrom)
 __global__ void bosc_kernel(const BMol* __restrict__ mols, const int* __restrict__ st, BCfg cfg) {
   const int m = blockIdx.x;
@@ -1334,6 +1408,12 @@ struct BatchWork {
   DevBuf<long long> gidx;
   DevBuf<double> results;
   DevBuf<int> nact;
+  // learned guess: features, network activations, outputs, pair lists
+  FeatureWork fw;
+  DevBuf<long long> dpairs, lpairs;
+  DevBuf<float> F, out;
+  DevBuf<int> lrow;
+  std::vector<DevBuf<float>> Z, H;
   int* hnact = nullptr;    // page-locked copy of the active count
   BatchWork() = default;
   BatchWork(const BatchWork&) = delete;
@@ -1344,6 +1424,10 @@ struct BatchWork {
 };
 
 constexpr int kGridCTAs = 152 * 4;   // persistent grids: 4 CTAs per SM
+// learned guess: candidate pairs (lowest orbital-energy gaps) scored per
+// molecule, as in the one-molecule solver; network rows per forward chunk
+constexpr long long kLearnedPairs = 16384;
+constexpr int kForwardRows = 1 << 20;
 
 template <typename T>
 void ensure_product_operands(Ctx& c, DevMol& m) {
@@ -1493,6 +1577,7 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
                  std::vector<int>& rcs, long long* graph_launches) {
   cudaStream_t s = c.stream;
   const bool rpa = opt.method == XS_TDHF, triplet = opt.spin == XS_TRIPLET;
+  const bool learned = opt.guess == XS_GUESS_LEARNED && !triplet && c.mlp && c.mlp->ready;
   BCfg cfg{};
   cfg.nmol = count;
   cfg.rpa = rpa;
@@ -1534,7 +1619,7 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     nsub += up32(S * ov) * (rpa ? 3 : 2) + up32(k2 * ov) * (rpa ? 2 : 1) + up32(mn * ov) +
             up32((rpa ? 3 : 2) * k2 * ov) + up32(S * S) * 6 + up32(S * k2) * 6 + up32(S * mn) + up32(mn * mn) * 2 +
             up32(S) + up32(d.kk) * 3 + up32(k2) + up32(mn) + up32(3 * (size_t)d.kk) + up32((size_t)d.nch * 4096) +
-            up32(syevk_scratch_doubles(smax, 2 * d.kk));
+            up32(syevk_scratch_doubles(smax, 2 * d.kk)) + up32(8) + (learned ? up32(ov) : 0);
     const size_t pm = (size_t)d.pmax, n = (size_t)d.n, nv = n * d.v;
     off_prod[q] = nprod;
     nprod += (sizeof(T) == 4 ? up32(pm * ov) : 0) + up32(pm * nv) * (rpa ? 3 : 2) + up32(pm * n * n) * (rpa ? 3 : 2) +
@@ -1545,7 +1630,7 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     std::vector<double> eps(m.n);
     XS_CUDA(cudaMemcpyAsync(eps.data(), m.eps.get(), sizeof(double) * m.n, cudaMemcpyDeviceToHost, s));
     XS_CUDA(cudaStreamSynchronize(s));
-    guess[q] = lowest_gaps(eps, m.o, m.v, nguess);
+    guess[q] = lowest_gaps(eps, m.o, m.v, learned ? std::min<long long>(d.ov, kLearnedPairs) : nguess);
     gld = std::max(gld, nguess);
   }
   bw.dsub.ensure(nsub);
@@ -1568,6 +1653,8 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     d.wts = take(S); d.omega = take(d.kk); d.osc = take(d.kk); d.nrm = take(k2); d.tn = take(mn);
     d.dm = take(3 * (size_t)d.kk); d.gpart = take((size_t)d.nch * 4096);
     d.syw = take(syevk_scratch_doubles(d.Smax, 2 * d.kk));
+    d.rhist = take(8);
+    d.shift = learned ? take(ov) : nullptr;
     T* pp = (sizeof(T) == 4 ? reinterpret_cast<T*>(bw.fprod.get()) : reinterpret_cast<T*>(bw.dprod.get())) + off_prod[q];
     auto takep = [&](size_t cnt) { T* r = pp; pp += up32(cnt); return r; };
     const size_t pm = (size_t)d.pmax, n = (size_t)d.n, nv = n * d.v;
@@ -1589,6 +1676,7 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     d.W = sizeof(T) == 4 ? static_cast<const void*>(m.Wf.get()) : static_cast<const void*>(m.W.get());
     m.nroots = d.kk;
     m.method = opt.method;
+    m.spin = opt.spin;
     m.U.alloc((size_t)d.kk * ov);
     m.Wv.alloc((size_t)d.kk * ov);
     d.U = m.U.get();
@@ -1599,7 +1687,8 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
   std::vector<int> hst((size_t)count * kSt, 0);
   std::vector<long long> hg((size_t)count * gld, 0);
   for (int q = 0; q < count; ++q) {
-    const int ng = static_cast<int>(guess[q].size());
+    const int ng = static_cast<int>(std::min<long long>(
+        guess[q].size(), std::min<long long>(h[q].ov, std::max(2 * h[q].kk, h[q].kk + 2))));
     hst[q * kSt + F_S] = ng;
     hst[q * kSt + F_SOLD] = 0;
     hst[q * kSt + F_NNEW] = ng;
@@ -1615,6 +1704,46 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
   if (!bw.hnact) XS_CUDA(cudaMallocHost(&bw.hnact, sizeof(int)));
   const BMol* dm = bw.dmols.get();
   int* dst = bw.dst.get();
+  if (learned) {
+    // features of every molecule's lowest-gap pairs, one network pass over all
+    // of them (in row chunks), then per molecule the guess pairs of highest
+    // predicted weight and the predicted diagonal shift on the scored pairs
+    HostScope h_learned("host:learned_guess");
+    std::vector<int> row0(count), nrow(count);
+    int total = 0;
+    for (int q = 0; q < count; ++q) {
+      row0[q] = total;
+      nrow[q] = static_cast<int>(guess[q].size());
+      total += nrow[q];
+    }
+    bw.F.ensure((size_t)total * kMlpFeatures);
+    bw.out.ensure((size_t)total * kMlpOutputs);
+    std::vector<long long> allp((size_t)total);
+    for (int q = 0; q < count; ++q) {
+      std::copy(guess[q].begin(), guess[q].end(), allp.begin() + row0[q]);
+      pair_features(c, c.mols[first + q], guess[q], bw.F.get() + (size_t)row0[q] * kMlpFeatures, bw.dpairs, bw.fw);
+    }
+    for (int r = 0; r < total; r += kForwardRows) {
+      const int rows = std::min(kForwardRows, total - r);
+      c.mlp->forward(s, rows, bw.F.get() + (size_t)r * kMlpFeatures, bw.Z, bw.H);
+      XS_CUDA(cudaMemcpyAsync(bw.out.get() + (size_t)r * kMlpOutputs, bw.H[kMlpLayers - 1].get(),
+                              sizeof(float) * rows * kMlpOutputs, cudaMemcpyDeviceToDevice, s));
+    }
+    bw.lpairs.ensure(allp.size());
+    XS_CUDA(cudaMemcpyAsync(bw.lpairs.get(), allp.data(), sizeof(long long) * allp.size(), cudaMemcpyHostToDevice, s));
+    bw.lrow.ensure(2 * (size_t)count);
+    std::vector<int> rr(row0);
+    rr.insert(rr.end(), nrow.begin(), nrow.end());
+    XS_CUDA(cudaMemcpyAsync(bw.lrow.get(), rr.data(), sizeof(int) * rr.size(), cudaMemcpyHostToDevice, s));
+    for (int q = 0; q < count; ++q) XS_CUDA(cudaMemsetAsync(h[q].shift, 0, sizeof(double) * h[q].ov, s));
+    bselect_kernel<<<count, 256, 0, s>>>(dm, dst, cfg, bw.lpairs.get(), bw.lrow.get(), bw.lrow.get() + count,
+                                         bw.out.get(), bw.gidx.get(), gld);
+    XS_CHECK_LAUNCH();
+    bshift_kernel<<<kGridCTAs, 256, 0, s>>>(dm, dst, cfg, bw.lpairs.get(), bw.lrow.get(), bw.lrow.get() + count,
+                                            bw.out.get());
+    XS_CHECK_LAUNCH();
+    XS_CUDA(cudaStreamSynchronize(s));   // the host pair lists are released after this scope
+  }
   bguess_kernel<<<kGridCTAs, 256, 0, s>>>(dm, dst, cfg, bw.gidx.get(), gld);
   XS_CHECK_LAUNCH();
   set_attributes();
@@ -1663,6 +1792,8 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     ss.converged = sq[F_STATUS] == BS_CONVERGED;
     ss.smax = d.Smax;
     ss.tol_used = cfg.tol;
+    ss.learned = learned;
+    ss.fallback = sq[F_NOSHIFT] != 0;
     const double* r = res.data() + (size_t)q * ldo;
     m.omega.assign(r, r + d.kk);
     m.resid.assign(r + d.kk, r + 2 * d.kk);

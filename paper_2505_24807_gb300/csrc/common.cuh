@@ -88,7 +88,7 @@ struct DevMol {
   bool ready = false;
   int scf_iterations = 0;
   // last excited-state solution
-  int nroots = 0, method = 0;
+  int nroots = 0, method = 0, spin = 0;
   DevBuf<double> U, Wv;   // nroots x ov: X+Y and X-Y (CIS: X and X)
   std::vector<double> omega, osc, resid;
   int iterations = 0;

@@ -798,6 +798,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   // keep the roots: U = X+Y (CIS: X), W = X-Y (CIS: X)
   m.nroots = kk;
   m.method = opt.method;
+  m.spin = opt.spin;
   m.U.alloc((size_t)kk * ov);
   m.Wv.alloc((size_t)kk * ov);
   XS_CUDA(cudaMemcpyAsync(m.U.get(), w.X.get(), sizeof(double) * kk * ov, cudaMemcpyDeviceToDevice, s));

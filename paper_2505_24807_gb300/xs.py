@@ -87,6 +87,7 @@ def load():
         "xs_subspace_gram": (i, [vp, i, i, C.c_longlong, vp, vp, vp, i]),
         "xs_subspace_combine": (i, [vp, i, i, i, C.c_longlong, vp, vp, vp, i]),
         "xs_spectrum": (i, [vp, i, vp, vp, d, i, vp, vp]),
+        "xs_gradient": (i, [vp, i, i, vp, C.POINTER(i)]),
         "xs_mlp_nparams": (i, []),
         "xs_mlp_init": (i, [vp, C.c_ulonglong]),
         "xs_mlp_get_weights": (i, [vp, vp]),
@@ -258,6 +259,15 @@ def xs_subspace_combine(ctx, X, coef, emulated=True):
     Y = np.empty((nout, L))
     _check(ctx, load().xs_subspace_combine(ctx, nb, S, nout, L, _ptr(X), _ptr(coef), _ptr(Y), int(bool(emulated))))
     return Y
+
+
+def xs_gradient(ctx, mol=0, root=0):
+    """d omega_root / d parameter (XS_NELEM x XS_NPARAM, eV per parameter unit)
+    of the last singlet CIS solve; returns (grad, adjoint iterations)."""
+    g = np.zeros((XS_NELEM, XS_NPARAM))
+    its = C.c_int()
+    _check(ctx, load().xs_gradient(ctx, int(mol), int(root), _ptr(g), C.byref(its)))
+    return g, its.value
 
 
 def xs_spectrum(ctx, omega, f, grid, width=0.1):
