@@ -64,7 +64,9 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # dram__bytes_write.sum, mean over the captured launches of one solve of the
 # workload), from the ncu summaries named in "source"; a kernel absent here
 # (or changed since its capture) reports traffic null.
-TRAFFIC = {}
+TRAFFIC = {
+    ("tc_gemm_tf32x3", "large"): dict(bytes_per_launch=5.34e8, source="profiles/tc_gemm_tf32x3_large.md"),
+}
 
 
 def traffic_of(name, workload):

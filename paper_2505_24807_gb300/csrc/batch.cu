@@ -107,6 +107,7 @@ struct BCfg {
   int max_iter;
   double tol;
   int pass;                           // Gram-Schmidt pass of the launch (0 or 1)
+  int smax;                           // largest subspace cap of the group
 };
 
 __device__ __forceinline__ double de_of(const BMol& d, long long l) {
@@ -583,11 +584,15 @@ __global__ void __launch_bounds__(256) bgram_kernel(const BMol* __restrict__ mol
   __shared__ double As[32][65];
   __shared__ double Bs[32][65];
   const int tid = threadIdx.x;
-  RAGGED_PROLOGUE([&](int m) { return gr_live<ROLE>(st, m, cfg) ? mols[m].nch : 0; }) {
+  RAGGED_PROLOGUE([&](int m) {
+    return gr_live<ROLE>(st, m, cfg) ? mols[m].nch * cdiv(gr_rows<ROLE>(mols[m], st, m), 64) : 0;
+  }) {
     const int m = find_mol(pref, cfg.nmol, u);
     const BMol& d = mols[m];
-    const int ch = u - pref[m];
-    const int rows = gr_rows<ROLE>(d, st, m), cols = gr_cols<ROLE>(d, st, m, cfg);
+    const int rows_all = gr_rows<ROLE>(d, st, m), cols = gr_cols<ROLE>(d, st, m, cfg);
+    const int nrb = cdiv(rows_all, 64), lu = u - pref[m];
+    const int ch = lu / nrb, rb = lu - ch * nrb;
+    const int r0 = rb * 64, rows = min(64, rows_all - r0);
     const int P = rows * cols;
     int f = 1;
     while (f < 32 && P * (2 * f) <= 256) f <<= 1;
@@ -608,7 +613,7 @@ __global__ void __launch_bounds__(256) bgram_kernel(const BMol* __restrict__ mol
       for (int e = tid; e < (rows + cols) * 32; e += 256) {
         const int r = e >> 5, ll = e & 31;
         const long long l = lb + ll;
-        if (r < rows) As[ll][r] = l < l1 ? gr_a<ROLE>(d, r)[l] : 0.0;
+        if (r < rows) As[ll][r] = l < l1 ? gr_a<ROLE>(d, r0 + r)[l] : 0.0;
         else Bs[ll][r - rows] = l < l1 ? gr_b<ROLE>(d, st, m, r - rows)[l] : 0.0;
       }
       __syncthreads();
@@ -620,7 +625,7 @@ __global__ void __launch_bounds__(256) bgram_kernel(const BMol* __restrict__ mol
         acc[q] = a;
       }
     }
-    double* part = d.gpart + (size_t)ch * 4096;
+    double* part = d.gpart + ((size_t)ch * 2 + rb) * 4096;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       double a = acc[q];
@@ -644,8 +649,9 @@ __global__ void __launch_bounds__(256) bgram_reduce_kernel(const BMol* __restric
     const int e = (u - pref[m]) * 256 + threadIdx.x;
     if (e >= rows * cols) continue;
     const int i = e / cols, c = e - i * cols;
+    const int rb = i >> 6, il = i & 63;
     double s = 0.0;
-    for (int ch = 0; ch < d.nch; ++ch) s += d.gpart[(size_t)ch * 4096 + i * 64 + c];
+    for (int ch = 0; ch < d.nch; ++ch) s += d.gpart[((size_t)ch * 2 + rb) * 4096 + il * 64 + c];
     if (ROLE == GR_PROJ) {
       const int cnt = sf(st, m, F_NNEW), sold = sf(st, m, F_SOLD);
       if (c < cnt) d.a1[(size_t)i * d.Smax + sold + c] = s;
@@ -1456,7 +1462,8 @@ void set_smem_attr(const void* fn, int bytes) {
 template <typename T, int MODE>
 int enqueue_iteration(cudaStream_t s, const BMol* mols, int* st, const BCfg& cfg, const double* par, int* nact,
                       int* hnact) {
-  constexpr int kCombSmem = 3 * kBatchMaxSub * 32 * 8;
+  const int kCombSmem = 3 * cfg.smax * 32 * 8;
+  const size_t kEigSmem = sizeof(double) * syevk_work_doubles(cfg.smax);
   int launches = 0;
   auto L = [&]() { BATCH_LAUNCHED(); ++launches; };
   // products of the appended vectors
@@ -1477,7 +1484,7 @@ int enqueue_iteration(cudaStream_t s, const BMol* mols, int* st, const BCfg& cfg
   // projected matrices and the Rayleigh-Ritz step
   bgram_kernel<GR_PROJ><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   bgram_reduce_kernel<GR_PROJ><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
-  beig_kernel<<<cfg.nmol, 1024, sizeof(double) * syevk_work_doubles(kBatchMaxSub), s>>>(mols, st, cfg); L();
+  beig_kernel<<<cfg.nmol, 1024, kEigSmem, s>>>(mols, st, cfg); L();
   if (!cfg.rpa) {
     britz_kernel<false><<<kGridCTAs, 256, 0, s>>>(mols, st, cfg); L();
   } else {
@@ -1514,6 +1521,13 @@ int enqueue_iteration(cudaStream_t s, const BMol* mols, int* st, const BCfg& cfg
 
 void set_attributes() {
   constexpr int kCombSmem = 3 * kBatchMaxSub * 32 * 8;
+  static const bool eig_attr = [] {
+    XS_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(beig_kernel),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(sizeof(double) * syevk_work_doubles(kBatchMaxSub))));
+    return true;
+  }();
+  (void)eig_attr;
   static const bool pair_attr = [] {
     for (const void* f : {reinterpret_cast<const void*>(bgpair_kernel<G_CIS>),
                           reinterpret_cast<const void*>(bgpair_kernel<G_RPA>),
@@ -1610,7 +1624,7 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     smax = std::min(smax, kBatchMaxSub);
     smax = static_cast<int>(std::min<long long>(smax, d.ov));
     smax = std::max(smax, static_cast<int>(std::min<long long>(d.ov, nguess + 2 * d.kk)));
-    if (smax > kBatchMaxSub) throw Error(XS_EINVAL, "batched solve: subspace above 64 vectors");
+    if (smax > kBatchMaxSub) throw Error(XS_EINVAL, "batched solve: subspace above 128 vectors");
     d.Smax = smax;
     d.nch = cdiv(d.ov, kGramChunk);
     d.ntr = m.gb_nrows; d.ntc = m.gb_ncols;
@@ -1618,7 +1632,7 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     off_sub[q] = nsub;
     nsub += up32(S * ov) * (rpa ? 3 : 2) + up32(k2 * ov) * (rpa ? 2 : 1) + up32(mn * ov) +
             up32((rpa ? 3 : 2) * k2 * ov) + up32(S * S) * 6 + up32(S * k2) * 6 + up32(S * mn) + up32(mn * mn) * 2 +
-            up32(S) + up32(d.kk) * 3 + up32(k2) + up32(mn) + up32(3 * (size_t)d.kk) + up32((size_t)d.nch * 4096) +
+            up32(S) + up32(d.kk) * 3 + up32(k2) + up32(mn) + up32(3 * (size_t)d.kk) + up32((size_t)d.nch * 2 * 4096) +
             up32(syevk_scratch_doubles(smax, 2 * d.kk)) + up32(8) + (learned ? up32(ov) : 0);
     const size_t pm = (size_t)d.pmax, n = (size_t)d.n, nv = n * d.v;
     off_prod[q] = nprod;
@@ -1651,7 +1665,7 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     d.Q = take(S * k2); d.E = take(S * k2); d.coef = take(4 * S * k2);
     d.tS = take(S * mn); d.G2 = take(mn * mn); d.Bm = take(mn * mn);
     d.wts = take(S); d.omega = take(d.kk); d.osc = take(d.kk); d.nrm = take(k2); d.tn = take(mn);
-    d.dm = take(3 * (size_t)d.kk); d.gpart = take((size_t)d.nch * 4096);
+    d.dm = take(3 * (size_t)d.kk); d.gpart = take((size_t)d.nch * 2 * 4096);
     d.syw = take(syevk_scratch_doubles(d.Smax, 2 * d.kk));
     d.rhist = take(8);
     d.shift = learned ? take(ov) : nullptr;
@@ -1682,6 +1696,7 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     d.U = m.U.get();
     d.Wv = m.Wv.get();
   }
+  for (int q = 0; q < count; ++q) cfg.smax = std::max(cfg.smax, h[q].Smax);
   bw.dmols.ensure(count);
   XS_CUDA(cudaMemcpyAsync(bw.dmols.get(), h.data(), sizeof(BMol) * count, cudaMemcpyHostToDevice, s));
   std::vector<int> hst((size_t)count * kSt, 0);

@@ -12,7 +12,7 @@ namespace xs {
 // most kBatchMaxSub vectors and its per-molecule small matrices live in shared
 // memory).
 constexpr int kBatchMaxRoots = 16;
-constexpr int kBatchMaxSub = 64;
+constexpr int kBatchMaxSub = 128;
 // Molecules per lock-step group: the ragged kernels' work-list prologue keeps
 // one prefix entry per molecule in shared memory.
 constexpr int kBatchGroup = 1024;
