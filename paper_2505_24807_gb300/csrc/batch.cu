@@ -844,7 +844,7 @@ __global__ void __launch_bounds__(256) britz_kernel(const BMol* __restrict__ mol
     const int m = find_mol(pref, cfg.nmol, u);
     const BMol& d = mols[m];
     const int S = sf(st, m, F_S), kk = d.kk, k = min(kk, S);
-    const int KK = kk <= 1 ? 1 : kk <= 2 ? 2 : kk <= 4 ? 4 : kk <= 8 ? 8 : 16;
+    const int KK = kk;   // exact: no float64 FMA on padding
     const int w = RPA ? 2 * KK : KK;
     __syncthreads();   // the previous unit's reads of cq are done
     for (int idx = threadIdx.x; idx < S * w; idx += blockDim.x) {
@@ -858,11 +858,12 @@ __global__ void __launch_bounds__(256) britz_kernel(const BMol* __restrict__ mol
     const long long l = (long long)(u - pref[m]) * kCombChunk + threadIdx.x;
     if (l >= d.ov) continue;
     switch (KK) {
-      case 1: ritz_column<1, RPA>(d, S, cq, om, l); break;
-      case 2: ritz_column<2, RPA>(d, S, cq, om, l); break;
-      case 4: ritz_column<4, RPA>(d, S, cq, om, l); break;
-      case 8: ritz_column<8, RPA>(d, S, cq, om, l); break;
+#define RITZ_CASE(K) \
+  case K: ritz_column<K, RPA>(d, S, cq, om, l); break;
+      RITZ_CASE(1) RITZ_CASE(2) RITZ_CASE(3) RITZ_CASE(4) RITZ_CASE(5) RITZ_CASE(6) RITZ_CASE(7) RITZ_CASE(8)
+      RITZ_CASE(9) RITZ_CASE(10) RITZ_CASE(11) RITZ_CASE(12) RITZ_CASE(13) RITZ_CASE(14) RITZ_CASE(15)
       default: ritz_column<16, RPA>(d, S, cq, om, l); break;
+#undef RITZ_CASE
     }
   }
 }

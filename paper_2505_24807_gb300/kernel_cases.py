@@ -6,6 +6,7 @@ captures of the full workload would hold ~12 GB on the device):
   python -m paper_2505_24807_gb300.kernel_cases tc      # TF32 transforms: one TDHF product, large molecule
   python -m paper_2505_24807_gb300.kernel_cases gbuild  # G build: one TDHF product, medium molecule
   python -m paper_2505_24807_gb300.kernel_cases slice   # digit split of 3 x 20 vectors of 600k amplitudes
+  python -m paper_2505_24807_gb300.kernel_cases batch   # one lock-step batched CIS solve, 256 molecules of 20-200 atoms
 
 Inputs are seeded; each case prints one line with a checksum.
 """
@@ -57,11 +58,21 @@ def case_slice():
     return (float(np.abs(Y).max()),)
 
 
+def case_batch():
+    ctx = xs.xs_create(0)
+    xs.xs_set_params(ctx, molgen.params_table(molgen.make_params(0)))
+    mols = [molgen.config_batch(s) for s in range(256)]
+    xs.xs_ground_state(ctx, mols)
+    out = xs.xs_excited(ctx, method=xs.XS_CIS, nroots=6, tol=1e-5, precision=xs.XS_MIXED, batched=1, n_mol=len(mols))
+    return float(out["omega"].sum()), int(out["info"]["iterations"])
+
+
 CASES = {
     "oz": case_oz,
     "tc": lambda: _product_case(molgen.config_large, 10),
     "gbuild": lambda: _product_case(molgen.config_medium, 8),
     "slice": case_slice,
+    "batch": case_batch,
 }
 
 
