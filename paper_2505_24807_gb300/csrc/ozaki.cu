@@ -306,14 +306,25 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+// largest |x| of each row, as the bit pattern of a non-negative double (its
+// ordering is the integer ordering); four independent loads in flight per
+// thread
 __global__ void oz_absmax_kernel(long long L, const double* __restrict__ X, long long ldx,
                                  unsigned long long* __restrict__ mx) {
   const int r = blockIdx.y;
   const double* x = X + static_cast<size_t>(r) * ldx;
-  unsigned long long m = 0;
-  for (long long l = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; l < L;
-       l += static_cast<long long>(gridDim.x) * blockDim.x)
-    m = max(m, static_cast<unsigned long long>(__double_as_longlong(fabs(x[l]))));
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  unsigned long long m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+  long long l = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (; l + 3 * stride < L; l += 4 * stride) {
+    const double a = x[l], b = x[l + stride], c = x[l + 2 * stride], d = x[l + 3 * stride];
+    m0 = max(m0, static_cast<unsigned long long>(__double_as_longlong(fabs(a))));
+    m1 = max(m1, static_cast<unsigned long long>(__double_as_longlong(fabs(b))));
+    m2 = max(m2, static_cast<unsigned long long>(__double_as_longlong(fabs(c))));
+    m3 = max(m3, static_cast<unsigned long long>(__double_as_longlong(fabs(d))));
+  }
+  for (; l < L; l += stride) m0 = max(m0, static_cast<unsigned long long>(__double_as_longlong(fabs(x[l]))));
+  unsigned long long m = max(max(m0, m1), max(m2, m3));
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(&mx[r], m);
 }
@@ -524,7 +535,9 @@ void oz_exponents(cudaStream_t s, int nvec, long long L, const double* X, long l
   w.mx.ensure(nvec);
   XS_CUDA(cudaMemsetAsync(w.mx.get(), 0, sizeof(unsigned long long) * nvec, s));
   if (L > 0) {
-    dim3 grid(static_cast<unsigned>(std::min<long long>(256, (L + 255) / 256)), nvec);
+    // about 8 CTAs per SM over all rows, at least 1024 amplitudes per CTA
+    const long long per_row = std::max<long long>(1, std::min<long long>((8LL * 152 + nvec - 1) / nvec, (L + 1023) / 1024));
+    dim3 grid(static_cast<unsigned>(per_row), nvec);
     oz_absmax_kernel<<<grid, 256, 0, s>>>(L, X, ldx, w.mx.get());
     XS_CHECK_LAUNCH();
   }

@@ -41,11 +41,21 @@ __global__ void precond_kernel(int n, int o, int v, int nvec, const double* __re
     const int i = static_cast<int>(e / v), a = static_cast<int>(e - (long long)i * v);
     const float gap = epsf[o + a] - epsf[i];
     const float sh = shift ? static_cast<float>(shift[e]) : 0.0f;
-    for (int k = 0; k < nvec; ++k) {
-      float d = omf[k] - gap;
-      if (shift) d -= sh;
-      if (fabsf(d) < 1e-4f) d = (d < 0.0f) ? -1e-4f : 1e-4f;
-      Tt[(long long)k * ov + e] = R[(long long)k * ov + e] * static_cast<double>(__frcp_rn(d));
+    // the residuals of 8 vectors loaded before any store (R and Tt may be the
+    // same array: each thread reads its own elements before writing them)
+    for (int k0 = 0; k0 < nvec; k0 += 8) {
+      double rv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) rv[q] = (k0 + q < nvec) ? R[(long long)(k0 + q) * ov + e] : 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + q;
+        if (k >= nvec) break;
+        float d = omf[k] - gap;
+        if (shift) d -= sh;
+        if (fabsf(d) < 1e-4f) d = (d < 0.0f) ? -1e-4f : 1e-4f;
+        Tt[(long long)k * ov + e] = rv[q] * static_cast<double>(__frcp_rn(d));
+      }
     }
   }
 }
@@ -64,12 +74,36 @@ __global__ void resid_kernel(long long len, const double* __restrict__ A, const 
   const double* a = A + (long long)k * len;
   const double* b = B ? B + (long long)k * len : nullptr;
   double w = omega ? omega[k] : 0.0;
-  double s = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
-    double r = b ? (a[i] - w * b[i]) : a[i];
-    if (R) R[(long long)k * len + i] = r;
-    s += r * r;
+  // four independent elements per step (loads in flight, fixed order)
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double* Rk = R ? R + (long long)k * len : nullptr;
+  for (; i + 3 * stride < len; i += 4 * stride) {
+    double r0 = a[i], r1 = a[i + stride], r2 = a[i + 2 * stride], r3 = a[i + 3 * stride];
+    if (b) {
+      r0 -= w * b[i];
+      r1 -= w * b[i + stride];
+      r2 -= w * b[i + 2 * stride];
+      r3 -= w * b[i + 3 * stride];
+    }
+    if (Rk) {
+      Rk[i] = r0;
+      Rk[i + stride] = r1;
+      Rk[i + 2 * stride] = r2;
+      Rk[i + 3 * stride] = r3;
+    }
+    s0 = fma(r0, r0, s0);
+    s1 = fma(r1, r1, s1);
+    s2 = fma(r2, r2, s2);
+    s3 = fma(r3, r3, s3);
   }
+  for (; i < len; i += stride) {
+    const double r = b ? (a[i] - w * b[i]) : a[i];
+    if (Rk) Rk[i] = r;
+    s0 = fma(r, r, s0);
+  }
+  double s = (s0 + s1) + (s2 + s3);
   __shared__ double sh[32];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
