@@ -289,9 +289,9 @@ int xs_subspace_gram(xs_ctx* ctx, int M, int N, long long L, const double* A, co
 int xs_subspace_combine(xs_ctx* ctx, int nb, int S, int nout, long long L, const double* X, const double* coef,
                         double* Y, int emulated);
 
-/* Parameter derivatives of a CIS excitation energy (paper, Section "Overview
- * of the capabilities of PySEQM": the semiempirical parameters are learned by
- * differentiating through the model).  After a singlet CIS xs_excited,
+/* Parameter derivatives of a CIS or TDHF excitation energy (paper, Section
+ * "Overview of the capabilities of PySEQM": the semiempirical parameters are
+ * learned by differentiating through the model).  After a singlet xs_excited,
  * grad (XS_NELEM x XS_NPARAM float64, host or device; rows H, C, N, O, fields
  * as listed at XS_NPARAM) receives d omega_root / d parameter in eV per unit
  * of the parameter, including the response of the ground-state orbitals: one
@@ -299,7 +299,7 @@ int xs_subspace_combine(xs_ctx* ctx, int nb, int S, int nout, long long L, const
  * then the derivatives of the core Hamiltonian, one-centre and two-centre
  * integrals contracted with the relaxed difference density.  cg_iterations
  * (may be NULL) receives the adjoint solve's iteration count.  XS_ESTATE if
- * the molecule has no singlet CIS solution, XS_EINVAL for a bad root,
+ * the molecule has no singlet solution, XS_EINVAL for a bad root,
  * XS_EUNSTABLE if A+B is not positive definite, XS_ENOCONV if the adjoint
  * solve does not converge in 500 iterations. */
 int xs_gradient(xs_ctx* ctx, int mol, int root, double* grad, int* cg_iterations);

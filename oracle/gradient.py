@@ -22,7 +22,8 @@ FIELDS = ("Uss", "Upp", "beta_s", "beta_p", "gss", "gsp", "gpp", "gp2", "hsp", "
 
 
 def excitation_energies(Z, xyz, params, method="CIS", k=1, D0=None):
-    """Lowest k singlet excitation energies (eV) by brute force, and the density."""
+    """Lowest k singlet excitation energies (eV) by brute force, and the density;
+    method "CIS" (Tamm-Dancoff) or anything else for the RPA (TDHF)."""
     mol = nddo.Molecule(Z, xyz, params)
     ints = nddo.Integrals(mol)
     res = scf.scf(mol, ints, D0=D0, tol_density=1e-12, tol_commutator=1e-11)

@@ -404,13 +404,13 @@ int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, 
 int xs_gradient(xs_ctx* ctx, int mol, int root, double* grad, int* cg_iterations) {
   return guarded(ctx, [&](Ctx& c) {
     DevMol& m = molecule(c, mol);
-    if (m.nroots <= 0 || m.method != XS_CIS || m.spin != XS_SINGLET || !m.U.get())
-      throw Error(XS_ESTATE, "xs_gradient needs a singlet CIS solution of the molecule");
+    if (m.nroots <= 0 || m.spin != XS_SINGLET || !m.U.get())
+      throw Error(XS_ESTATE, "xs_gradient needs a singlet CIS or TDHF solution of the molecule");
     if (root < 0 || root >= m.nroots) throw Error(XS_EINVAL, "root out of range");
     if (!grad) throw Error(XS_EINVAL, "null gradient array");
     std::vector<double> g((size_t)XS_NELEM * XS_NPARAM);
     int its = 0;
-    xs::cis_parameter_gradient(c, m, root, g.data(), &its);
+    xs::parameter_gradient(c, m, root, g.data(), &its);
     copy_any(c.stream, grad, g.data(), sizeof(double) * g.size());
     XS_CUDA(cudaStreamSynchronize(c.stream));
     if (cg_iterations) *cg_iterations = its;

@@ -29,8 +29,8 @@ void mo_dipoles(Ctx& c, DevMol& m);
 void oscillator_strengths(Ctx& c, DevMol& m, int kk, const double* U, const double* omega_dev, double* f_dev);
 
 // d omega_root / d theta for every NDDO parameter (XS_NELEM x XS_NPARAM,
-// host array) of the last singlet CIS solve of m, with the orbital response
-// by one adjoint (A+B) solve (gradient.cu).
-void cis_parameter_gradient(Ctx& c, DevMol& m, int root, double* grad_host, int* cg_iterations);
+// host array) of the last singlet CIS or TDHF solve of m, with the orbital
+// response by one adjoint (A+B) solve (gradient.cu).
+void parameter_gradient(Ctx& c, DevMol& m, int root, double* grad_host, int* cg_iterations);
 
 }  // namespace xs

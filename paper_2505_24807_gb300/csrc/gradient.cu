@@ -1,19 +1,26 @@
-// Derivatives of CIS excitation energies with respect to the NDDO parameters
-// (paper, Section "Overview of the capabilities of PySEQM": the model
-// parameters are differentiable so that they can be learned).
+// Derivatives of CIS and TDHF excitation energies with respect to the NDDO
+// parameters (paper, Section "Overview of the capabilities of PySEQM": the
+// model parameters are differentiable so that they can be learned).
 //
 // For a normalised CIS root X (nocc x nvir) of the closed-shell ground state
 // (S = I, F = H + G(D/2), G(Q) = 2J(Q) - K(Q)):
 //   omega = Tr(F Delta) + <R, G(R)>,
 //   R = C_occ X C_vir^T,  Delta = C_vir X^T X C_vir^T - C_occ X X^T C_occ^T.
+// For a TDHF root with U = X+Y, W = X-Y, U.W = 1, omega = [U^T (A+B) U +
+// W^T (A-B) W] / 2 is stationary in U and W, and in the same form
+//   omega = Tr(F Delta) + <Q1, G(Q1)> + <Q2, G(Q2)>,
+//   Q1 = sym(C_occ U C_vir^T), Q2 = antisym(C_occ W C_vir^T),
+//   Delta = C_vir (U^T U + W^T W)/2 C_vir^T - C_occ (U U^T + W W^T)/2 C_occ^T
+// (G(Q2) = -K(Q2): the Coulomb part vanishes for the antisymmetric Q2).
 // The orbitals move with the parameters through the SCF condition
 // F_ai = 0, whose linear response is (A+B) z = -(C_occ^T dF C_vir) with the
 // singlet A+B of the TDHF problem.  With the orbital gradient of omega
-//   L_ia = 2 [X G_vv^T - G_oo^T X]_ia + 2 [C_occ^T G(Delta) C_vir]_ia,
-//   G_vv = C_vir^T G(R) C_vir, G_oo = C_occ^T G(R) C_occ,
+//   L_ia = sum over the pairs (Y, Q) = (X, R) (CIS) or (U, Q1), (W, Q2) (TDHF) of
+//          2 [Y G_vv^T - G_oo^T Y]_ia,  G_vv = C_vir^T G(Q) C_vir, G_oo = C_occ^T G(Q) C_occ,
+//        + 2 [C_occ^T G(Delta) C_vir]_ia,
 // one adjoint solve (A+B) Z = L (conjugate gradients on the library's float64
 // (A+B) products) serves every parameter:
-//   d omega / d theta = Tr(dH/dtheta P) + <P, dG/dtheta(D/2)> + <R, dG/dtheta(R)>,
+//   d omega / d theta = Tr(dH/dtheta P) + <P, dG/dtheta(D/2)> + sum_Q <Q, dG/dtheta(Q)>,
 //   P = Delta - sym(C_occ Z C_vir^T).
 // The parameter derivatives are contracted directly, with no derivative
 // matrices formed: the core Hamiltonian (U on the diagonal, the resonance
@@ -116,7 +123,8 @@ __device__ int product_terms(bool heavy, int p, double D1, double D2, Term* out)
 }
 
 // diagonal-block packs of the densities: for on-atom product p of atom A,
-// the sum over its ordered AO pairs of Q[mu][nu], for Q = P, D/2, R
+// the sum over its ordered AO pairs of Q[mu][nu], for Q = P, D/2, Q1 (the
+// antisymmetric Q2 packs to zero)
 __global__ void pack_kernel(int natoms, int n, const int* __restrict__ ao_off, const int* __restrict__ nao,
                             const int* __restrict__ prod_off, const double* __restrict__ P, const double* __restrict__ Dh,
                             const double* __restrict__ R, double* __restrict__ pk) {
@@ -141,8 +149,8 @@ __global__ void __launch_bounds__(128) pair_grad_kernel(int natoms, int n, const
                                                         const int* __restrict__ prod_off,
                                                         const int* __restrict__ elem, const double* __restrict__ par,
                                                         const double* __restrict__ P, const double* __restrict__ Dh,
-                                                        const double* __restrict__ R, const double* __restrict__ pk,
-                                                        double* __restrict__ grad) {
+                                                        const double* __restrict__ R, const double* __restrict__ Rm,
+                                                        const double* __restrict__ pk, double* __restrict__ grad) {
   __shared__ double gs[XS_NELEM * XS_NPARAM];
   for (int i = threadIdx.x; i < XS_NELEM * XS_NPARAM; i += blockDim.x) gs[i] = 0.0;
   __syncthreads();
@@ -167,7 +175,7 @@ __global__ void __launch_bounds__(128) pair_grad_kernel(int natoms, int n, const
     }
     const double Rd = sqrt(R2);
     // off-diagonal blocks (zero past a hydrogen's single AO)
-    double Pab[4][4], Pba[4][4], Dab[4][4], Dba[4][4], Rab[4][4], Rba[4][4];
+    double Pab[4][4], Pba[4][4], Dab[4][4], Dba[4][4], Rab[4][4], Rba[4][4], Sab[4][4], Sba[4][4];
     for (int i = 0; i < 4; ++i)
       for (int j = 0; j < 4; ++j) {
         const bool ok = i < nA && j < nB;
@@ -178,6 +186,8 @@ __global__ void __launch_bounds__(128) pair_grad_kernel(int natoms, int n, const
         Dba[j][i] = ok ? Dh[ba] : 0.0;
         Rab[i][j] = ok ? R[ab] : 0.0;
         Rba[j][i] = ok ? R[ba] : 0.0;
+        Sab[i][j] = (ok && Rm) ? Rm[ab] : 0.0;
+        Sba[j][i] = (ok && Rm) ? Rm[ba] : 0.0;
       }
     // two-centre integrals
     const double sqrt_pi = 1.77245385090551602730;
@@ -211,6 +221,7 @@ __global__ void __launch_bounds__(128) pair_grad_kernel(int natoms, int n, const
             const int y = cb ? b2 : b1, z = cb ? b1 : b2;
             gam -= Pab[u][y] * Dab[w][z] + Pba[y][u] * Dba[z][w];
             gam -= Rab[u][y] * Rab[w][z] + Rba[y][u] * Rba[z][w];
+            gam -= Sab[u][y] * Sab[w][z] + Sba[y][u] * Sba[z][w];
           }
         }
         if (q == 0) gam -= ZB * PpA;
@@ -334,11 +345,11 @@ __device__ double onec(int a, int b, int c, int d, const double* q) {
 }
 
 // per atom: U and the one-centre integral derivatives,
-// <P, dG1(D/2)> + <R, dG1(R)> with G1(Q)_mn = sum [2 (mn|ls) - (ml|ns)] Q_ls
+// <P, dG1(D/2)> + sum_Q <Q, dG1(Q)> with G1(Q)_mn = sum [2 (mn|ls) - (ml|ns)] Q_ls
 __global__ void atom_grad_kernel(int natoms, int n, const int* __restrict__ ao_off, const int* __restrict__ nao,
                                  const int* __restrict__ elem, const double* __restrict__ P,
                                  const double* __restrict__ Dh, const double* __restrict__ R,
-                                 double* __restrict__ grad) {
+                                 const double* __restrict__ R2, double* __restrict__ grad) {
   const int A = blockIdx.x * blockDim.x + threadIdx.x;
   if (A >= natoms) return;
   const int e = elem[A], o = ao_off[A], na = nao[A];
@@ -362,9 +373,18 @@ __global__ void atom_grad_kernel(int natoms, int n, const int* __restrict__ ao_o
             if (coul == 0.0 && exch == 0.0) continue;
             acc += at(P, mu, nu) * (2.0 * coul - exch) * at(Dh, la, sg);
             acc += at(R, mu, nu) * (2.0 * coul - exch) * at(R, la, sg);
+            if (R2) acc += at(R2, mu, nu) * (2.0 * coul - exch) * at(R2, la, sg);
           }
     atomicAdd(&grad[e * XS_NPARAM + P_GSS + k], acc);
   }
+}
+
+// Q = (R + sign R^T) / 2
+__global__ void sym_part_kernel(int n, double sign, const double* __restrict__ R, double* __restrict__ Q) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int i = static_cast<int>(idx / n), j = static_cast<int>(idx % n);
+  Q[idx] = 0.5 * (R[idx] + sign * R[(size_t)j * n + i]);
 }
 
 __global__ void sym_sub_kernel(int n, const double* __restrict__ Delta, const double* __restrict__ RZ,
@@ -420,38 +440,57 @@ double dot(cudaStream_t s, long long len, const double* a, const double* b, DevB
 
 }  // namespace
 
-void cis_parameter_gradient(Ctx& c, DevMol& m, int root, double* grad_host, int* cg_iterations) {
+void parameter_gradient(Ctx& c, DevMol& m, int root, double* grad_host, int* cg_iterations) {
   cudaStream_t s = c.stream;
+  const bool rpa = m.method == XS_TDHF;
   const int n = m.n, o = m.o, v = m.v;
   const long long ov = (long long)o * v, nn = (long long)n * n;
   const double* CT = m.CT.get();
   const double* CTocc = CT;
   const double* CTvir = CT + (size_t)o * n;
-  const double* X = m.U.get() + (size_t)root * ov;
-  DevBuf<double> R(nn), GR(nn), Dl(nn), GD(nn), Dh(nn), tmp((size_t)n * std::max(o, v)), Gvv((size_t)v * v),
-      Goo((size_t)o * o), T((size_t)std::max(o, v) * std::max(o, v)), L(ov), Z(ov), r(ov), zv(ov), p(ov),
-      Ap(ov), Am(ov), RZ(nn), P(nn), pk((size_t)3 * m.np), grad((size_t)XS_NELEM * XS_NPARAM), part;
+  // amplitudes: CIS X; TDHF U = X+Y and W = X-Y
+  const double* Y1 = m.U.get() + (size_t)root * ov;
+  const double* Y2 = rpa ? m.Wv.get() + (size_t)root * ov : nullptr;
+  DevBuf<double> R(nn), R2(rpa ? nn : 1), Q(nn), GR(nn), Dl(nn), GD(nn), Dh(nn), tmp((size_t)n * std::max(o, v)),
+      Gvv((size_t)v * v), Goo((size_t)o * o), T((size_t)std::max(o, v) * std::max(o, v)), L(ov), Z(ov), r(ov), zv(ov),
+      p(ov), Ap(ov), Am(ov), RZ(nn), P(nn), pk((size_t)3 * m.np), grad((size_t)XS_NELEM * XS_NPARAM), part;
   DevBuf<double> ws;
-  // R = C_occ X C_vir^T, G(R)
-  gemm<double>(s, true, false, n, v, o, 1.0, CTocc, n, 0, X, v, 0, 0.0, tmp.get(), v, 0, 1);
-  gemm<double>(s, false, false, n, n, v, 1.0, tmp.get(), v, 0, CTvir, n, 0, 0.0, R.get(), n, 0, 1);
-  gbuild<double>(s, m, c.d_par.get(), G_CIS, 1, R.get(), GR.get(), nullptr, ws);
-  // Delta = C_vir (X^T X) C_vir^T - C_occ (X X^T) C_occ^T, G(Delta); D/2 = C_occ C_occ^T
-  gemm<double>(s, true, false, v, v, o, 1.0, X, v, 0, X, v, 0, 0.0, T.get(), v, 0, 1);
+  auto transition = [&](const double* Y, double* out) {   // C_occ Y C_vir^T
+    gemm<double>(s, true, false, n, v, o, 1.0, CTocc, n, 0, Y, v, 0, 0.0, tmp.get(), v, 0, 1);
+    gemm<double>(s, false, false, n, n, v, 1.0, tmp.get(), v, 0, CTvir, n, 0, 0.0, out, n, 0, 1);
+  };
+  // pair densities: CIS Q1 = R; TDHF Q1 = sym(R_U), Q2 = antisym(R_W)
+  transition(Y1, rpa ? Q.get() : R.get());
+  if (rpa) {
+    sym_part_kernel<<<grid1(nn, 256), 256, 0, s>>>(n, 1.0, Q.get(), R.get());
+    transition(Y2, Q.get());
+    sym_part_kernel<<<grid1(nn, 256), 256, 0, s>>>(n, -1.0, Q.get(), R2.get());
+    XS_CHECK_LAUNCH();
+  }
+  // Delta = C_vir T C_vir^T - C_occ T' C_occ^T, T = (Y1^T Y1 + Y2^T Y2) / w, T' = (Y1 Y1^T + Y2 Y2^T) / w
+  const double wsc = rpa ? 0.5 : 1.0;
+  gemm<double>(s, true, false, v, v, o, wsc, Y1, v, 0, Y1, v, 0, 0.0, T.get(), v, 0, 1);
+  if (rpa) gemm<double>(s, true, false, v, v, o, wsc, Y2, v, 0, Y2, v, 0, 1.0, T.get(), v, 0, 1);
   gemm<double>(s, true, false, n, v, v, 1.0, CTvir, n, 0, T.get(), v, 0, 0.0, tmp.get(), v, 0, 1);
   gemm<double>(s, false, false, n, n, v, 1.0, tmp.get(), v, 0, CTvir, n, 0, 0.0, Dl.get(), n, 0, 1);
-  gemm<double>(s, false, true, o, o, v, 1.0, X, v, 0, X, v, 0, 0.0, T.get(), o, 0, 1);
+  gemm<double>(s, false, true, o, o, v, wsc, Y1, v, 0, Y1, v, 0, 0.0, T.get(), o, 0, 1);
+  if (rpa) gemm<double>(s, false, true, o, o, v, wsc, Y2, v, 0, Y2, v, 0, 1.0, T.get(), o, 0, 1);
   gemm<double>(s, true, false, n, o, o, 1.0, CTocc, n, 0, T.get(), o, 0, 0.0, tmp.get(), o, 0, 1);
   gemm<double>(s, false, false, n, n, o, -1.0, tmp.get(), o, 0, CTocc, n, 0, 1.0, Dl.get(), n, 0, 1);
   gemm<double>(s, true, false, n, n, o, 1.0, CTocc, n, 0, CTocc, n, 0, 0.0, Dh.get(), n, 0, 1);
   gbuild<double>(s, m, c.d_par.get(), G_CIS, 1, Dl.get(), GD.get(), nullptr, ws);
-  // L = 2 (X G_vv^T - G_oo^T X) + 2 C_occ^T G(Delta) C_vir
-  gemm<double>(s, false, true, n, v, n, 1.0, GR.get(), n, 0, CTvir, n, 0, 0.0, tmp.get(), v, 0, 1);      // G(R) C_vir
-  gemm<double>(s, false, false, v, v, n, 1.0, CTvir, n, 0, tmp.get(), v, 0, 0.0, Gvv.get(), v, 0, 1);      // G_vv
-  gemm<double>(s, false, true, n, o, n, 1.0, GR.get(), n, 0, CTocc, n, 0, 0.0, tmp.get(), o, 0, 1);       // G(R) C_occ
-  gemm<double>(s, false, false, o, o, n, 1.0, CTocc, n, 0, tmp.get(), o, 0, 0.0, Goo.get(), o, 0, 1);      // G_oo
-  gemm<double>(s, false, true, o, v, v, 2.0, X, v, 0, Gvv.get(), v, 0, 0.0, L.get(), v, 0, 1);
-  gemm<double>(s, true, false, o, v, o, -2.0, Goo.get(), o, 0, X, v, 0, 1.0, L.get(), v, 0, 1);
+  // L = sum_(Y, Q) 2 (Y G_vv^T - G_oo^T Y) + 2 C_occ^T G(Delta) C_vir
+  XS_CUDA(cudaMemsetAsync(L.get(), 0, sizeof(double) * ov, s));
+  for (int t = 0; t < (rpa ? 2 : 1); ++t) {
+    const double* Yt = t == 0 ? Y1 : Y2;
+    gbuild<double>(s, m, c.d_par.get(), G_CIS, 1, t == 0 ? R.get() : R2.get(), GR.get(), nullptr, ws);
+    gemm<double>(s, false, true, n, v, n, 1.0, GR.get(), n, 0, CTvir, n, 0, 0.0, tmp.get(), v, 0, 1);    // G C_vir
+    gemm<double>(s, false, false, v, v, n, 1.0, CTvir, n, 0, tmp.get(), v, 0, 0.0, Gvv.get(), v, 0, 1);    // G_vv
+    gemm<double>(s, false, true, n, o, n, 1.0, GR.get(), n, 0, CTocc, n, 0, 0.0, tmp.get(), o, 0, 1);     // G C_occ
+    gemm<double>(s, false, false, o, o, n, 1.0, CTocc, n, 0, tmp.get(), o, 0, 0.0, Goo.get(), o, 0, 1);    // G_oo
+    gemm<double>(s, false, true, o, v, v, 2.0, Yt, v, 0, Gvv.get(), v, 0, 1.0, L.get(), v, 0, 1);
+    gemm<double>(s, true, false, o, v, o, -2.0, Goo.get(), o, 0, Yt, v, 0, 1.0, L.get(), v, 0, 1);
+  }
   gemm<double>(s, false, true, n, v, n, 1.0, GD.get(), n, 0, CTvir, n, 0, 0.0, tmp.get(), v, 0, 1);       // G(Delta) C_vir
   gemm<double>(s, false, false, o, v, n, 2.0, CTocc, n, 0, tmp.get(), v, 0, 1.0, L.get(), v, 0, 1);
   // (A+B) Z = L by preconditioned conjugate gradients on the float64 products
@@ -502,11 +541,13 @@ void cis_parameter_gradient(Ctx& c, DevMol& m, int root, double* grad_host, int*
   if (npair > 0) {
     pair_grad_kernel<<<grid1(npair, 128), 128, 0, s>>>(na, n, m.xyz.get(), m.atom_ao_off.get(), m.atom_nao.get(),
                                                        m.atom_prod_off.get(), m.atom_elem.get(), c.d_par.get(), P.get(),
-                                                       Dh.get(), R.get(), pk.get(), grad.get());
+                                                       Dh.get(), R.get(), rpa ? R2.get() : nullptr, pk.get(),
+                                                       grad.get());
     XS_CHECK_LAUNCH();
   }
   atom_grad_kernel<<<(na + 127) / 128, 128, 0, s>>>(na, n, m.atom_ao_off.get(), m.atom_nao.get(), m.atom_elem.get(),
-                                                    P.get(), Dh.get(), R.get(), grad.get());
+                                                    P.get(), Dh.get(), R.get(), rpa ? R2.get() : nullptr,
+                                                    grad.get());
   XS_CHECK_LAUNCH();
   XS_CUDA(cudaMemcpyAsync(grad_host, grad.get(), sizeof(double) * XS_NELEM * XS_NPARAM, cudaMemcpyDeviceToHost, s));
   XS_CUDA(cudaStreamSynchronize(s));

@@ -263,7 +263,7 @@ def xs_subspace_combine(ctx, X, coef, emulated=True):
 
 def xs_gradient(ctx, mol=0, root=0):
     """d omega_root / d parameter (XS_NELEM x XS_NPARAM, eV per parameter unit)
-    of the last singlet CIS solve; returns (grad, adjoint iterations)."""
+    of the last singlet CIS or TDHF solve; returns (grad, adjoint iterations)."""
     g = np.zeros((XS_NELEM, XS_NPARAM))
     its = C.c_int()
     _check(ctx, load().xs_gradient(ctx, int(mol), int(root), _ptr(g), C.byref(its)))
