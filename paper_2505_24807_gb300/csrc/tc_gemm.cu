@@ -3,21 +3,30 @@
 // D = A B^T with A (M x K) and B (N x K) both K-major float32 matrices, each
 // given as a TF32 pair (hi, lo) with x ~= hi + lo (hi rounded to TF32, lo the
 // TF32 remainder).  The product is formed as hi*hi + hi*lo + lo*hi on the
-// 5th-generation tensor cores (kind::tf32) with float32 accumulation in TMEM,
-// which keeps about 21 significant bits -- the "split-precision (hi + lo)
+// 5th-generation tensor cores (kind::tf32) -- the "split-precision (hi + lo)
 // products" that carry the dense C X C^T transforms of the A*X product.
+//
+// The tensor cores add each 8-term MMA step into their float32 accumulator
+// with truncation, a bias of about half an ulp of the running sum per step
+// that grows with K.  So the accumulator is promoted every kChunkBlocks K
+// blocks (128 terms): the MMA warp accumulates each chunk of K into its own
+// TMEM slot, and the epilogue warps add the finished chunk sums into
+// round-to-nearest float32 registers.  The truncation bias then scales with
+// 128 instead of K (17x less at K = 2200).
 //
 // Persistent CTAs (one per SM) walk the 128 x BN output tiles (cta_group::1,
 // M = 128):
 //   warp 0      TMA producer: four 128-byte-swizzled boxes per K block of 32
-//   warp 1      TMEM allocation and the single-thread MMA issue into two
-//               alternating accumulators
-//   warps 2..5  epilogue: tcgen05.ld of the 128 accumulator lanes, stores
-// A 3-stage mbarrier ring couples producer and MMA across tiles;
-// tcgen05.commit frees a stage and signals the epilogue, which hands the
-// accumulator back through a second barrier pair.  Every wait is bounded by the
-// global timer; a timeout sets the error word, the CTA skips the remaining
-// work, waits (bounded) for its issued copies and MMAs, frees TMEM and exits.
+//   warp 1      TMEM allocation and the single-thread MMA issue into a ring
+//               of NSLOT chunk accumulators
+//   warps 2..   epilogue (4, or 8 for 256-wide tiles: two warps per group of
+//               32 TMEM lanes, each owning 128 columns): tcgen05.ld of each
+//               chunk sum into registers, stores once per tile
+// A mbarrier ring couples producer and MMA across tiles; tcgen05.commit frees
+// a stage, and signals the epilogue per chunk, which hands the slot back
+// through a second barrier ring.  Every wait is bounded by the global timer; a
+// timeout sets the error word, the CTA skips the remaining work, waits
+// (bounded) for its issued copies and MMAs, frees TMEM and exits.
 #include <mutex>
 #include <unordered_map>
 
@@ -39,6 +48,14 @@ constexpr int BK = 32;       // 32 tf32 = 128 bytes = one swizzle atom row
 // re-reads per flop)
 template <int BN>
 __host__ __device__ constexpr int stages_for() { return BN >= 256 ? 2 : (BN >= 128 ? 3 : 4); }
+constexpr int kChunkBlocks = 4;   // K blocks (of 32 terms) per promoted chunk
+// TMEM chunk slots (BN columns each, at most 512 columns) and epilogue warps
+template <int BN>
+__host__ __device__ constexpr int slots_for() { return BN >= 256 ? 2 : 4; }
+template <int BN>
+__host__ __device__ constexpr int epi_warps_for() { return BN >= 256 ? 8 : 4; }
+template <int BN>
+__host__ __device__ constexpr int threads_for() { return 64 + 32 * epi_warps_for<BN>(); }
 
 __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y, int z,
                                          int rank3) {
@@ -76,7 +93,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // across tiles and the MMA warp alternates two TMEM accumulators so that a
 // tile's epilogue overlaps the next tile's loads and MMAs.
 template <int BN>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(threads_for<BN>(), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int M, int N,
                    int Kpad, int a3, int b3, int ntm, int ntn, int ntiles, EpiArgs ep, int* err) {
@@ -84,18 +101,21 @@ __global__ void __launch_bounds__(192, 1)
   // 1024-byte aligned stage buffers (the 128-byte swizzle repeats every 1024 bytes)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int STAGES = stages_for<BN>();
+  constexpr int NSLOT = slots_for<BN>();
+  constexpr int EPI = epi_warps_for<BN>();
+  constexpr int CW = BN < 128 ? BN : 128;   // accumulator columns per epilogue warp
   constexpr int A_BYTES = BM * BK * 4;
   constexpr int B_BYTES = BN * BK * 4;
   constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   uint8_t* stage_base = base;
   uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;   // [2]
-  uint64_t* acce = accf + 2;         // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  uint64_t* accf = empty + STAGES;   // [NSLOT]
+  uint64_t* acce = accf + NSLOT;     // [NSLOT]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + NSLOT);
   // epilogue staging: per epilogue warp a 32 x 16 block, transposed so that
   // global stores run along rows
-  float* stage_ep = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(acce + 2) + 16);
+  float* stage_ep = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(acce + NSLOT) + 16);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nk = Kpad / BK;
@@ -111,13 +131,13 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NSLOT; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 128);
+      mbar_init(&acce[b], 32 * EPI);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
+  if (warp == 1) tmem_alloc(tmem_slot, NSLOT * BN);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -149,58 +169,85 @@ __global__ void __launch_bounds__(192, 1)
     for (long long q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
       mbar_wait(&empty[q % STAGES], static_cast<uint32_t>((q / STAGES) & 1), err, 0) || true;
   } else if (warp == 1 && lane == 0) {
-    // MMA issue
+    // MMA issue: chunk q of the CTA's sequence accumulates into slot q % NSLOT
     constexpr uint32_t idesc = idesc_f32acc(2, BM, BN);
-    long long g = 0;
-    int i = 0;
+    long long g = 0, q = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
-      const int buf = i & 1;
-      if (i >= 2 && !mbar_wait(&acce[buf], static_cast<uint32_t>(((i >> 1) + 1) & 1), err, 4)) break;
-      fence_after_sync();
-      const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
-      for (int kb = 0; kb < nk; ++kb, ++g) {
-        const int s = static_cast<int>(g % STAGES);
-        if (!mbar_wait(&full[s], static_cast<uint32_t>((g / STAGES) & 1), err, 2)) {
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int kc = 0; kc < nk && ok; kc += kChunkBlocks, ++q) {
+        const int slot = static_cast<int>(q % NSLOT);
+        const long long use = q / NSLOT;
+        if (use >= 1 && !mbar_wait(&acce[slot], static_cast<uint32_t>((use + 1) & 1), err, 4)) {
           ok = false;
           break;
         }
         fence_after_sync();
-        uint8_t* st = stage_base + s * STAGE_BYTES;
-        const uint32_t ah = smem_u32(st), al = smem_u32(st + A_BYTES);
-        const uint32_t bh = smem_u32(st + 2 * A_BYTES), bl = smem_u32(st + 2 * A_BYTES + B_BYTES);
+        const uint32_t acc = tmem + static_cast<uint32_t>(slot * BN);
+        const int kend = kc + kChunkBlocks < nk ? kc + kChunkBlocks : nk;
+        for (int kb = kc; kb < kend; ++kb, ++g) {
+          const int s = static_cast<int>(g % STAGES);
+          if (!mbar_wait(&full[s], static_cast<uint32_t>((g / STAGES) & 1), err, 2)) {
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          uint8_t* st = stage_base + s * STAGE_BYTES;
+          const uint32_t ah = smem_u32(st), al = smem_u32(st + A_BYTES);
+          const uint32_t bh = smem_u32(st + 2 * A_BYTES), bl = smem_u32(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-        for (int kk = 0; kk < BK / 8; ++kk) {
-          const uint32_t off = kk * 32;  // 8 tf32 per MMA step
-          const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
-          mma_tf32(acc, sdesc(ah + off), sdesc(bh + off), idesc, acc0);
-          mma_tf32(acc, sdesc(ah + off), sdesc(bl + off), idesc, 1u);
-          mma_tf32(acc, sdesc(al + off), sdesc(bh + off), idesc, 1u);
+          for (int kk = 0; kk < BK / 8; ++kk) {
+            const uint32_t off = kk * 32;  // 8 tf32 per MMA step
+            const uint32_t acc0 = (kb > kc || kk > 0) ? 1u : 0u;
+            mma_tf32(acc, sdesc(ah + off), sdesc(bh + off), idesc, acc0);
+            mma_tf32(acc, sdesc(ah + off), sdesc(bl + off), idesc, 1u);
+            mma_tf32(acc, sdesc(al + off), sdesc(bh + off), idesc, 1u);
+          }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
+        if (ok) mma_commit(&accf[slot]);
       }
-      if (ok) mma_commit(&accf[buf]);
     }
   } else if (warp >= 2) {
-    // epilogue: TMEM lanes 32*(warp % 4) .. +31 are this warp's rows
+    // epilogue: TMEM lanes 32*(warp % 4) .. +31 are this warp's rows, columns
+    // colh*CW .. +CW-1 its columns
     const int lane_base = 32 * (warp % 4);
-    int i = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    const int colh = (warp - 2) / 4;
+    long long q = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int m0, n0, bz;
       tile_of(t, m0, n0, bz);
-      const int buf = i & 1;
-      if (!mbar_wait(&accf[buf], static_cast<uint32_t>((i >> 1) & 1), err, 3)) break;
-      fence_after_sync();
-      const uint32_t trow = tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(lane_base) << 16);
+      float acc[CW];
+#pragma unroll
+      for (int j = 0; j < CW; ++j) acc[j] = 0.0f;
+      for (int kc = 0; kc < nk; kc += kChunkBlocks, ++q) {
+        const int slot = static_cast<int>(q % NSLOT);
+        if (!mbar_wait(&accf[slot], static_cast<uint32_t>((q / NSLOT) & 1), err, 3)) {
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        const uint32_t trow = tmem + static_cast<uint32_t>(slot * BN + colh * CW) +
+                              (static_cast<uint32_t>(lane_base) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < CW; c0 += 16) {
+          float v[16];
+          tmem_ld16(trow + c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[c0 + j] += v[j];
+        }
+        fence_before_sync();
+        mbar_arrive(&acce[slot]);
+      }
+      if (!ok) break;
       float* st = stage_ep + (warp - 2) * 32 * 17;
       const int c2 = lane & 15, rb = lane >> 4;
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tmem_ld16(trow + c0, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) st[lane * 17 + j] = v[j];
+      for (int c0 = 0; c0 < CW; c0 += 16) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) st[lane * 17 + j] = acc[c0 + j];
         __syncwarp();
-        const int col = n0 + c0 + c2;
+        const int col = n0 + colh * CW + c0 + c2;
 #pragma unroll 4
         for (int k = 0; k < 16; ++k) {
           const int r2 = rb + 2 * k;
@@ -231,15 +278,13 @@ __global__ void __launch_bounds__(192, 1)
         }
         __syncwarp();
       }
-      fence_before_sync();
-      mbar_arrive(&acce[buf]);
     }
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 1) {
     fence_after_sync();
-    tmem_dealloc(tmem, 2 * BN);
+    tmem_dealloc(tmem, NSLOT * BN);
   }
 }
 
@@ -318,7 +363,8 @@ CUtensorMap make_map(const float* ptr, int rows, int kpad, int ld, int batch, lo
 template <int BN>
 size_t smem_bytes() {
   constexpr int STAGES = stages_for<BN>();
-  return 1024 + STAGES * (2 * BM * BK * 4 + 2 * BN * BK * 4) + (2 * STAGES + 4) * 8 + 16 + 4 * 32 * 17 * 4;
+  return 1024 + STAGES * (2 * BM * BK * 4 + 2 * BN * BK * 4) + (2 * STAGES + 2 * slots_for<BN>()) * 8 + 16 +
+         epi_warps_for<BN>() * 32 * 17 * 4;
 }
 
 }  // namespace
@@ -380,7 +426,7 @@ void launch_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, in
   const int nsm = sm_count();
   const int grid = ntiles < nsm ? ntiles : nsm;   // persistent: one CTA per SM
   ProfScope ps(s, "tc_gemm_tf32x3", 0.0, 2.0 * 3.0 * M * N * (double)Kpad * batch);
-  tc_gemm_kernel<BNv><<<grid, 192, smem, s>>>(ah, al, bh, bl, M, N, Kpad, A.batched && batch > 1 ? 1 : 0,
+  tc_gemm_kernel<BNv><<<grid, threads_for<BNv>(), smem, s>>>(ah, al, bh, bl, M, N, Kpad, A.batched && batch > 1 ? 1 : 0,
                                               B.batched && batch > 1 ? 1 : 0, ntm, ntn, ntiles, ep, d_err);
   XS_CHECK_LAUNCH();
 }

@@ -31,17 +31,20 @@ def mixed_product_tol(n):
 
     The product chains four split-TF32 GEMMs, each contracting over at most n
     terms.  The tensor cores add every 8-term MMA step into a float32
-    accumulator with truncation, which biases each output by about
-    (K / 8) steps x half an ulp (2^-24) x 2/3 of the final magnitude (the
-    mean running sum of random-signed terms): (K / 12) 2^-24 relative per GEMM.
-    Each GEMM also drops lo*lo (2^-22 relative) and reads lo rounded to TF32
-    (2 x 2^-22), and stores its output in float32.  Summed over the four
-    GEMMs, with a factor 2 of headroom.  The exact float64 term de*X carries
-    no rounding, so the error is measured against the rest of the product
-    (C_occ^T G C_vir).  Measured on a GB300: 1.9e-6 at n = 62, 5.8e-6 at
-    n = 220, 1.3e-5 at n = 600, 4.7e-5 at n = 2200 (this bound: 8.2e-6,
-    1.4e-5, 3.0e-5, 9.3e-5)."""
-    per_gemm = (n / 12.0) * 2.0 ** -24 + 3.0 * 2.0 ** -22
+    accumulator with truncation, which biases a sum of K terms by about
+    (K / 8) steps x half an ulp (2^-24) x 2/3 of its final magnitude (the mean
+    running sum): (K / 12) 2^-24 relative.  The GEMM promotes its accumulator
+    every 128 terms into round-to-nearest float32 registers, so K is at most
+    128 in that bias, and the sqrt(K / 128) promoting additions add about half
+    an ulp each.  Each GEMM also drops lo*lo (2^-22 relative) and reads lo
+    rounded to TF32 (2 x 2^-22), and stores its output in float32.  Summed over
+    the four GEMMs, with a factor 2 of headroom.  The exact float64 term de*X
+    carries no rounding, so the error is measured against the rest of the
+    product (C_occ^T G C_vir).  Measured on a GB300 at n = 2200: 3.4e-6 to
+    5.3e-6 for 2 to 80 vectors (this bound: 1.2e-5; without the promotion the
+    same products were 2.4e-5 to 3.8e-5 off)."""
+    k = min(n, 128)
+    per_gemm = (k / 12.0) * 2.0 ** -24 + (n / 128.0) ** 0.5 * 2.0 ** -25 + 3.0 * 2.0 ** -22
     return 2.0 * 4.0 * per_gemm
 
 
