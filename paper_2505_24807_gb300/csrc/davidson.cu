@@ -65,7 +65,7 @@ struct Work {
   DevBuf<oz_t> Vtn, Vnn, S1nn, S2nn, Btn, Tnn;
   int ldkT = 0;
   DevBuf<int> eV, eS1, eS2, eB;
-  DevBuf<double> coef;
+  DevBuf<double> coef, rcoef;   // combination coefficients; the deferred TDHF Ritz block
   OzWork ozw;
   // learned guess: features, network activations, predicted shift
   FeatureWork fw;
@@ -329,10 +329,14 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   const int kk = static_cast<int>(std::min<long long>(opt.nroots, ov));
   const bool use_oz = opt.subspace == XS_SUBSPACE_EMULATED ||
                       (opt.subspace == XS_SUBSPACE_AUTO && opt.precision == XS_MIXED && ov >= kOzMinLength);
-  // subspace cap: 10 vectors per root (16 for TDHF on small problems, where
-  // the subspace eigenproblem is cheap and the larger space saves iterations;
-  // on large ones it grows as S^3: large TDHF, cap 100 vs 160 is ~9% faster)
-  int Smax = opt.max_subspace > 0 ? opt.max_subspace : std::max(48, (rpa && !use_oz ? 16 : 10) * kk);
+  // subspace cap: 10 vectors per root; TDHF 16 with the float64-pipe
+  // subspace, and 20 with the tensor-core subspace on problems of at least
+  // 2^19 amplitudes, where one product costs far more than the S^3 subspace
+  // eigensolve (2200 AOs, 10 roots, learned guess: cap 200 vs 100 is 38 vs 55
+  // iterations, 462 vs 484 ms; cap 240 is slower again).  Medium problems keep
+  // 10: there the eigensolve is a third of the solve.
+  const int per_root = !rpa ? 10 : (!use_oz ? 16 : (ov >= (1LL << 19) ? 20 : 10));
+  int Smax = opt.max_subspace > 0 ? opt.max_subspace : std::max(48, per_root * kk);
   Smax = static_cast<int>(std::min<long long>(Smax, ov));
   Smax = std::min(Smax, 1000);
   const int max_iter = opt.max_iter > 0 ? opt.max_iter : 200;
@@ -425,6 +429,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     if (rpa) ensure_zeroed(w.S2nn, (size_t)ov * w.ldk);
     w.eV.ensure(Smax); w.eS1.ensure(Smax); w.eS2.ensure(Smax); w.eB.ensure(w.bcap);
     w.coef.ensure((size_t)4 * Smax * 2 * kk);
+    if (rpa) w.rcoef.ensure((size_t)Smax * 2 * kk);
   }
   w.nrm.ensure(2 * kk + 2); w.nrm2.ensure(2 * kk + 2); w.omega.ensure(kk); w.Bm.ensure(4 * kk * kk + 4);
   w.flag.ensure(4);
@@ -517,6 +522,19 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   int it = 0, kq = 1;
   bool converged = false, polishing = false;
   int status = XS_OK;
+  // TDHF on the tensor-core subspace: the Ritz vectors [X+Y; X-Y] = V [u~ w~]
+  // are needed only when the solve ends, the polish starts or V is collapsed,
+  // so their combination (one pass over V's digits) waits until then; the
+  // coefficients of the last Rayleigh-Ritz step and the rows of V they refer
+  // to (unchanged until a collapse) are kept
+  bool ritz_pending = false;
+  int ritz_S = 0;
+  auto flush_ritz = [&]() {
+    if (!ritz_pending) return;
+    const OzBlock rz{w.Vnn.get(), w.ldk, w.eV.get(), w.rcoef.get(), 2 * kk};
+    oz_combine(s, 1, &rz, ritz_S, 2 * kk, ov, 1.0, 0.0, w.X.get(), ov, w.ozw, c.tc_err.get());
+    ritz_pending = false;
+  };
   for (it = 1; it <= max_iter + 1; ++it) {
     // projected matrices: new columns Sold..S-1 over all rows 0..S-1
     if (w.oz) {
@@ -600,8 +618,10 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
                                 {w.Vnn.get(), w.ldk, w.eV.get(), w.coef.get() + cb, 2 * kk},
                                 {w.S2nn.get(), w.ldk, w.eS2.get(), w.coef.get() + 2 * cb, 2 * kk}};
         oz_combine(s, 3, blk, S, 2 * kk, ov, 1.0, 0.0, R1p, ov, w.ozw, c.tc_err.get());
-        const OzBlock rz{w.Vnn.get(), w.ldk, w.eV.get(), w.coef.get() + 3 * cb, 2 * kk};
-        oz_combine(s, 1, &rz, S, 2 * kk, ov, 1.0, 0.0, w.X.get(), ov, w.ozw, c.tc_err.get());
+        XS_CUDA(cudaMemcpyAsync(w.rcoef.get(), w.coef.get() + 3 * cb, sizeof(double) * cb, cudaMemcpyDeviceToDevice,
+                                s));
+        ritz_pending = true;
+        ritz_S = S;
         row_norms(s, k, ov, R1p, w.nrm.get());
         row_norms(s, k, ov, R2p, w.nrm.get() + kk);
       } else {
@@ -645,6 +665,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       all = all && conv[j];
     }
     if (polishing) { converged = true; st.polished = true; break; }
+    if ((all && k == kk) || it >= max_iter) flush_ritz();
     if (all && k == kk) {
       if (opt.precision == XS_MIXED) {
         // Rayleigh-Ritz once more in the span of the converged Ritz vectors
@@ -682,9 +703,21 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     }
     precondition(s, k, o, v, m.eps.get(), w.omega.get(), R1p, R1p, shift);
     if (rpa) precondition(s, k, o, v, m.eps.get(), w.omega.get(), R2p, R2p, shift);
+    // new directions, roots with the largest residual first.  When the
+    // subspace has room for only part of the block but for at least a quarter
+    // of it, the part that fits is appended and the restart waits; below
+    // that, V is collapsed onto the current Ritz vectors first.
+    std::vector<int> order;
+    for (int j = 0; j < k; ++j)
+      if (!conv[j]) order.push_back(j);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hn[x] > hn[y]; });
+    const int per = rpa ? 2 : 1;
+    const int want = static_cast<int>(order.size()) * per;
+    const bool restart = want > Smax - S && Smax - S < std::max(per, want / 4);
+    const int take = (restart || want <= Smax - S) ? static_cast<int>(order.size()) : (Smax - S) / per;
     int nnew = 0;
-    for (int j = 0; j < k; ++j) {
-      if (conv[j]) continue;
+    for (int q = 0; q < take; ++q) {
+      const int j = order[q];
       XS_CUDA(cudaMemcpyAsync(w.T.get() + nnew * ov, R1p + j * ov, sizeof(double) * ov,
                               cudaMemcpyDeviceToDevice, s));
       ++nnew;
@@ -694,8 +727,10 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
         ++nnew;
       }
     }
-    if (S + nnew > Smax) {
-      // collapse onto the current Ritz vectors
+    if (restart) {
+      // collapse onto the current Ritz vectors (which the deferred Ritz
+      // combination needs in the old basis)
+      flush_ritz();
       int nc;
       if (!rpa) {
         nc = kq;
@@ -782,6 +817,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
   }
   h_loop.stop();
   HostScope h_finish("host:finish");
+  if (status == XS_OK) flush_ritz();   // V rows < ritz_S are unchanged since the last Rayleigh-Ritz step
   check_device_error(c);
   st.iterations = std::min(it, max_iter);
   {

@@ -73,7 +73,7 @@ def test_large_many_roots_under_memory_limit():
         # operands (8 digits x 2 bytes, both layouts for V)
         lp = (ov + 63) // 64 * 64
         per_vec = 8.0 * 3 * ov + 16.0 * lp + 16.0 * 3 * ov
-        cap = 180    # the default cap is 10 vectors per root (400)
+        cap = 180    # the default cap is 20 vectors per root (800)
         lim = xs.xs_excited(ctx.h, method=xs.XS_TDHF, nroots=k, tol=1e-5, precision=xs.XS_MIXED,
                             memory_limit=(cap + 0.5) * per_vec)
         assert lim["info"]["max_subspace_used"] == cap
