@@ -43,12 +43,14 @@ namespace {
 template <typename T>
 __host__ __device__ constexpr int gv_for() { return sizeof(T) == 4 ? 4 : 1; }   // float32: 4 matrices per group (shared memory)
 
-// TF32 pair of a float (hi rounded to TF32, lo = x - hi exact): the split
-// epilogue writes the tensor-core operand of the back-transform directly
+// TF32 pair of a float (hi and lo = x - hi both rounded to nearest TF32: the
+// tensor cores would otherwise truncate lo's low bits, a bias toward zero):
+// the split epilogue writes the tensor-core operand of the back-transform
+// directly
 __device__ __forceinline__ void tf32_pair(float x, float& hi, float& lo) {
   const uint32_t bits = __float_as_uint(x);
   hi = __uint_as_float((bits + 0x1000u) & 0xFFFFE000u);
-  lo = x - hi;
+  lo = __uint_as_float((__float_as_uint(x - hi) + 0x1000u) & 0xFFFFE000u);
 }
 
 // Output of the tile kernel: plain G (and G-) with row stride n, or (SPLIT)

@@ -18,10 +18,12 @@ namespace {
 __device__ __forceinline__ bool sa_heavy(int4 a) { return a.y & 16; }
 __device__ __forceinline__ int sa_nao(int4 a) { return a.y & 15; }
 
+// TF32 pair: hi and lo = x - hi both rounded to nearest TF32 (the tensor
+// cores would truncate lo's low bits, a bias toward zero)
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
   const uint32_t bits = __float_as_uint(x);
   hi = __uint_as_float((bits + 0x1000u) & 0xFFFFE000u);
-  lo = x - hi;
+  lo = __uint_as_float((__float_as_uint(x - hi) + 0x1000u) & 0xFFFFE000u);
 }
 
 struct PairOut {

@@ -12,7 +12,8 @@
 // blocks (128 terms): the MMA warp accumulates each chunk of K into its own
 // TMEM slot, and the epilogue warps add the finished chunk sums into
 // round-to-nearest float32 registers.  The truncation bias then scales with
-// 128 instead of K (17x less at K = 2200).
+// 128 instead of K (17x less at K = 2200; 32-term chunks cut it 4x further
+// but cost 8% of the GEMM's rate in the epilogue round trips).
 //
 // Persistent CTAs (one per SM) walk the 128 x BN output tiles (cta_group::1,
 // M = 128):
@@ -63,13 +64,19 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* tm, uint6
   else tma_load_2d(dst, tm, bar, x, y);
 }
 
-// TF32 split of a float: hi keeps the 10 explicit mantissa bits (rounded to
-// nearest, ties away), lo = x - hi (exact in float32).
+// Round a float32 to the nearest TF32 (10 explicit mantissa bits, ties away
+// from zero: symmetric in sign).
+__device__ __forceinline__ float tf32_rn(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// TF32 split of a float: hi = x rounded to TF32, lo = x - hi rounded to TF32.
+// The tensor cores read a float32 operand as TF32 by dropping its low 13
+// bits, so an unrounded lo would bias every hi*lo product toward zero; the
+// rounded pair leaves an unbiased remainder of about 2^-22 |x|.
 __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
-  uint32_t b = __float_as_uint(x);
-  uint32_t h = (b + 0x1000u) & 0xFFFFE000u;
-  hi = __uint_as_float(h);
-  lo = x - hi;
+  hi = tf32_rn(x);
+  lo = tf32_rn(x - hi);
 }
 
 struct EpiArgs {
@@ -303,10 +310,8 @@ __global__ void split_pad_kernel(int rows, int cols, int ld_dst, const S* __rest
     const S* s = src + b * sstride;
     const double x = transpose ? static_cast<double>(s[(long long)c * ld_src + r])
                                : static_cast<double>(s[(long long)r * ld_src + c]);
-    const float xf = static_cast<float>(x);
-    uint32_t bits = __float_as_uint(xf);
-    h = __uint_as_float((bits + 0x1000u) & 0xFFFFE000u);
-    l = static_cast<float>(x - static_cast<double>(h));
+    h = tf32_rn(static_cast<float>(x));
+    l = tf32_rn(static_cast<float>(x - static_cast<double>(h)));
   }
   hi[b * dstride + idx] = h;
   lo[b * dstride + idx] = l;
@@ -333,9 +338,8 @@ __global__ void split_pad_t_kernel(int rows, int cols, int ld_dst, const double*
     const double x = t[threadIdx.x][k];
     float h = 0.0f, l = 0.0f;
     if (c < cols) {
-      const uint32_t bits = __float_as_uint(static_cast<float>(x));
-      h = __uint_as_float((bits + 0x1000u) & 0xFFFFE000u);
-      l = static_cast<float>(x - static_cast<double>(h));
+      h = tf32_rn(static_cast<float>(x));
+      l = tf32_rn(static_cast<float>(x - static_cast<double>(h)));
     }
     const long long at = b * dstride + (long long)r * ld_dst + c;
     hi[at] = h;

@@ -37,12 +37,14 @@ def mixed_product_tol(n):
     every 128 terms into round-to-nearest float32 registers, so K is at most
     128 in that bias, and the sqrt(K / 128) promoting additions add about half
     an ulp each.  Each GEMM also drops lo*lo (2^-22 relative) and reads lo
-    rounded to TF32 (2 x 2^-22), and stores its output in float32.  Summed over
+    rounded to TF32 (2 x 2^-22; lo is rounded to nearest TF32 when split, so
+    this part is unbiased), and stores its output in float32.  Summed over
     the four GEMMs, with a factor 2 of headroom.  The exact float64 term de*X
     carries no rounding, so the error is measured against the rest of the
-    product (C_occ^T G C_vir).  Measured on a GB300 at n = 2200: 3.4e-6 to
-    5.3e-6 for 2 to 80 vectors (this bound: 1.2e-5; without the promotion the
-    same products were 2.4e-5 to 3.8e-5 off)."""
+    product (C_occ^T G C_vir).  Measured on a GB300: 2.1e-6 at n = 62,
+    4.1e-6 at n = 600, 3.6e-6 at n = 2200 (this bound: 8.4e-6, 1.1e-5,
+    1.2e-5; with one float32 accumulator over all of K and an unrounded lo the
+    same products were 1.9e-6, 1.3e-5 and 4.7e-5 off)."""
     k = min(n, 128)
     per_gemm = (k / 12.0) * 2.0 ** -24 + (n / 128.0) ** 0.5 * 2.0 ** -25 + 3.0 * 2.0 ** -22
     return 2.0 * 4.0 * per_gemm
