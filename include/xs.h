@@ -112,7 +112,7 @@ typedef struct {
                         1: lock-step batch -- every molecule of the last xs_ground_state call advances
                         one Davidson iteration per replay of one captured CUDA graph whose kernels walk
                         device-side work lists over all molecules (no zero padding; converged molecules
-                        retire on the device); up to 16 roots, subspaces of at most 64 vectors, products
+                        retire on the device); up to 16 roots, subspaces of at most 128 vectors, products
                         in float32 SIMT (XS_MIXED) or float64 (XS_FP64), float64 subspace; the learned
                         guess is scored for all molecules in one network pass;
                         2: molecules concurrently, each on its own stream and host thread */
