@@ -6,9 +6,10 @@
 // sub-partition whatever the number of active lanes, and a float64 divide
 // costs ~640 cycles, so the kernel keeps float64 work in as few warps as hold
 // data and moves what can be approximate to float32:
-//   1. Householder tridiagonalisation Q^T A Q = T in float64 (shared memory
-//      when S <= kSmemMax, else global scratch) on the lower triangle only
-//      (half the rank-2 update's float64 instructions); the reflectors go to
+//   1. Householder tridiagonalisation Q^T A Q = T in float64 on the packed
+//      lower triangle (half the rank-2 update's float64 instructions; shared
+//      memory up to S = kSmemMax = 224, else global scratch, which runs ~3x
+//      slower per step); the reflectors go to
 //      global scratch, the matrix-vector product of each step is split over
 //      row segments, reductions run only in the warps that hold data;
 //   2. the k lowest eigenvalues of T by Sturm-count multisection in float32,
@@ -55,7 +56,6 @@ void syevk(cudaStream_t s, int S, int k, const double* A, int lda, double* w, do
            DevBuf<double>& scratch, int* info) {
   if (S <= 0 || k <= 0) return;
   if (k > S) k = S;
-  const int ld = S + 1;
   if (S > 1024) throw Error(XS_EINVAL, "syevk: matrix larger than 1024");
   // working set (matrix, tridiagonal, reflector, products, eigenvalues,
   // float32 copy, cluster indices) in doubles
@@ -81,10 +81,10 @@ void cholesky(cudaStream_t s, int S, double* A, int lda, int* flag) {
   if (S <= 0) return;
   ProfScope ps(s, "cholesky_f64", 0.0, S * (double)S * S / 3.0);
   if (S <= kCholSmemMax) {
-    const size_t smem = sizeof(double) * (size_t)S * (S + 1);
+    const size_t smem = sizeof(double) * (size_t)S * (S + 1) / 2;
     static const bool attr = [] {   // once per process (thread-safe initialisation)
       XS_CUDA(cudaFuncSetAttribute(cholesky_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(sizeof(double) * kCholSmemMax * (kCholSmemMax + 1))));
+                                   static_cast<int>(sizeof(double) * kCholSmemMax * (kCholSmemMax + 1) / 2)));
       return true;
     }();
     (void)attr;

@@ -12,9 +12,12 @@ namespace xs {
 namespace {
 
 
-constexpr int kSmemMax = 160;   // largest S whose working set fits in shared memory
+constexpr int kSmemMax = 224;   // largest S whose working set fits in shared memory
 constexpr int kSeg = 8;         // row segments of the tridiagonalisation's matrix-vector product
 constexpr int kMaxRR = 4;       // clusters up to this size get a Rayleigh-Ritz rotation
+
+// packed lower triangle: element (i, j), j <= i
+__host__ __device__ __forceinline__ size_t tri(int i, int j) { return (size_t)i * (i + 1) / 2 + j; }
 
 __device__ __forceinline__ double warp_sum(double x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -198,10 +201,9 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
   extern __shared__ double sh[];
   __shared__ double red[33];
   __shared__ double scal[8];
-  const int ld = S + 1;
   double* base = SMEM ? sh : gscratch;
-  double* a = base;                          // S x ld working copy; later Z and LU scratch
-  double* d = a + (size_t)S * ld;
+  double* a = base;                          // packed lower triangle; later Z and LU scratch
+  double* d = a + tri(S, 0);
   double* e = d + S;
   double* v = e + S;                         // current reflector
   double* p = v + S;                         // B v, then w
@@ -210,11 +212,11 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
   float* df = reinterpret_cast<float*>(lam + S);
   float* e2f = df + S;
   int* cl = reinterpret_cast<int*>(e2f + S); // first index of each eigenvalue's cluster
-  double* gfree = gscratch + (SMEM ? 0 : ((size_t)S * ld + (size_t)(5 + kSeg) * S + 2 * S));
+  double* gfree = gscratch + (SMEM ? 0 : (tri(S, 0) + (size_t)(5 + kSeg) * S + 2 * S));
   double* R = gfree;                         // reflectors: row j holds v_j (S - j - 1 entries)
   // eigenvectors and inverse-iteration LU rows: in the freed matrix area of
   // shared memory when they fit, else in global scratch
-  const bool zsm = SMEM && 6 * k <= ld;
+  const bool zsm = SMEM && 12 * k <= S + 1;   // 6 S k doubles in the S (S + 1) / 2 of the matrix
   double* Zw = zsm ? a : gfree + (size_t)S * S;      // S x k, row stride k
   double* lu = Zw + (size_t)S * k;                    // 5 S per vector
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -222,7 +224,7 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
 
   for (int idx = tid; idx < S * S; idx += nt) {
     const int i = idx / S, j = idx % S;
-    a[i * ld + j] = Ain[(long long)i * lda + j];
+    if (j <= i) a[tri(i, j)] = Ain[(long long)i * lda + j];
   }
   __syncthreads();
 
@@ -231,7 +233,7 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
     const int r0 = j + 1, m = S - r0;
     double part = 0.0;
     if (tid < m) {
-      const double x = a[(r0 + tid) * ld + j];
+      const double x = a[tri(r0 + tid, j)];
       part = x * x;
     }
     // column norm; the final reduction's lane forms the step's scalars (in
@@ -249,9 +251,9 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
         if (nw > 1) y = warp_sum(y);
         if (lane == 0) {
           const double sigma = y;
-          const double x0 = a[r0 * ld + j];
+          const double x0 = a[tri(r0, j)];
           const double nx = sqrt(sigma);
-          const double scale_ref = fabs(a[j * ld + j]) + nx;
+          const double scale_ref = fabs(a[tri(j, j)]) + nx;
           const bool sk = !(nx > 1e-300) || nx <= 1e-300 * scale_ref;
           const double al = sk ? x0 : ((x0 > 0.0) ? -nx : nx);
           scal[0] = al;
@@ -267,7 +269,7 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
     if (!skip) {
       const double inv = scal[1];
       if (tid < m) {
-        const double x = a[(r0 + tid) * ld + j];
+        const double x = a[tri(r0 + tid, j)];
         const double vi = ((tid == 0) ? (x - alpha) : x) * inv;
         v[tid] = vi;
         Rj[tid] = vi;
@@ -282,7 +284,7 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
         const int l1 = min(m, (g + 1) * len);
         double acc = 0.0;
         for (int l = g * len; l < l1; ++l) {
-          const int at = (l >= i) ? (r0 + l) * ld + r0 + i : (r0 + i) * ld + r0 + l;
+          const size_t at = (l >= i) ? tri(r0 + l, r0 + i) : tri(r0 + i, r0 + l);
           acc = fma(a[at], v[l], acc);
         }
         ps[g * m + i] = acc;
@@ -299,7 +301,7 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
       // rank-2 update of the lower triangle only: B -= v w^T + w v^T
       for (int i = warp; i < m; i += nwarp) {
         const double vi = v[i], wi = p[i];
-        double* row = a + (r0 + i) * ld + r0;
+        double* row = a + tri(r0 + i, r0);
         for (int l = lane; l <= i; l += 32) row[l] = fma(-vi, p[l], fma(-wi, v[l], row[l]));
       }
     } else if (tid < m) {
@@ -307,17 +309,17 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
       Rj[tid] = 0.0;
     }
     if (tid == 0) {
-      d[j] = a[j * ld + j];
+      d[j] = a[tri(j, j)];
       e[j] = alpha;
     }
     __syncthreads();
   }
   if (tid == 0) {
     if (S >= 2) {
-      d[S - 2] = a[(S - 2) * ld + S - 2];
-      e[S - 2] = a[(S - 1) * ld + S - 2];
+      d[S - 2] = a[tri(S - 2, S - 2)];
+      e[S - 2] = a[tri(S - 1, S - 2)];
     }
-    d[S - 1] = a[(S - 1) * ld + S - 1];
+    d[S - 1] = a[tri(S - 1, S - 1)];
   }
   __syncthreads();
   for (int i = tid; i < S; i += nt) {
@@ -490,10 +492,10 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
 }
 
 // a = L L^T (lower L, in place, lda), flag[0] = 1 when a pivot is not positive
-// Right-looking Cholesky on the lower triangle, one CTA: the matrix staged in
-// shared memory (row stride S + 1) when it fits, the column scaled by one
-// reciprocal per step, the trailing update one warp per row.
-constexpr int kCholSmemMax = 120;
+// Right-looking Cholesky on the lower triangle, one CTA: the triangle staged
+// packed in shared memory when it fits, the column scaled by one reciprocal
+// per step, the trailing update one warp per row.
+constexpr int kCholSmemMax = 224;
 
 template <bool SMEM>
 __device__ void cholesky_body(int S, double* A, int lda, int* flag) {
@@ -501,39 +503,38 @@ __device__ void cholesky_body(int S, double* A, int lda, int* flag) {
   __shared__ double inv;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
-  const int ld = SMEM ? S + 1 : lda;
-  double* L = SMEM ? sh : A;
+  // element (i, l), l <= i: packed in shared memory, else in place in A
+  auto at = [&](int i, int l) -> double& { return SMEM ? sh[tri(i, l)] : A[(long long)i * lda + l]; };
   if (SMEM) {
     for (int idx = tid; idx < S * S; idx += nt) {
       const int i = idx / S, l = idx % S;
-      if (l <= i) L[i * ld + l] = A[(long long)i * lda + l];
+      if (l <= i) sh[tri(i, l)] = A[(long long)i * lda + l];
     }
     __syncthreads();
   }
   for (int j = 0; j < S; ++j) {
     if (tid == 0) {
-      double x = L[(long long)j * ld + j];
+      double x = at(j, j);
       if (!(x > 0.0)) { *flag = 1; x = 1e-300; }
       const double piv = sqrt(x);
-      L[(long long)j * ld + j] = piv;
+      at(j, j) = piv;
       inv = 1.0 / piv;
     }
     __syncthreads();
     const double r = inv;
-    for (int i = j + 1 + tid; i < S; i += nt) L[(long long)i * ld + j] *= r;
+    for (int i = j + 1 + tid; i < S; i += nt) at(i, j) *= r;
     __syncthreads();
     // trailing update of the lower triangle
     for (int i = j + 1 + warp; i < S; i += nwarp) {
-      const double lij = L[(long long)i * ld + j];
-      double* row = L + (long long)i * ld;
-      for (int l = j + 1 + lane; l <= i; l += 32) row[l] = fma(-lij, L[(long long)l * ld + j], row[l]);
+      const double lij = at(i, j);
+      for (int l = j + 1 + lane; l <= i; l += 32) at(i, l) = fma(-lij, at(l, j), at(i, l));
     }
     __syncthreads();
   }
   for (int idx = tid; idx < S * S; idx += nt) {
     const int i = idx / S, l = idx % S;
     if (l > i) A[(long long)i * lda + l] = 0.0;
-    else if (SMEM) A[(long long)i * lda + l] = L[i * ld + l];
+    else if (SMEM) A[(long long)i * lda + l] = sh[tri(i, l)];
   }
 }
 
@@ -542,7 +543,7 @@ __device__ void cholesky_body(int S, double* A, int lda, int* flag) {
 // products, eigenvalues, float32 copy, cluster indices); shared memory when
 // S <= kSmemMax
 __host__ __device__ constexpr size_t syevk_work_doubles(int n) {
-  return (size_t)n * (n + 1) + (size_t)(5 + kSeg) * n + 2 * (size_t)n;
+  return (size_t)n * (n + 1) / 2 + (size_t)(5 + kSeg) * n + 2 * (size_t)n;
 }
 // global scratch of syevk_body: the working set past kSmemMax, the
 // reflectors (S x S), then eigenvectors and inverse-iteration LU rows (6 S per

@@ -43,3 +43,29 @@ def test_parameter_gradient_matches_finite_differences(method):
     for f in ("Upp", "beta_p", "gsp", "gpp", "gp2", "hsp", "D1", "D2", "zeta_p"):
         assert g[0, FIELDS.index(f)] == 0.0
     assert checked >= 20
+
+
+@pytest.mark.parametrize("method", ["CIS", "RPA"])
+def test_gradient_after_lockstep_batch(method):
+    """The lock-step batch keeps each molecule's amplitudes, so xs_gradient
+    after a batched solve equals xs_gradient after a per-molecule solve of the
+    same molecule (both float64, converged far below the gradient's
+    sensitivity)."""
+    params = molgen.make_params(0)
+    mols = [molgen.config_small(2), molgen.config_small(1)]
+    meth = xs.XS_CIS if method == "CIS" else xs.XS_TDHF
+    ctx = context(params)
+    try:
+        xs.xs_ground_state(ctx.h, mols, scf_tol=1e-12)
+        xs.xs_excited(ctx.h, method=meth, nroots=2, tol=1e-9, precision=xs.XS_FP64, batched=1, n_mol=2)
+        g_batch, _ = xs.xs_gradient(ctx.h, 1, 0)
+    finally:
+        ctx.close()
+    ctx = context(params)
+    try:
+        xs.xs_ground_state(ctx.h, [mols[1]], scf_tol=1e-12)
+        xs.xs_excited(ctx.h, method=meth, nroots=2, tol=1e-9, precision=xs.XS_FP64)
+        g_solo, _ = xs.xs_gradient(ctx.h, 0, 0)
+    finally:
+        ctx.close()
+    assert np.abs(g_batch - g_solo).max() <= 1e-6 * max(1.0, np.abs(g_solo).max())
