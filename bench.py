@@ -65,7 +65,8 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # workload), from the ncu summaries named in "source"; a kernel absent here
 # (or changed since its capture) reports traffic null.
 TRAFFIC = {
-    ("tc_gemm_tf32x3", "large"): dict(bytes_per_launch=5.34e8, source="profiles/tc_gemm_tf32x3_large.md"),
+    ("tc_gemm_tf32x3", "large"): dict(bytes_per_launch=6.648e8, source="profiles/tc_gemm_tf32x3_large.md"),
+    ("gbuild_assemble_f32", "large"): dict(bytes_per_launch=1.2252e9, source="profiles/tc_gemm_tf32x3_large.md"),
 }
 
 
@@ -617,7 +618,7 @@ def main():
                     config=dict(workload=args.workload, desc=wl["desc"], precision=args.precision,
                                 guess="learned" if guess == xs.XS_GUESS_LEARNED else "plain",
                                 nao=nao, nocc=nocc, tol_eV=wl["tol"], tol_used_eV=last["info"]["tol_used"],
-                                l2="inputs larger than L2 (V, (A+B)V, (A-B)V: ~12 GB working set)",
+                                l2="inputs larger than L2 (V, (A+B)V, (A-B)V and their digit operands: ~21 GB working set)",
                                 setup_seconds=round(setup_s, 3), scf_iterations=gs["max_scf_iter_used"]),
                     iterations=int(last["info"]["iterations"]), products=int(last["info"]["products"]),
                     converged=int(last["info"]["converged"]),
