@@ -15,6 +15,15 @@
 #include "prof.h"
 
 namespace xs {
+
+#ifdef __CUDACC__
+// High 32 bits of |x|'s bit pattern (sign cleared: exponent and the top 20
+// mantissa bits).  Ordered like |x| and enough for its binary exponent: the
+// per-row maxima that set the digit exponents of the Davidson subspace.
+__device__ __forceinline__ unsigned int abs_hi(double x) {
+  return static_cast<unsigned int>(static_cast<unsigned long long>(__double_as_longlong(x)) >> 32) & 0x7FFFFFFFu;
+}
+#endif
 struct Mlp;
 }
 

@@ -65,6 +65,10 @@ struct Work {
   DevBuf<oz_t> Vtn, Vnn, S1nn, S2nn, Btn, Tnn;
   int ldkT = 0;
   DevBuf<int> eV, eS1, eS2, eB;
+  // per-row max |x| (abs_hi) formed by the kernels that write the rows
+  // (product epilogues, combinations, row scaling): the digit exponents need
+  // no extra pass over the float64 rows
+  DevBuf<unsigned int> mxV, mxS1, mxS2, mxT;
   DevBuf<double> coef, rcoef;   // combination coefficients; the deferred TDHF Ritz block
   OzWork ozw;
   // learned guess: features, network activations, predicted shift
@@ -92,31 +96,39 @@ struct Work {
   ~Work() { if (hpin) cudaFreeHost(hpin); }
 };
 
-// digits of V rows [first, first + count) in both layouts
-void slice_V(Ctx& c, Work& w, long long ov, int first, int count) {
+// exponents of count rows of X: from the maxima the writing kernel formed
+// (mx), else by a pass over the rows
+void exponents(Ctx& c, Work& w, long long ov, const double* X, int count, int* e, const unsigned int* mx) {
+  if (mx) oz_exponents_from_max(c.stream, count, mx, e, c.tc_err.get());
+  else oz_exponents(c.stream, count, ov, X, ov, e, w.ozw, c.tc_err.get());
+}
+
+// digits of V rows [first, first + count) in both layouts (mx: their maxima, or null)
+void slice_V(Ctx& c, Work& w, long long ov, int first, int count, const unsigned int* mx = nullptr) {
   if (!w.oz || count <= 0) return;
   const double* X = w.V.get() + (size_t)first * ov;
-  oz_exponents(c.stream, count, ov, X, ov, w.eV.get() + first, w.ozw, c.tc_err.get());
+  exponents(c, w, ov, X, count, w.eV.get() + first, mx);
   oz_slice(c.stream, count, ov, X, ov, w.eV.get() + first, w.Vtn.get(), w.Lp, first, w.Vnn.get(), w.ldk, first);
 }
 
 // digits of product rows [first, first + count) (S1 or S2): nn layout, and the
 // tn layout into rows tn_r0.. of the scratch operand Btn when with_tn
 void slice_P(Ctx& c, Work& w, long long ov, const double* P, DevBuf<int>& e, DevBuf<oz_t>& nn, int first, int count,
-             bool with_tn, int tn_r0 = 0) {
+             bool with_tn, int tn_r0 = 0, const unsigned int* mx = nullptr) {
   if (!w.oz || count <= 0) return;
   if (with_tn && tn_r0 + count > w.bcap) throw Error(XS_EINVAL, "subspace scratch operand too small");
   const double* X = P + (size_t)first * ov;
-  oz_exponents(c.stream, count, ov, X, ov, e.get() + first, w.ozw, c.tc_err.get());
+  exponents(c, w, ov, X, count, e.get() + first, mx);
   oz_slice(c.stream, count, ov, X, ov, e.get() + first, with_tn ? w.Btn.get() : nullptr, w.Lp, tn_r0, nn.get(),
            w.ldk, first);
 }
 
 // digits of count scratch rows T into Btn (exponents eB), and into Tnn when with_nn
-void slice_T(Ctx& c, Work& w, long long ov, const double* T, int count, bool with_nn = false) {
+void slice_T(Ctx& c, Work& w, long long ov, const double* T, int count, bool with_nn = false,
+             const unsigned int* mx = nullptr) {
   if (count > w.bcap || (with_nn && count * kOzDigits > w.ldkT))
     throw Error(XS_EINVAL, "subspace scratch operand too small");
-  oz_exponents(c.stream, count, ov, T, ov, w.eB.get(), w.ozw, c.tc_err.get());
+  exponents(c, w, ov, T, count, w.eB.get(), mx);
   oz_slice(c.stream, count, ov, T, ov, w.eB.get(), w.Btn.get(), w.Lp, 0, with_nn ? w.Tnn.get() : nullptr, w.ldkT, 0);
 }
 
@@ -171,22 +183,26 @@ __global__ void inv_norms_kernel(int n, const double* __restrict__ nrm, double* 
 
 // Orthonormalise the nnew rows of T against V[0:S] (classical Gram-Schmidt,
 // repeated when the first pass cancels much of a row) and among themselves (Loewdin, dropping directions whose Gram
-// eigenvalue is below kLowdinThresh); writes the kept rows to V[S:].
-int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double* Vout) {
+// eigenvalue is below kLowdinThresh); writes the kept rows to Vout (and,
+// on the tensor-core subspace, their maxima to vmax when given).
+int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double* Vout,
+                          unsigned int* vmax = nullptr) {
   cudaStream_t s = c.stream;
+  // maxima of T's rows from the kernels that write them (tensor-core subspace)
+  unsigned int* tmax = w.oz ? w.mxT.get() : nullptr;
   // unit rows first (on the device: no host round trip)
   row_norms(s, nnew, ov, w.T.get(), w.nrm.get());
   inv_norms_kernel<<<grid1(nnew, 64), 64, 0, s>>>(nnew, w.nrm.get(), w.nrm2.get());
   XS_CHECK_LAUNCH();
-  scale_rows(s, nnew, ov, w.T.get(), w.nrm2.get());
+  scale_rows(s, nnew, ov, w.T.get(), w.nrm2.get(), tmax);
   std::vector<double> h(nnew);
   for (int pass = 0; pass < 2 && S > 0; ++pass) {
     if (w.oz) {
-      slice_T(c, w, ov, w.T.get(), nnew);
+      slice_T(c, w, ov, w.T.get(), nnew, false, tmax);
       oz_gram(s, S, nnew, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eB.get(), 1.0, 0.0, w.tS.get(),
               nnew, w.ozw, c.tc_err.get());
       const OzBlock b{w.Vnn.get(), w.ldk, w.eV.get(), w.tS.get(), nnew};
-      oz_combine(s, 1, &b, S, nnew, ov, -1.0, 1.0, w.T.get(), ov, w.ozw, c.tc_err.get());
+      oz_combine(s, 1, &b, S, nnew, ov, -1.0, 1.0, w.T.get(), ov, w.ozw, c.tc_err.get(), tmax);
     } else {
       gram<double>(s, S, nnew, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.T.get(),
                    static_cast<int>(ov), w.tS.get(), nnew, 1.0, 0.0, w.gws);
@@ -202,7 +218,7 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
     }
   }
   if (w.oz) {
-    slice_T(c, w, ov, w.T.get(), nnew, true);
+    slice_T(c, w, ov, w.T.get(), nnew, true, tmax);
     oz_gram(s, nnew, nnew, ov, w.Btn.get(), w.Lp, w.eB.get(), w.Btn.get(), w.Lp, w.eB.get(), 1.0, 0.0, w.E2.get(),
             nnew, w.ozw, c.tc_err.get());
   } else {
@@ -221,7 +237,7 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
       // Vout = Bm T on the tensor cores: coefficients Bm^T (nnew x nkeep)
       transpose(s, nkeep, nnew, w.Bm.get(), w.coef.get());
       const OzBlock b{w.Tnn.get(), w.ldkT, w.eB.get(), w.coef.get(), nkeep};
-      oz_combine(s, 1, &b, nnew, nkeep, ov, 1.0, 0.0, Vout, ov, w.ozw, c.tc_err.get());
+      oz_combine(s, 1, &b, nnew, nkeep, ov, 1.0, 0.0, Vout, ov, w.ozw, c.tc_err.get(), vmax);
     } else {
       gemm<double>(s, false, false, nkeep, static_cast<int>(ov), nnew, 1.0, w.Bm.get(), nnew, 0, w.T.get(),
                    static_cast<int>(ov), 0, 0.0, Vout, static_cast<int>(ov), 0, 1);
@@ -428,6 +444,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     ensure_zeroed(w.S1nn, (size_t)ov * w.ldk);
     if (rpa) ensure_zeroed(w.S2nn, (size_t)ov * w.ldk);
     w.eV.ensure(Smax); w.eS1.ensure(Smax); w.eS2.ensure(Smax); w.eB.ensure(w.bcap);
+    w.mxV.ensure(Smax); w.mxS1.ensure(Smax); w.mxS2.ensure(Smax); w.mxT.ensure(w.bcap);
     w.coef.ensure((size_t)4 * Smax * 2 * kk);
     if (rpa) w.rcoef.ensure((size_t)Smax * 2 * kk);
   }
@@ -445,14 +462,18 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       for (auto& e : ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     }
   } events_guard{prod_events};
+  bool prod_max = false;   // the last products formed their rows' maxima
   auto apply = [&](int first, int count) {
     cudaEvent_t e0, e1;
     XS_CUDA(cudaEventCreate(&e0));
     XS_CUDA(cudaEventCreate(&e1));
     prod_events.emplace_back(e0, e1);
     XS_CUDA(cudaEventRecord(e0, s));
+    // the tensor-core products' epilogue forms the rows' maxima for the digit split
+    prod_max = w.oz && prod_prec == XS_MIXED;
     products(c, m, opt.method, prod_prec, count, w.V.get() + first * ov, w.S1.get() + first * ov,
-             rpa ? w.S2.get() + first * ov : nullptr, triplet);
+             rpa ? w.S2.get() + first * ov : nullptr, triplet, prod_max ? w.mxS1.get() + first : nullptr,
+             prod_max && rpa ? w.mxS2.get() + first : nullptr);
     XS_CUDA(cudaEventRecord(e1, s));
     st.products += count;
   };
@@ -539,13 +560,13 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     // projected matrices: new columns Sold..S-1 over all rows 0..S-1
     if (w.oz) {
       const int cnt = S - Sold;
-      slice_P(c, w, ov, w.S1.get(), w.eS1, w.S1nn, Sold, cnt, true, 0);
+      slice_P(c, w, ov, w.S1.get(), w.eS1, w.S1nn, Sold, cnt, true, 0, prod_max ? w.mxS1.get() + Sold : nullptr);
       if (!rpa) {
         oz_gram(s, S, cnt, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS1.get() + Sold, 1.0, 0.0,
                 w.a1.get() + Sold, Smax, w.ozw, c.tc_err.get());
       } else {
         // V^T [(A+B) V_new | (A-B) V_new] in one pass over V's digits
-        slice_P(c, w, ov, w.S2.get(), w.eS2, w.S2nn, Sold, cnt, true, cnt);
+        slice_P(c, w, ov, w.S2.get(), w.eS2, w.S2nn, Sold, cnt, true, cnt, prod_max ? w.mxS2.get() + Sold : nullptr);
         XS_CUDA(cudaMemcpyAsync(w.eB.get(), w.eS1.get() + Sold, sizeof(int) * cnt, cudaMemcpyDeviceToDevice, s));
         XS_CUDA(cudaMemcpyAsync(w.eB.get() + cnt, w.eS2.get() + Sold, sizeof(int) * cnt, cudaMemcpyDeviceToDevice,
                                 s));
@@ -677,9 +698,9 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
         if (rpa)
           XS_CUDA(cudaMemcpyAsync(w.T.get() + (size_t)k * ov, w.AX, sizeof(double) * k * ov,
                                   cudaMemcpyDeviceToDevice, s));
-        const int nb = orthonormalise_append(c, w, 0, nrows, ov, w.V.get());
+        const int nb = orthonormalise_append(c, w, 0, nrows, ov, w.V.get(), w.oz ? w.mxV.get() : nullptr);
         if (nb >= k) {
-          slice_V(c, w, ov, 0, nb);
+          slice_V(c, w, ov, 0, nb, w.oz ? w.mxV.get() : nullptr);
           prod_prec = kPrecF32;
           apply(0, nb);
           S = nb;
@@ -808,9 +829,10 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     }
     nnew = std::min(nnew, Smax - S);
     if (nnew <= 0) break;  // the subspace already spans everything it can hold
-    int nkeep = orthonormalise_append(c, w, S, nnew, ov, w.V.get() + (size_t)S * ov);
+    int nkeep = orthonormalise_append(c, w, S, nnew, ov, w.V.get() + (size_t)S * ov,
+                                      w.oz ? w.mxV.get() + S : nullptr);
     if (nkeep == 0) break;  // no new direction: stagnation
-    slice_V(c, w, ov, S, nkeep);
+    slice_V(c, w, ov, S, nkeep, w.oz ? w.mxV.get() + S : nullptr);
     Sold = S;
     S += nkeep;
     apply(Sold, nkeep);

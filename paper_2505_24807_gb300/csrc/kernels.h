@@ -84,7 +84,10 @@ void scatter(cudaStream_t s, int n, const long long* idx, const double* val, dou
 void residual_norms(cudaStream_t s, int nvec, long long len, const double* A, const double* B,
                     const double* omega, double* out_norm, double* R);
 void row_norms(cudaStream_t s, int nvec, long long len, const double* X, double* out_norm);
-void scale_rows(cudaStream_t s, int nvec, long long len, double* X, const double* scale);
+// X[r] *= scale[r]; rowmax (optional, zeroed here): per row abs_hi
+// (common.cuh) of the largest |scaled x|
+void scale_rows(cudaStream_t s, int nvec, long long len, double* X, const double* scale,
+                unsigned int* rowmax = nullptr);
 void convert_d2f(cudaStream_t s, long long n, const double* a, float* b);
 void convert_f2d(cudaStream_t s, long long n, const float* a, double* b);
 void split_d2f(cudaStream_t s, long long n, const double* a, float* hi, float* lo);

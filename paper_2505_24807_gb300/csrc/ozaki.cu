@@ -109,6 +109,7 @@ struct OzArgs {
   long long L;
   double beta;
   const double* scale;   // mode 1: per output k, alpha 2^(f_k - 42) and alpha 2^(f_k - 63)
+  unsigned int* rowmax;   // mode 1, optional: per output k abs_hi of the largest |y|
 };
 
 template <int BN>
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(192, 1)
               int* err) {
   using C = OzCfg<BN>;
   extern __shared__ uint8_t smem_raw[];
+  __shared__ unsigned int kmax[32];   // mode 1 with rowmax: this CTA's per-output maxima
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(base + C::STAGES * C::STAGE);
   uint64_t* empty = full + C::STAGES;
@@ -185,6 +187,7 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) tmem_alloc(tmem_slot, 2 * C::TCOLS);
+  if (threadIdx.x < 32) kmax[threadIdx.x] = 0u;
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -284,6 +287,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int k = 0; k < a.ncols; ++k) {
           float v[8];
           tmem_ld8(trow + k * 8, v);
+          unsigned int ym = 0;
           if (l < a.L) {
             double h, gg;
             horner8(v, h, gg);
@@ -291,6 +295,11 @@ __global__ void __launch_bounds__(192, 1)
             double* p = a.Y + static_cast<size_t>(k) * a.ldy + l;
             if (a.beta != 0.0) y = fma(a.beta, *p, y);
             *p = y;
+            ym = abs_hi(y);
+          }
+          if (a.rowmax) {   // the output's largest |y|: per CTA in shared memory, flushed at exit
+            ym = __reduce_max_sync(0xffffffffu, ym);
+            if (lane == 0 && ym) atomicMax(&kmax[k], ym);
           }
         }
       }
@@ -304,38 +313,40 @@ __global__ void __launch_bounds__(192, 1)
     fence_after_sync();
     tmem_dealloc(tmem, 2 * C::TCOLS);
   }
+  if (a.mode == 1 && a.rowmax && threadIdx.x < a.ncols && kmax[threadIdx.x])
+    atomicMax(&a.rowmax[threadIdx.x], kmax[threadIdx.x]);
 }
 
-// largest |x| of each row, as the bit pattern of a non-negative double (its
-// ordering is the integer ordering); four independent loads in flight per
-// thread
+// abs_hi of the largest |x| of each row (common.cuh: the high word of the
+// bit pattern, ordered like |x|); four independent loads in flight per thread
 __global__ void oz_absmax_kernel(long long L, const double* __restrict__ X, long long ldx,
-                                 unsigned long long* __restrict__ mx) {
+                                 unsigned int* __restrict__ mx) {
   const int r = blockIdx.y;
   const double* x = X + static_cast<size_t>(r) * ldx;
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  unsigned long long m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+  unsigned int m0 = 0, m1 = 0, m2 = 0, m3 = 0;
   long long l = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   for (; l + 3 * stride < L; l += 4 * stride) {
     const double a = x[l], b = x[l + stride], c = x[l + 2 * stride], d = x[l + 3 * stride];
-    m0 = max(m0, static_cast<unsigned long long>(__double_as_longlong(fabs(a))));
-    m1 = max(m1, static_cast<unsigned long long>(__double_as_longlong(fabs(b))));
-    m2 = max(m2, static_cast<unsigned long long>(__double_as_longlong(fabs(c))));
-    m3 = max(m3, static_cast<unsigned long long>(__double_as_longlong(fabs(d))));
+    m0 = max(m0, abs_hi(a));
+    m1 = max(m1, abs_hi(b));
+    m2 = max(m2, abs_hi(c));
+    m3 = max(m3, abs_hi(d));
   }
-  for (; l < L; l += stride) m0 = max(m0, static_cast<unsigned long long>(__double_as_longlong(fabs(x[l]))));
-  unsigned long long m = max(max(m0, m1), max(m2, m3));
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(&mx[r], m);
+  for (; l < L; l += stride) m0 = max(m0, abs_hi(x[l]));
+  unsigned int m = __reduce_max_sync(0xffffffffu, max(max(m0, m1), max(m2, m3)));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(&mx[r], m);
 }
 
-__global__ void oz_exp_kernel(int nvec, const unsigned long long* __restrict__ mx, int* __restrict__ e, int* err) {
+// exponents from abs_hi row maxima: max |x| < 2^(e-1), e = 0 for an all-zero
+// (or subnormal) row; a non-finite maximum raises the error word (code 10)
+__global__ void oz_exp_kernel(int nvec, const unsigned int* __restrict__ mx, int* __restrict__ e, int* err) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nvec) return;
-  const unsigned long long b = mx[r];
-  const int ex = static_cast<int>((b >> 52) & 0x7FF);
+  const unsigned int hw = mx[r];
+  const int ex = static_cast<int>((hw >> 20) & 0x7FF);
   if (ex == 0x7FF) atomicCAS(err, 0, 10);
-  e[r] = (b == 0) ? 0 : ex - 1021;
+  e[r] = (ex == 0) ? 0 : ex - 1021;
 }
 
 // One CTA per 64 consecutive amplitudes l and up to 32 vectors: digits are
@@ -528,12 +539,18 @@ constexpr int kMaxCols = 256 / kOzDigits;   // vectors (gram) or outputs (combin
 
 }  // namespace
 
+void oz_exponents_from_max(cudaStream_t s, int nvec, const unsigned int* mx, int* e, int* err) {
+  if (nvec <= 0) return;
+  oz_exp_kernel<<<(nvec + 127) / 128, 128, 0, s>>>(nvec, mx, e, err);
+  XS_CHECK_LAUNCH();
+}
+
 void oz_exponents(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, int* e, OzWork& w,
                   int* err) {
   if (nvec <= 0) return;
   ProfScope ps(s, "oz_exponents", 8.0 * nvec * L, 0.0);
   w.mx.ensure(nvec);
-  XS_CUDA(cudaMemsetAsync(w.mx.get(), 0, sizeof(unsigned long long) * nvec, s));
+  XS_CUDA(cudaMemsetAsync(w.mx.get(), 0, sizeof(unsigned int) * nvec, s));
   if (L > 0) {
     // about 8 CTAs per SM over all rows, at least 1024 amplitudes per CTA
     const long long per_row = std::max<long long>(1, std::min<long long>((8LL * 152 + nvec - 1) / nvec, (L + 1023) / 1024));
@@ -592,8 +609,9 @@ void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long lo
 }
 
 void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, long long L, double alpha, double beta,
-                double* Y, long long ldy, OzWork& w, int* err) {
+                double* Y, long long ldy, OzWork& w, int* err, unsigned int* rowmax) {
   if (nout <= 0 || L <= 0) return;
+  if (rowmax) XS_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(unsigned int) * nout, s));
   if (nb < 1 || nb > 3) throw Error(XS_EINVAL, "oz_combine: 1 to 3 blocks");
   if (S <= 0) throw Error(XS_EINVAL, "oz_combine: empty subspace");
   const int Kp = oz_ldk(S);
@@ -631,6 +649,7 @@ void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, lon
       a.L = L;
       a.beta = kb == 0 ? beta : 1.0;
       a.scale = w.scale.get();
+      a.rowmax = (rowmax && kb + KB_CHUNK >= kb_total) ? rowmax + k0 : nullptr;
       ProfScope ps(s, "oz_combine",
                    2.0 * kOzDigits * static_cast<double>(L) * a.kb_per_cta * BKE / kOzDigits +
                        8.0 * nk * (double)L * (a.beta != 0.0 ? 2 : 1),

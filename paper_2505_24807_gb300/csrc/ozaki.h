@@ -29,13 +29,17 @@ struct OzWork {
   DevBuf<double> part;              // split partial sums of oz_gram
   DevBuf<oz_t> bmat;                // digit matrix of the oz_combine coefficients
   DevBuf<double> scale;             // their per-output weights (two per output)
-  DevBuf<unsigned long long> mx;    // per-row max |x| bit patterns
+  DevBuf<unsigned int> mx;          // per-row abs_hi of max |x|
 };
 
 // e[r] such that max_l |X[r][l]| < 2^(e[r]-1), rows r < nvec (row stride ldx).
 // A non-finite entry raises the error word (code 10).
 void oz_exponents(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, int* e, OzWork& w,
                   int* err);
+
+// The same exponents from per-row maxima already formed by the kernel that
+// wrote the rows (abs_hi of max |x|, common.cuh; see oz_combine's rowmax).
+void oz_exponents_from_max(cudaStream_t s, int nvec, const unsigned int* mx, int* e, int* err);
 
 // Digit planes of rows r < nvec of X (exponents e[r]), written as
 //   tn: planes [(tn_r0 + r) * 8 + i][l] (row stride Lp >= L, a multiple of 8;
@@ -64,9 +68,11 @@ struct OzBlock {
 };
 
 // Y[k][l] (row stride ldy) = alpha * sum_b sum_{m<S} coef_b[m][k] X_b[m][l] + beta * Y[k][l]
-// for k < nout, l < L, over nb <= 3 blocks.
+// for k < nout, l < L, over nb <= 3 blocks.  rowmax (optional, nout entries):
+// per output row abs_hi (common.cuh) of the largest |Y[k][l]|, formed in the
+// epilogue (input of oz_exponents_from_max).
 void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, long long L, double alpha, double beta,
-                double* Y, long long ldy, OzWork& w, int* err);
+                double* Y, long long ldy, OzWork& w, int* err, unsigned int* rowmax = nullptr);
 
 // Row stride of the nn layout for up to S rows.
 inline int oz_ldk(int S) { return ((S * kOzDigits + 63) / 64) * 64; }

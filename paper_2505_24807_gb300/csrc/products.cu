@@ -129,10 +129,10 @@ void products_f32(Ctx& c, DevMol& m, int method, int nvec, const double* X, doub
 }
 
 void products(Ctx& c, DevMol& m, int method, int precision, int nvec, const double* X, double* Y1, double* Y2,
-              bool triplet) {
+              bool triplet, unsigned int* mx1, unsigned int* mx2) {
   if (nvec <= 0) return;
   if (precision == XS_MIXED) {
-    products_mixed(c, m, method, nvec, X, Y1, Y2, triplet);
+    products_mixed(c, m, method, nvec, X, Y1, Y2, triplet, mx1, mx2);
     return;
   }
   if (precision == kPrecF32) {

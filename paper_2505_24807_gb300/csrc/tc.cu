@@ -19,7 +19,8 @@
 
 namespace xs {
 
-void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2, bool triplet) {
+void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2, bool triplet,
+                    unsigned int* mx1, unsigned int* mx2) {
   cudaStream_t s = c.stream;
   const int n = m.n, o = m.o, v = m.v;
   const int np_ = pad32(n), op = pad32(o), vp = pad32(v);
@@ -90,6 +91,8 @@ void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, do
     err.alloc(1);
     XS_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
   }
+  if (mx1) XS_CUDA(cudaMemsetAsync(mx1, 0, sizeof(unsigned int) * nvec, s));
+  if (mx2 && rpa) XS_CUDA(cudaMemsetAsync(mx2, 0, sizeof(unsigned int) * nvec, s));
 
   for (int k0 = 0; k0 < nvec; k0 += chunk) {
     const int k = (nvec - k0) < chunk ? (nvec - k0) : chunk;
@@ -133,6 +136,7 @@ void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, do
       const float* Gph = pass == 0 ? Gh : Gmh;
       const float* Gpl = pass == 0 ? Gl : Gml;
       double* Yout = (pass == 0 ? Y1 : Y2) + k0 * ov;
+      unsigned int* mxo = pass == 0 ? mx1 : mx2;
       {  // S^T = C_vir^T G^T : M = v, N = n, K = n
         TcOperand A{CTvir_h, CTvir_l, np_, 0, false};
         TcOperand B{Gph, Gpl, np_, (long long)n * np_, true};
@@ -145,6 +149,7 @@ void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, do
         TcOperand B{Sh, Sl, np_, (long long)v * np_, true};
         TcEpilogue e;
         e.mode = 2; e.Y = Yout; e.X = Xk; e.eps = m.eps.get(); e.ld = v; e.bstride = ov; e.o = o;
+        e.rowmax = mxo ? mxo + k0 : nullptr;
         tc_gemm(s, A, B, o, v, np_, k, e, err.get());
       }
     }

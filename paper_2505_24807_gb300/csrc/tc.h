@@ -6,7 +6,8 @@
 
 namespace xs {
 
+// mx1, mx2: optional per-vector abs_hi maxima of Y1 / Y2 (see products.h)
 void products_mixed(Ctx& c, DevMol& m, int method, int nvec, const double* X, double* Y1, double* Y2,
-                    bool triplet = false);
+                    bool triplet = false, unsigned int* mx1 = nullptr, unsigned int* mx2 = nullptr);
 
 }  // namespace xs

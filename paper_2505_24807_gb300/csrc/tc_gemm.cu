@@ -89,6 +89,7 @@ struct EpiArgs {
   int ld;               // leading dimension of the output rows
   long long bstride;    // output stride between batch entries
   int o;                // mode 2: number of occupied orbitals (eps offset of the virtuals)
+  unsigned int* rowmax;   // mode 2, optional: per batch entry abs_hi of max |Y|
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
       if (!ok) break;
       float* st = stage_ep + (warp - 2) * 32 * 17;
       const int c2 = lane & 15, rb = lane >> 4;
+      unsigned int ymax = 0;   // mode 2: abs_hi of the largest |Y| this lane stored
 #pragma unroll
       for (int c0 = 0; c0 < CW; c0 += 16) {
 #pragma unroll
@@ -280,10 +282,16 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
             ep.Dlo[rbo + col] = l;
           } else {
             const double de = ep.eps[ep.o + col] - ep.eps[row];
-            ep.Y[rbo + col] = static_cast<double>(x) + de * ep.X[rbo + col];
+            const double y = static_cast<double>(x) + de * ep.X[rbo + col];
+            ep.Y[rbo + col] = y;
+            ymax = max(ymax, abs_hi(y));
           }
         }
         __syncwarp();
+      }
+      if (ep.mode == 2 && ep.rowmax) {
+        ymax = __reduce_max_sync(0xffffffffu, ymax);
+        if (lane == 0 && ymax) atomicMax(&ep.rowmax[bz], ymax);
       }
     }
   }
@@ -417,7 +425,7 @@ void launch_tc(cudaStream_t s, const TcOperand& A, const TcOperand& B, int M, in
   const CUtensorMap al = make_map(A.lo, M, Kpad, A.ld, A.batched ? batch : 1, A.bstride, BM);
   const CUtensorMap bh = make_map(B.hi, N, Kpad, B.ld, B.batched ? batch : 1, B.bstride, BNv);
   const CUtensorMap bl = make_map(B.lo, N, Kpad, B.ld, B.batched ? batch : 1, B.bstride, BNv);
-  EpiArgs ep{e.mode, e.D, e.Dlo, e.Y, e.X, e.eps, e.ld, e.bstride, e.o};
+  EpiArgs ep{e.mode, e.D, e.Dlo, e.Y, e.X, e.eps, e.ld, e.bstride, e.o, e.rowmax};
   const size_t smem = smem_bytes<BNv>();
   static const bool attr_set = [smem] {   // once per process (thread-safe initialisation)
     XS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BNv>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -17,7 +17,9 @@ struct TcOperand {
 };
 
 // Epilogue: mode 0 stores float D; mode 1 stores the TF32 pair (D, Dlo) of the
-// result; mode 2 stores double Y = D + (eps[o + col] - eps[row]) X.
+// result; mode 2 stores double Y = D + (eps[o + col] - eps[row]) X and, when
+// rowmax is set, raises rowmax[b] to abs_hi of the largest |Y| of batch entry
+// b (common.cuh; the caller zeroes it first).
 struct TcEpilogue {
   int mode = 0;
   float* D = nullptr;
@@ -28,6 +30,7 @@ struct TcEpilogue {
   int ld = 0;
   long long bstride = 0;
   int o = 0;
+  unsigned int* rowmax = nullptr;
 };
 
 // D[b] (M x N) = A[b] B[b]^T from TF32 pairs: hi*hi + hi*lo + lo*hi, float32

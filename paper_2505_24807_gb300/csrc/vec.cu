@@ -1,6 +1,7 @@
 // Elementwise and reduction kernels of libxs (Davidson steps 4-6 of the
 // paper's Section "GPU Implementation": residuals, norms, diagonal
 // preconditioner; and the orbital-energy term of Eq. cis_matrix_vector).
+#include <algorithm>
 #include <cfloat>
 
 #include "kernels.h"
@@ -128,10 +129,23 @@ __global__ void sqrt_kernel(int n, double* x) {
   if (i < n) x[i] = sqrt(x[i]);
 }
 
-__global__ void scale_rows_kernel(int nvec, long long len, double* X, const double* __restrict__ scale) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= len * nvec) return;
-  X[idx] *= scale[idx / len];
+// row r of X scaled by scale[r]; with rowmax, abs_hi of the largest |scaled
+// x| of the row (one atomic max per warp)
+__global__ void scale_rows_kernel(long long len, double* X, const double* __restrict__ scale,
+                                  unsigned int* __restrict__ rowmax) {
+  const int r = blockIdx.y;
+  double* x = X + (long long)r * len;
+  const double f = scale[r];
+  unsigned int m = 0;
+  for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < len; l += (long long)gridDim.x * blockDim.x) {
+    const double y = x[l] * f;
+    x[l] = y;
+    m = max(m, abs_hi(y));
+  }
+  if (rowmax) {
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&rowmax[r], m);
+  }
 }
 
 __global__ void d2f_kernel(long long n, const double* __restrict__ a, float* __restrict__ b) {
@@ -234,11 +248,15 @@ void row_norms(cudaStream_t s, int nvec, long long len, const double* X, double*
   residual_norms(s, nvec, len, X, nullptr, nullptr, out_norm, nullptr);
 }
 
-void scale_rows(cudaStream_t s, int nvec, long long len, double* X, const double* scale) {
+void scale_rows(cudaStream_t s, int nvec, long long len, double* X, const double* scale,
+                unsigned int* rowmax) {
   long long n = (long long)nvec * len;
   if (n == 0) return;
   ProfScope ps(s, "scale_rows", 16.0 * n, 0.0);
-  scale_rows_kernel<<<grid1(n, 256), 256, 0, s>>>(nvec, len, X, scale);
+  if (rowmax) XS_CUDA(cudaMemsetAsync(rowmax, 0, sizeof(unsigned int) * nvec, s));
+  // about 8 CTAs per SM over all rows, at least 1024 elements per CTA
+  const long long per_row = std::max<long long>(1, std::min<long long>((8LL * 152 + nvec - 1) / nvec, (len + 1023) / 1024));
+  scale_rows_kernel<<<dim3(static_cast<unsigned>(per_row), nvec), 256, 0, s>>>(len, X, scale, rowmax);
   XS_CHECK_LAUNCH();
 }
 
