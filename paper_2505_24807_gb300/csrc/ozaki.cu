@@ -112,13 +112,20 @@ struct OzArgs {
   unsigned int* rowmax;   // mode 1, optional: per output k abs_hi of the largest |y|
 };
 
+// Tile widths up to 256 columns alternate two TMEM accumulators (a tile's
+// epilogue overlaps the next tile's MMAs); the 320-column Gram tile (40
+// vectors: the TDHF projections of 20 new vectors in one pass over V) holds
+// one 512-column accumulator, issues an N = 256 and an N = 64 MMA per K step
+// and loads its B tile as two 160-row boxes.
 template <int BN>
 struct OzCfg {
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr int STAGES = (200 * 1024) / STAGE > 8 ? 8 : (200 * 1024) / STAGE;
-  static constexpr int TCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  static constexpr int NBUF = BN > 256 ? 1 : 2;
+  static constexpr int TCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : BN <= 256 ? 256 : 512;
+  static constexpr int BOX = BN > 256 ? BN / 2 : BN;   // B rows per TMA box
   static constexpr size_t SMEM = 1024 + static_cast<size_t>(STAGES) * STAGE + (2 * STAGES + 4) * 8 + 16;
 };
 
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(tmem_slot, 2 * C::TCOLS);
+  if (warp == 1) tmem_alloc(tmem_slot, C::NBUF * C::TCOLS);
   if (threadIdx.x < 32) kmax[threadIdx.x] = 0u;
   fence_before_sync();
   __syncthreads();
@@ -217,22 +224,25 @@ __global__ void __launch_bounds__(192, 1)
           tma_load_2d(st, ta, &full[s], (kb - b * a.kb_per_blk) * BKE, m0);
         }
         tma_load_2d(st + C::A_BYTES, &tmB, &full[s], kb * BKE, 0);
+        if (C::BOX < BN) tma_load_2d(st + C::A_BYTES + C::BOX * 128, &tmB, &full[s], kb * BKE, C::BOX);
       }
     }
     // the copies still in flight complete before the CTA leaves (bounded)
     for (long long q = (g > C::STAGES ? g - C::STAGES : 0); q < g; ++q)
       mbar_wait(&empty[q % C::STAGES], static_cast<uint32_t>((q / C::STAGES) & 1), err, 0) || true;
   } else if (warp == 1 && lane == 0) {
-    // MMA issue
-    constexpr uint32_t idesc = idesc_f32acc(1, BM, BN);
+    // MMA issue (N1 columns, plus N2 more for the 320-column tile)
+    constexpr int N1 = BN > 256 ? 256 : BN, N2 = BN - N1;
+    constexpr uint32_t idesc = idesc_f32acc(1, BM, N1);
+    constexpr uint32_t idesc2 = idesc_f32acc(1, BM, N2 > 0 ? N2 : 16);
     long long g = 0;
     int i = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++i) {
       int m0, kb0, nk, kc;
       tile_of(t, m0, kb0, nk, kc);
-      const int buf = i & 1;
-      if (i >= 2 && !mbar_wait(&acce[buf], static_cast<uint32_t>(((i >> 1) + 1) & 1), err, 4)) break;
+      const int buf = i % C::NBUF, use = i / C::NBUF;
+      if (use >= 1 && !mbar_wait(&acce[buf], static_cast<uint32_t>((use + 1) & 1), err, 4)) break;
       fence_after_sync();
       const uint32_t acc = tmem + static_cast<uint32_t>(buf * C::TCOLS);
       for (int it = 0; it < nk; ++it, ++g) {
@@ -248,6 +258,8 @@ __global__ void __launch_bounds__(192, 1)
         for (int kk = 0; kk < BKE / 16; ++kk) {
           const uint32_t off = kk * 32;   // 16 bf16 per MMA step
           mma_bf16(acc, sdesc(aa + off), sdesc(bb + off), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+          if (N2 > 0)
+            mma_bf16(acc + N1, sdesc(aa + off), sdesc(bb + N1 * 128 + off), idesc2, (it > 0 || kk > 0) ? 1u : 0u);
         }
         mma_commit(&empty[s]);
       }
@@ -261,8 +273,8 @@ __global__ void __launch_bounds__(192, 1)
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++i) {
       int m0, kb0, nk, kc;
       tile_of(t, m0, kb0, nk, kc);
-      const int buf = i & 1;
-      if (!mbar_wait(&accf[buf], static_cast<uint32_t>((i >> 1) & 1), err, 3)) break;
+      const int buf = i % C::NBUF;
+      if (!mbar_wait(&accf[buf], static_cast<uint32_t>((i / C::NBUF) & 1), err, 3)) break;
       fence_after_sync();
       const uint32_t trow = tmem + static_cast<uint32_t>(buf * C::TCOLS) + (static_cast<uint32_t>(32 * q) << 16);
       if (a.mode == 0) {
@@ -311,7 +323,7 @@ __global__ void __launch_bounds__(192, 1)
   __syncthreads();
   if (warp == 1) {
     fence_after_sync();
-    tmem_dealloc(tmem, 2 * C::TCOLS);
+    tmem_dealloc(tmem, C::NBUF * C::TCOLS);
   }
   if (a.mode == 1 && a.rowmax && threadIdx.x < a.ncols && kmax[threadIdx.x])
     atomicMax(&a.rowmax[threadIdx.x], kmax[threadIdx.x]);
@@ -523,7 +535,7 @@ void launch_oz(cudaStream_t s, const CUtensorMap& a0, const CUtensorMap& a1, con
   XS_CHECK_LAUNCH();
 }
 
-int pick_bn(int cols) { return cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 192 ? 192 : 256; }
+int pick_bn(int cols) { return cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 192 ? 192 : cols <= 256 ? 256 : 320; }
 
 void dispatch(cudaStream_t s, int bn, const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& a2,
               const CUtensorMap& b, const OzArgs& args, int* err) {
@@ -531,11 +543,13 @@ void dispatch(cudaStream_t s, int bn, const CUtensorMap& a0, const CUtensorMap& 
     case 64: launch_oz<64>(s, a0, a1, a2, b, args, err); break;
     case 128: launch_oz<128>(s, a0, a1, a2, b, args, err); break;
     case 192: launch_oz<192>(s, a0, a1, a2, b, args, err); break;
-    default: launch_oz<256>(s, a0, a1, a2, b, args, err); break;
+    case 256: launch_oz<256>(s, a0, a1, a2, b, args, err); break;
+    default: launch_oz<320>(s, a0, a1, a2, b, args, err); break;
   }
 }
 
-constexpr int kMaxCols = 256 / kOzDigits;   // vectors (gram) or outputs (combine) per launch
+constexpr int kMaxCols = 256 / kOzDigits;       // outputs of a combination per launch
+constexpr int kMaxGramCols = 320 / kOzDigits;   // B vectors of a Gram per launch
 
 }  // namespace
 
@@ -582,12 +596,12 @@ void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long lo
   const int kb_total = static_cast<int>((L + BKE - 1) / BKE);
   const int nchunk = (kb_total + KB_CHUNK - 1) / KB_CHUNK;
   const CUtensorMap ta = make_map_bf16(Atn, L, static_cast<long long>(M) * kOzDigits, Alp, BM);
-  for (int n0 = 0; n0 < N; n0 += kMaxCols) {
-    const int nn = std::min(kMaxCols, N - n0);
+  for (int n0 = 0; n0 < N; n0 += kMaxGramCols) {
+    const int nn = std::min(kMaxGramCols, N - n0);
     const int bn = pick_bn(nn * kOzDigits);
     const CUtensorMap tb =
         make_map_bf16(Btn + static_cast<size_t>(n0) * kOzDigits * Blp, L, static_cast<long long>(nn) * kOzDigits, Blp,
-                      bn);
+                      bn > 256 ? bn / 2 : bn);
     w.part.ensure(static_cast<size_t>(nchunk) * M * nn);
     OzArgs a{};
     a.mode = 0;

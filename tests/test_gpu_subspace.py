@@ -33,7 +33,10 @@ def _mixed(rng, shape, spread=10.0):
     return x
 
 
-@pytest.mark.parametrize("M,N,L", [(37, 5, 5000 + 37), (3, 33, 4096), (160, 20, 100_003), (1, 1, 1)])
+# N = 37, 40 and 81 reach the 320-column Gram tile (up to 40 B vectors per
+# launch, a partly filled second 160-row box for 37, three launches for 81)
+@pytest.mark.parametrize("M,N,L", [(37, 5, 5000 + 37), (3, 33, 4096), (160, 20, 100_003), (1, 1, 1),
+                                   (50, 40, 30_011), (17, 37, 9000), (5, 81, 5000)])
 def test_gram_matches_float64(ctx, M, N, L):
     from paper_2505_24807_gb300 import xs
     rng = np.random.default_rng(M * 1000 + N + L)
@@ -58,6 +61,20 @@ def test_gram_integers_exact(ctx):
     L = 20_000
     A = rng.integers(-2**16, 2**16, size=(19, L))
     B = rng.integers(-2**16, 2**16, size=(9, L))
+    exact = A @ B.T
+    assert np.abs(exact).max() < 2**53
+    got = xs.xs_subspace_gram(ctx, A.astype(np.float64), B.astype(np.float64), emulated=True)
+    assert np.array_equal(got, exact.astype(np.float64))
+
+
+def test_gram_integers_exact_wide(ctx):
+    """The 320-column Gram tile (40 B vectors, one pass over A) is exact on
+    integer inputs like the narrower tiles."""
+    from paper_2505_24807_gb300 import xs
+    rng = np.random.default_rng(11)
+    L = 12_345
+    A = rng.integers(-2**16, 2**16, size=(23, L))
+    B = rng.integers(-2**16, 2**16, size=(40, L))
     exact = A @ B.T
     assert np.abs(exact).max() < 2**53
     got = xs.xs_subspace_gram(ctx, A.astype(np.float64), B.astype(np.float64), emulated=True)
