@@ -685,9 +685,10 @@ int xs_subspace_gram(xs_ctx* ctx, int M, int N, long long L, const double* A, co
       xs::OzWork w;
       xs::oz_exponents(s, M, L, dA.get(), L, eA.get(), w, c.tc_err.get());
       xs::oz_exponents(s, N, L, dB.get(), L, eB.get(), w, c.tc_err.get());
-      xs::oz_slice(s, M, L, dA.get(), L, eA.get(), ta.get(), Lp, 0, nullptr, 0, 0);
-      xs::oz_slice(s, N, L, dB.get(), L, eB.get(), tb.get(), Lp, 0, nullptr, 0, 0);
-      xs::oz_gram(s, M, N, L, ta.get(), Lp, eA.get(), tb.get(), Lp, eB.get(), 1.0, 0.0, dC.get(), N, w,
+      const long long PA = (long long)M * xs::kOzDigits, PB = (long long)N * xs::kOzDigits;   // plane capacities
+      xs::oz_slice(s, M, L, dA.get(), L, eA.get(), ta.get(), PA, 0, nullptr, 0, 0);
+      xs::oz_slice(s, N, L, dB.get(), L, eB.get(), tb.get(), PB, 0, nullptr, 0, 0);
+      xs::oz_gram(s, M, N, L, ta.get(), PA, eA.get(), tb.get(), PB, eB.get(), 1.0, 0.0, dC.get(), N, w,
                   c.tc_err.get());
       xs::check_device_error(c);
     } else {

@@ -60,7 +60,7 @@ struct Work {
   // V as Gram operand (tn) and as combination operand (nn), A V / (A+B) V and
   // (A-B) V as combination operands, one scratch tn operand (new vectors)
   bool oz = false;
-  long long Lp = 0;
+  long long Lp = 0, Pv = 0, Pb = 0;   // amplitudes per plane; plane capacities of Vtn and Btn
   int ldk = 0, bcap = 0;
   DevBuf<oz_t> Vtn, Vnn, S1nn, S2nn, Btn, Tnn;
   int ldkT = 0;
@@ -108,7 +108,7 @@ void slice_V(Ctx& c, Work& w, long long ov, int first, int count, const unsigned
   if (!w.oz || count <= 0) return;
   const double* X = w.V.get() + (size_t)first * ov;
   exponents(c, w, ov, X, count, w.eV.get() + first, mx);
-  oz_slice(c.stream, count, ov, X, ov, w.eV.get() + first, w.Vtn.get(), w.Lp, first, w.Vnn.get(), w.ldk, first);
+  oz_slice(c.stream, count, ov, X, ov, w.eV.get() + first, w.Vtn.get(), w.Pv, first, w.Vnn.get(), w.ldk, first);
 }
 
 // digits of product rows [first, first + count) (S1 or S2): nn layout, and the
@@ -119,7 +119,7 @@ void slice_P(Ctx& c, Work& w, long long ov, const double* P, DevBuf<int>& e, Dev
   if (with_tn && tn_r0 + count > w.bcap) throw Error(XS_EINVAL, "subspace scratch operand too small");
   const double* X = P + (size_t)first * ov;
   exponents(c, w, ov, X, count, e.get() + first, mx);
-  oz_slice(c.stream, count, ov, X, ov, e.get() + first, with_tn ? w.Btn.get() : nullptr, w.Lp, tn_r0, nn.get(),
+  oz_slice(c.stream, count, ov, X, ov, e.get() + first, with_tn ? w.Btn.get() : nullptr, w.Pb, tn_r0, nn.get(),
            w.ldk, first);
 }
 
@@ -129,7 +129,7 @@ void slice_T(Ctx& c, Work& w, long long ov, const double* T, int count, bool wit
   if (count > w.bcap || (with_nn && count * kOzDigits > w.ldkT))
     throw Error(XS_EINVAL, "subspace scratch operand too small");
   exponents(c, w, ov, T, count, w.eB.get(), mx);
-  oz_slice(c.stream, count, ov, T, ov, w.eB.get(), w.Btn.get(), w.Lp, 0, with_nn ? w.Tnn.get() : nullptr, w.ldkT, 0);
+  oz_slice(c.stream, count, ov, T, ov, w.eB.get(), w.Btn.get(), w.Pb, 0, with_nn ? w.Tnn.get() : nullptr, w.ldkT, 0);
 }
 
 // Coefficients of the CIS step, outputs [X (kk) | R (kk)] with X_j = V q_j and
@@ -199,7 +199,7 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
   for (int pass = 0; pass < 2 && S > 0; ++pass) {
     if (w.oz) {
       slice_T(c, w, ov, w.T.get(), nnew, false, tmax);
-      oz_gram(s, S, nnew, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eB.get(), 1.0, 0.0, w.tS.get(),
+      oz_gram(s, S, nnew, ov, w.Vtn.get(), w.Pv, w.eV.get(), w.Btn.get(), w.Pb, w.eB.get(), 1.0, 0.0, w.tS.get(),
               nnew, w.ozw, c.tc_err.get());
       const OzBlock b{w.Vnn.get(), w.ldk, w.eV.get(), w.tS.get(), nnew};
       oz_combine(s, 1, &b, S, nnew, ov, -1.0, 1.0, w.T.get(), ov, w.ozw, c.tc_err.get(), tmax);
@@ -219,7 +219,7 @@ int orthonormalise_append(Ctx& c, Work& w, int S, int nnew, long long ov, double
   }
   if (w.oz) {
     slice_T(c, w, ov, w.T.get(), nnew, true, tmax);
-    oz_gram(s, nnew, nnew, ov, w.Btn.get(), w.Lp, w.eB.get(), w.Btn.get(), w.Lp, w.eB.get(), 1.0, 0.0, w.E2.get(),
+    oz_gram(s, nnew, nnew, ov, w.Btn.get(), w.Pb, w.eB.get(), w.Btn.get(), w.Pb, w.eB.get(), 1.0, 0.0, w.E2.get(),
             nnew, w.ozw, c.tc_err.get());
   } else {
     gram<double>(s, nnew, nnew, static_cast<int>(ov), w.T.get(), static_cast<int>(ov), w.T.get(),
@@ -426,11 +426,13 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       XS_CUDA(cudaMemsetAsync(c.tc_err.get(), 0, sizeof(int), s));
     }
     w.Lp = oz_lp(ov);
+    w.Pv = (long long)Smax * kOzDigits;
     w.ldk = oz_ldk(Smax);
     const int tcap = std::max(maxnew, std::max(nguess, 2 * kk));   // rows of a new block
     w.bcap = (rpa ? 2 : 1) * tcap;                                  // TDHF projections: two blocks
     w.Vtn.ensure((size_t)Smax * kOzDigits * w.Lp);
     w.Btn.ensure((size_t)w.bcap * kOzDigits * w.Lp);
+    w.Pb = (long long)w.bcap * kOzDigits;
     w.ldkT = oz_ldk(tcap);
     // digit rows past the live vectors are read (times zero coefficients) and
     // must be finite: zero them when (re)allocated; later contents are digits
@@ -562,7 +564,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
       const int cnt = S - Sold;
       slice_P(c, w, ov, w.S1.get(), w.eS1, w.S1nn, Sold, cnt, true, 0, prod_max ? w.mxS1.get() + Sold : nullptr);
       if (!rpa) {
-        oz_gram(s, S, cnt, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS1.get() + Sold, 1.0, 0.0,
+        oz_gram(s, S, cnt, ov, w.Vtn.get(), w.Pv, w.eV.get(), w.Btn.get(), w.Pb, w.eS1.get() + Sold, 1.0, 0.0,
                 w.a1.get() + Sold, Smax, w.ozw, c.tc_err.get());
       } else {
         // V^T [(A+B) V_new | (A-B) V_new] in one pass over V's digits
@@ -570,7 +572,7 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
         XS_CUDA(cudaMemcpyAsync(w.eB.get(), w.eS1.get() + Sold, sizeof(int) * cnt, cudaMemcpyDeviceToDevice, s));
         XS_CUDA(cudaMemcpyAsync(w.eB.get() + cnt, w.eS2.get() + Sold, sizeof(int) * cnt, cudaMemcpyDeviceToDevice,
                                 s));
-        oz_gram(s, S, 2 * cnt, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eB.get(), 1.0, 0.0, w.tS.get(),
+        oz_gram(s, S, 2 * cnt, ov, w.Vtn.get(), w.Pv, w.eV.get(), w.Btn.get(), w.Pb, w.eB.get(), 1.0, 0.0, w.tS.get(),
                 2 * cnt, w.ozw, c.tc_err.get());
         XS_CUDA(cudaMemcpy2DAsync(w.a1.get() + Sold, sizeof(double) * Smax, w.tS.get(), sizeof(double) * 2 * cnt,
                                   sizeof(double) * cnt, S, cudaMemcpyDeviceToDevice, s));
@@ -812,10 +814,10 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
         if (w.oz) {
           slice_V(c, w, ov, 0, nc);
           slice_P(c, w, ov, w.S1.get(), w.eS1, w.S1nn, 0, nc, true);
-          oz_gram(s, nc, nc, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS1.get(), 1.0, 0.0,
+          oz_gram(s, nc, nc, ov, w.Vtn.get(), w.Pv, w.eV.get(), w.Btn.get(), w.Pb, w.eS1.get(), 1.0, 0.0,
                   w.a1.get(), Smax, w.ozw, c.tc_err.get());
           slice_P(c, w, ov, w.S2.get(), w.eS2, w.S2nn, 0, nc, true);
-          oz_gram(s, nc, nc, ov, w.Vtn.get(), w.Lp, w.eV.get(), w.Btn.get(), w.Lp, w.eS2.get(), 1.0, 0.0,
+          oz_gram(s, nc, nc, ov, w.Vtn.get(), w.Pv, w.eV.get(), w.Btn.get(), w.Pb, w.eS2.get(), 1.0, 0.0,
                   w.a2.get(), Smax, w.ozw, c.tc_err.get());
         } else {
           gram<double>(s, nc, nc, static_cast<int>(ov), w.V.get(), static_cast<int>(ov), w.S1.get(),

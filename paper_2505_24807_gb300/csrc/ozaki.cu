@@ -217,14 +217,17 @@ __global__ void __launch_bounds__(192, 1)
         mbar_expect_tx(&full[s], C::STAGE);
         const int kb = kb0 + it;
         if (a.mode == 0) {
-          tma_load_2d(st, &tmA0, &full[s], kb * BKE, m0);
+          // blocked planes (3-D maps: amplitude in block, plane, block): the
+          // tile's planes of one K block are one contiguous read
+          tma_load_3d(st, &tmA0, &full[s], 0, m0, kb);
+          tma_load_3d(st + C::A_BYTES, &tmB, &full[s], 0, 0, kb);
+          if (C::BOX < BN) tma_load_3d(st + C::A_BYTES + C::BOX * 128, &tmB, &full[s], 0, C::BOX, kb);
         } else {
           const int b = kb / a.kb_per_blk;
           const CUtensorMap* ta = b == 0 ? &tmA0 : (b == 1 ? &tmA1 : &tmA2);
           tma_load_2d(st, ta, &full[s], (kb - b * a.kb_per_blk) * BKE, m0);
+          tma_load_2d(st + C::A_BYTES, &tmB, &full[s], kb * BKE, 0);
         }
-        tma_load_2d(st + C::A_BYTES, &tmB, &full[s], kb * BKE, 0);
-        if (C::BOX < BN) tma_load_2d(st + C::A_BYTES + C::BOX * 128, &tmB, &full[s], kb * BKE, C::BOX);
       }
     }
     // the copies still in flight complete before the CTA leaves (bounded)
@@ -369,14 +372,15 @@ constexpr int kSliceL = 64, kSliceR = 32;
 
 __global__ void __launch_bounds__(256) oz_slice_kernel(int nvec, long long L, const double* __restrict__ X,
                                                        long long ldx, const int* __restrict__ e,
-                                                       oz_t* __restrict__ tn, long long Lp, int tn_r0,
-                                                       oz_t* __restrict__ nn, int ldk, int nn_r0) {
+                                                       oz_t* __restrict__ tn, long long Lp, long long P,
+                                                       int tn_r0, oz_t* __restrict__ nn, int ldk, int nn_r0) {
   __shared__ uint4 tile[kSliceR][kSliceL];
   const long long l0 = static_cast<long long>(blockIdx.x) * kSliceL;
   const int r0 = blockIdx.y * kSliceR;
   const int nr = min(kSliceR, nvec - r0);
   // each thread splits two consecutive amplitudes, so every tn plane gets one
-  // 4-byte store per pair (Lp and the pair's first index are even)
+  // 4-byte store per pair (the pair's first index is even and shares its
+  // 64-amplitude block)
   constexpr int kPairs = kSliceL / 2;
   for (int item = threadIdx.x; item < nr * kPairs; item += blockDim.x) {
     const int r = item / kPairs, li = 2 * (item % kPairs);
@@ -400,7 +404,8 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(int nvec, long long L, co
 #pragma unroll
       for (int i = 0; i < kOzDigits; ++i) {
         const uint32_t two = static_cast<uint32_t>(digit_bits(d0[i])) | (static_cast<uint32_t>(digit_bits(d1[i])) << 16);
-        *reinterpret_cast<uint32_t*>(tn + (static_cast<size_t>(tn_r0 + rv) * kOzDigits + i) * Lp + l) = two;
+        const size_t p = static_cast<size_t>(tn_r0 + rv) * kOzDigits + i;
+        *reinterpret_cast<uint32_t*>(tn + ((static_cast<size_t>(l >> 6) * P + p) << 6) + (l & 63)) = two;
       }
     }
     if (nn) {
@@ -495,6 +500,24 @@ __global__ void oz_coef_kernel(int nb, int S, int Kp, int k0, CoefArgs ca, doubl
 }
 
 // inner x rows bf16 matrix, row stride ld elements, boxes of 64 x box_rows
+// tn digit planes (oz_slice): rows planes of a blocked array with plane
+// capacity P, nblk blocks of 64 amplitudes; box = 64 amplitudes x box_rows
+// planes of one block
+CUtensorMap make_map_planes(const oz_t* ptr, long long rows, long long P, long long nblk, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(BKE), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(nblk)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(BKE) * 2, static_cast<cuuint64_t>(P) * BKE * 2};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(BKE), static_cast<cuuint32_t>(box_rows), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || rows <= 0 || nblk <= 0 || P < rows)
+    throw Error(XS_EINVAL, "digit planes not 16-byte aligned, empty or beyond their capacity");
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<oz_t*>(ptr), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(XS_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+  return m;
+}
+
 CUtensorMap make_map_bf16(const oz_t* ptr, long long inner, long long rows, long long ld, int box_rows) {
   CUtensorMap m;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(rows)};
@@ -577,31 +600,33 @@ void oz_exponents(cudaStream_t s, int nvec, long long L, const double* X, long l
 }
 
 void oz_slice(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, const int* e, oz_t* tn,
-              long long Lp, int tn_r0, oz_t* nn, int ldk, int nn_r0) {
+              long long P, int tn_r0, oz_t* nn, int ldk, int nn_r0) {
   if (nvec <= 0 || (!tn && !nn)) return;
-  if (tn && (Lp < L || Lp % 8)) throw Error(XS_EINVAL, "oz_slice: bad plane stride");
+  const long long Lp = oz_lp(L);
+  if (tn && P < static_cast<long long>(tn_r0 + nvec) * kOzDigits) throw Error(XS_EINVAL, "oz_slice: plane capacity");
   if (nn && ldk % 64) throw Error(XS_EINVAL, "oz_slice: bad nn stride");
   const long long span = tn ? Lp : L;
   ProfScope ps(s, "oz_slice", 8.0 * nvec * L + (tn ? 16.0 * nvec * Lp : 0.0) + (nn ? 16.0 * nvec * L : 0.0), 0.0);
   dim3 grid(static_cast<unsigned>((span + kSliceL - 1) / kSliceL), (nvec + kSliceR - 1) / kSliceR);
-  oz_slice_kernel<<<grid, 256, 0, s>>>(nvec, L, X, ldx, e, tn, Lp, tn_r0, nn, ldk, nn_r0);
+  oz_slice_kernel<<<grid, 256, 0, s>>>(nvec, L, X, ldx, e, tn, Lp, P, tn_r0, nn, ldk, nn_r0);
   XS_CHECK_LAUNCH();
 }
 
-void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long long Alp, const int* eA,
-             const oz_t* Btn, long long Blp, const int* eB, double alpha, double beta, double* C, int ldc,
+void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long long AP, const int* eA,
+             const oz_t* Btn, long long BP, const int* eB, double alpha, double beta, double* C, int ldc,
              OzWork& w, int* err) {
   if (M <= 0 || N <= 0) return;
   if (L <= 0) throw Error(XS_EINVAL, "oz_gram: empty vectors");
   const int kb_total = static_cast<int>((L + BKE - 1) / BKE);
   const int nchunk = (kb_total + KB_CHUNK - 1) / KB_CHUNK;
-  const CUtensorMap ta = make_map_bf16(Atn, L, static_cast<long long>(M) * kOzDigits, Alp, BM);
+  const long long nblk = oz_lp(L) / BKE;
+  const CUtensorMap ta = make_map_planes(Atn, static_cast<long long>(M) * kOzDigits, AP, nblk, BM);
   for (int n0 = 0; n0 < N; n0 += kMaxGramCols) {
     const int nn = std::min(kMaxGramCols, N - n0);
     const int bn = pick_bn(nn * kOzDigits);
-    const CUtensorMap tb =
-        make_map_bf16(Btn + static_cast<size_t>(n0) * kOzDigits * Blp, L, static_cast<long long>(nn) * kOzDigits, Blp,
-                      bn > 256 ? bn / 2 : bn);
+    // B planes n0 * 8.. of every block: the map starts n0 * 8 planes into block 0
+    const CUtensorMap tb = make_map_planes(Btn + static_cast<size_t>(n0) * kOzDigits * BKE,
+                                           static_cast<long long>(nn) * kOzDigits, BP, nblk, bn > 256 ? bn / 2 : bn);
     w.part.ensure(static_cast<size_t>(nchunk) * M * nn);
     OzArgs a{};
     a.mode = 0;

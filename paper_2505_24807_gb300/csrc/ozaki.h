@@ -42,18 +42,21 @@ void oz_exponents(cudaStream_t s, int nvec, long long L, const double* X, long l
 void oz_exponents_from_max(cudaStream_t s, int nvec, const unsigned int* mx, int* e, int* err);
 
 // Digit planes of rows r < nvec of X (exponents e[r]), written as
-//   tn: planes [(tn_r0 + r) * 8 + i][l] (row stride Lp >= L, a multiple of 8;
-//       columns L..Lp-1 are set to 0), i = 0 the most significant digit;
+//   tn: plane p = (tn_r0 + r) * 8 + i (i = 0 the most significant digit) in
+//       blocks of 64 amplitudes: element (p, l) at ((l / 64) * P + p) * 64 +
+//       l % 64, P the array's plane capacity (each block holds all its planes'
+//       64 digits contiguously, so a tile of consecutive planes is one
+//       contiguous read); amplitudes L..oz_lp(L)-1 are set to 0;
 //   nn: [l][(nn_r0 + r) * 8 + i] (row stride ldk, a multiple of 64).
 // Either output may be null.
 void oz_slice(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, const int* e, oz_t* tn,
-              long long Lp, int tn_r0, oz_t* nn, int ldk, int nn_r0);
+              long long P, int tn_r0, oz_t* nn, int ldk, int nn_r0);
 
 // C (M x N, row stride ldc) = alpha * A B^T + beta * C, where A holds M rows and
-// B holds N rows of length L as tn digit planes (row strides Alp, Blp) with
+// B holds N rows of length L as tn digit planes (plane capacities AP, BP) with
 // exponents eA, eB.  Split over L into float32-exact chunks of 4096.
-void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long long Alp, const int* eA,
-             const oz_t* Btn, long long Blp, const int* eB, double alpha, double beta, double* C, int ldc,
+void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long long AP, const int* eA,
+             const oz_t* Btn, long long BP, const int* eB, double alpha, double beta, double* C, int ldc,
              OzWork& w, int* err);
 
 // One block of a combination: the first S rows of a stored set (nn digit
@@ -76,7 +79,7 @@ void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, lon
 
 // Row stride of the nn layout for up to S rows.
 inline int oz_ldk(int S) { return ((S * kOzDigits + 63) / 64) * 64; }
-// Row stride of the tn layout for vectors of length L.
+// Amplitudes of the tn layout for vectors of length L (whole 64-amplitude blocks).
 inline long long oz_lp(long long L) { return ((L + 63) / 64) * 64; }
 
 }  // namespace xs
