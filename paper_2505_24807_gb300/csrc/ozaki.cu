@@ -223,9 +223,11 @@ __global__ void __launch_bounds__(192, 1)
           tma_load_3d(st + C::A_BYTES, &tmB, &full[s], 0, 0, kb);
           if (C::BOX < BN) tma_load_3d(st + C::A_BYTES + C::BOX * 128, &tmB, &full[s], 0, C::BOX, kb);
         } else {
+          // blocked nn rows (3-D maps: column in block, amplitude, block): a
+          // tile's 128 amplitudes of one column block are one contiguous read
           const int b = kb / a.kb_per_blk;
           const CUtensorMap* ta = b == 0 ? &tmA0 : (b == 1 ? &tmA1 : &tmA2);
-          tma_load_2d(st, ta, &full[s], (kb - b * a.kb_per_blk) * BKE, m0);
+          tma_load_3d(st, ta, &full[s], 0, m0, kb - b * a.kb_per_blk);
           tma_load_2d(st + C::A_BYTES, &tmB, &full[s], kb * BKE, 0);
         }
       }
@@ -418,9 +420,10 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(int nvec, long long L, co
   for (int item = threadIdx.x; item < kSliceL * nr; item += blockDim.x) {
     const int li = item / nr, r = item % nr;
     const long long l = l0 + li;
-    if (l < L)
-      *reinterpret_cast<uint4*>(nn + static_cast<size_t>(l) * ldk + static_cast<size_t>(nn_r0 + r0 + r) * kOzDigits) =
-          tile[r][li];
+    if (l < L) {
+      const size_t k = static_cast<size_t>(nn_r0 + r0 + r) * kOzDigits;   // 64-column blocks, all amplitudes each
+      *reinterpret_cast<uint4*>(nn + (((k >> 6) * L + l) << 6) + (k & 63)) = tile[r][li];
+    }
   }
 }
 
@@ -604,7 +607,8 @@ void oz_slice(cudaStream_t s, int nvec, long long L, const double* X, long long 
   if (nvec <= 0 || (!tn && !nn)) return;
   const long long Lp = oz_lp(L);
   if (tn && P < static_cast<long long>(tn_r0 + nvec) * kOzDigits) throw Error(XS_EINVAL, "oz_slice: plane capacity");
-  if (nn && ldk % 64) throw Error(XS_EINVAL, "oz_slice: bad nn stride");
+  if (nn && (ldk % 64 || static_cast<long long>(nn_r0 + nvec) * kOzDigits > ldk))
+    throw Error(XS_EINVAL, "oz_slice: nn column capacity");
   const long long span = tn ? Lp : L;
   ProfScope ps(s, "oz_slice", 8.0 * nvec * L + (tn ? 16.0 * nvec * Lp : 0.0) + (nn ? 16.0 * nvec * L : 0.0), 0.0);
   dim3 grid(static_cast<unsigned>((span + kSliceL - 1) / kSliceL), (nvec + kSliceR - 1) / kSliceR);
@@ -659,8 +663,9 @@ void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, lon
   CUtensorMap ta[3];
   CoefArgs ca{};
   for (int b = 0; b < nb; ++b) {
-    if (blk[b].ldk < Kp || blk[b].ldk % 64) throw Error(XS_EINVAL, "oz_combine: nn stride too small");
-    ta[b] = make_map_bf16(blk[b].nn, Kp, L, blk[b].ldk, BM);
+    if (blk[b].ldk < Kp || blk[b].ldk % 64) throw Error(XS_EINVAL, "oz_combine: nn capacity too small");
+    // the first Kp / 64 column blocks of L amplitudes each (the same 3-D form as the tn planes)
+    ta[b] = make_map_planes(blk[b].nn, L, L, Kp / BKE, BM);
     ca.coef[b] = blk[b].coef;
     ca.ldc[b] = blk[b].ldc;
     ca.e[b] = blk[b].e;

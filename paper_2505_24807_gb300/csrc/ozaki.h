@@ -47,7 +47,10 @@ void oz_exponents_from_max(cudaStream_t s, int nvec, const unsigned int* mx, int
 //       l % 64, P the array's plane capacity (each block holds all its planes'
 //       64 digits contiguously, so a tile of consecutive planes is one
 //       contiguous read); amplitudes L..oz_lp(L)-1 are set to 0;
-//   nn: [l][(nn_r0 + r) * 8 + i] (row stride ldk, a multiple of 64).
+//   nn: column k = (nn_r0 + r) * 8 + i of amplitude row l, in blocks of 64
+//       columns: element (l, k) at ((k / 64) * L + l) * 64 + k % 64 (each
+//       block holds its 64 columns of every amplitude contiguously; ldk, a
+//       multiple of 64, is the column capacity).
 // Either output may be null.
 void oz_slice(cudaStream_t s, int nvec, long long L, const double* X, long long ldx, const int* e, oz_t* tn,
               long long P, int tn_r0, oz_t* nn, int ldk, int nn_r0);
@@ -60,8 +63,8 @@ void oz_gram(cudaStream_t s, int M, int N, long long L, const oz_t* Atn, long lo
              OzWork& w, int* err);
 
 // One block of a combination: the first S rows of a stored set (nn digit
-// layout with row stride ldk, exponents e) and its coefficients coef[m][k]
-// (row stride ldc).
+// layout with column capacity ldk, exponents e) and its coefficients
+// coef[m][k] (row stride ldc).
 struct OzBlock {
   const oz_t* nn;
   int ldk;
@@ -77,7 +80,7 @@ struct OzBlock {
 void oz_combine(cudaStream_t s, int nb, const OzBlock* blk, int S, int nout, long long L, double alpha, double beta,
                 double* Y, long long ldy, OzWork& w, int* err, unsigned int* rowmax = nullptr);
 
-// Row stride of the nn layout for up to S rows.
+// Column capacity of the nn layout for up to S rows (whole 64-column blocks).
 inline int oz_ldk(int S) { return ((S * kOzDigits + 63) / 64) * 64; }
 // Amplitudes of the tn layout for vectors of length L (whole 64-amplitude blocks).
 inline long long oz_lp(long long L) { return ((L + 63) / 64) * 64; }
