@@ -199,7 +199,8 @@ int xs_apply(xs_ctx* ctx, int mol, int kind, int nvec, const double* in, double*
  * batched Davidson steps 1-6; RPA in the symmetric subspace form of
  * Stratmann, Scuseria and Frisch).  Outputs are host or device arrays of
  * n_mol * nroots entries: omega (eV), osc (oscillator strengths), resid
- * (final residual norms, eV); iters has n_mol entries.  Any output may be
+ * (final residual norms, eV); iters has n_mol entries.  A molecule has
+ * nocc * nvir roots at most: entries past them are 0.  Any output may be
  * NULL.  Returns XS_ENOCONV with best estimates filled if the iteration cap
  * is reached, XS_EUNSTABLE if A - B is not positive definite (TDHF). */
 int xs_excited(xs_ctx* ctx, const xs_ex_opts* opts, double* omega, double* osc, int* iters,
@@ -288,6 +289,17 @@ int xs_subspace_gram(xs_ctx* ctx, int M, int N, long long L, const double* A, co
 /* Y (nout x L) = sum_{b<nb} coef_b^T X_b, X: nb x S x L, coef: nb x S x nout, 1 <= nb <= 3 */
 int xs_subspace_combine(xs_ctx* ctx, int nb, int S, int nout, long long L, const double* X, const double* coef,
                         double* Y, int emulated);
+
+/* The Rayleigh-Ritz eigensolver of the Davidson step on its own (paper,
+ * batched step 3: diagonalise the projected matrix, keep the lowest K):
+ * the k lowest eigenpairs of the symmetric S x S float64 matrix A (row-major,
+ * 1 <= k <= S <= 1024), eigenvalues ascending in w (k entries), eigenvectors
+ * in the columns of Z (S x k, row-major: Z[i * k + t]).  Householder
+ * tridiagonalisation, float32 Sturm multisection, float64 inverse iteration
+ * (clusters of close eigenvalues orthogonalised as they are found), one CTA.
+ * Host or device pointers owned by the caller; synchronous.  XS_EINVAL for bad
+ * sizes. */
+int xs_subspace_eig(xs_ctx* ctx, int S, int k, const double* A, double* w, double* Z);
 
 /* Parameter derivatives of a CIS or TDHF excitation energy (paper, Section
  * "Overview of the capabilities of PySEQM": the semiempirical parameters are

@@ -13,6 +13,7 @@
 #include "kernels.h"
 #include "products.h"
 #include "scf.h"
+#include "syev.h"
 
 using xs::Ctx;
 using xs::DevBuf;
@@ -696,6 +697,21 @@ int xs_subspace_gram(xs_ctx* ctx, int M, int N, long long L, const double* A, co
                        dC.get(), N, 1.0, 0.0, c.ws0);
     }
     copy_any(s, C, dC.get(), sizeof(double) * M * N);
+    XS_CUDA(cudaStreamSynchronize(s));
+    return XS_OK;
+  });
+}
+
+int xs_subspace_eig(xs_ctx* ctx, int S, int k, const double* A, double* w, double* Z) {
+  return guarded(ctx, [&](Ctx& c) {
+    if (S < 1 || S > 1024 || k < 1 || k > S || !A || !w || !Z) throw Error(XS_EINVAL, "bad eigensolver arguments");
+    cudaStream_t s = c.stream;
+    DevBuf<double> dA((size_t)S * S), dw((size_t)k), dZ((size_t)S * k), scratch;
+    DevBuf<int> info(1);
+    copy_any(s, dA.get(), A, sizeof(double) * S * S);
+    xs::syevk(s, S, k, dA.get(), S, dw.get(), dZ.get(), k, scratch, info.get());
+    copy_any(s, w, dw.get(), sizeof(double) * k);
+    copy_any(s, Z, dZ.get(), sizeof(double) * S * k);
     XS_CUDA(cudaStreamSynchronize(s));
     return XS_OK;
   });

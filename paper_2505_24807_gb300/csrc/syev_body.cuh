@@ -389,22 +389,47 @@ __device__ void syevk_body(int S, int k, const double* __restrict__ Ain, int lda
   }
   __syncthreads();
 
-  // 3. float64 inverse iteration, thread t -> column t of Zw
+  // 3. float64 inverse iteration, one thread per cluster (an isolated
+  //    eigenvalue is a cluster of one) -> columns of Zw.  Inside a cluster the
+  //    members are found in order, each solve followed by Gram-Schmidt against
+  //    the members already found: independent iterations of a nearly
+  //    degenerate pair converge to nearly the same vector, and orthogonalising
+  //    them afterwards would magnify their error outside the cluster by the
+  //    inverse of the angle between them.
   const double tiny = 1e-30 * tnorm;
-  for (int t = tid; t < k; t += nt) {
-    double* y = Zw + t;
-    double* lut = lu + (size_t)t * 5 * S;
-    for (int i = 0; i < S; ++i) y[(long long)i * k] = 1.0 + 0.01 * ((i * 7 + t * 3) % 11);
-    inverse_step(S, d, e, lam[t], tiny, true, lut, y, k);
-    inverse_step(S, d, e, lam[t], tiny, false, lut, y, k);
-    if (cl[t] == t && (t + 1 >= k || cl[t + 1] != t)) {
-      // isolated: one more solve shifted by the Rayleigh quotient
+  auto orth_against = [&](double* y, int c0, int u) {   // y -= sum_{c0 <= v < u} (z_v . y) z_v, then normalise
+    for (int v = c0; v < u; ++v) {
+      const double* z = Zw + v;
+      double dot = 0.0;
+      for (int i = 0; i < S; ++i) dot = fma(z[(long long)i * k], y[(long long)i * k], dot);
+      for (int i = 0; i < S; ++i) y[(long long)i * k] = fma(-dot, z[(long long)i * k], y[(long long)i * k]);
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < S; ++i) nrm = fma(y[(long long)i * k], y[(long long)i * k], nrm);
+    const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+    for (int i = 0; i < S; ++i) y[(long long)i * k] *= inv;
+  };
+  for (int c0 = tid; c0 < k; c0 += nt) {
+    if (cl[c0] != c0) continue;   // not the first member of its cluster
+    int c1 = c0 + 1;
+    while (c1 < k && cl[c1] == c0) ++c1;
+    for (int t = c0; t < c1; ++t) {
+      double* y = Zw + t;
+      double* lut = lu + (size_t)t * 5 * S;
+      for (int i = 0; i < S; ++i) y[(long long)i * k] = 1.0 + 0.01 * ((i * 7 + t * 3) % 11);
+      inverse_step(S, d, e, lam[t], tiny, true, lut, y, k);
+      orth_against(y, c0, t);
+      inverse_step(S, d, e, lam[t], tiny, false, lut, y, k);
+      orth_against(y, c0, t);
+      // one more solve shifted by the Rayleigh quotient: the spread shift of
+      // a cluster member sits up to (members) x sep from the cluster, which
+      // leaves neighbouring eigenvectors in y at (sep / gap)^2; shifted by the
+      // Rayleigh quotient they fall by a further (spread inside / gap)
       const double rq = rayleigh(S, d, e, y, k);
       inverse_step(S, d, e, rq, tiny, true, lut, y, k);
-    } else {
-      inverse_step(S, d, e, lam[t], tiny, false, lut, y, k);
+      if (c1 - c0 > 1) orth_against(y, c0, t);
     }
-    lam[t] = rayleigh(S, d, e, y, k);
+    for (int t = c0; t < c1; ++t) lam[t] = rayleigh(S, d, e, Zw + t, k);
   }
   __syncthreads();
   // clusters: Gram-Schmidt inside each, then (up to kMaxRR members) a

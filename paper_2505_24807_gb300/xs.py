@@ -86,6 +86,7 @@ def load():
         "xs_gbuild_noalloc": (i, [vp, i, i, vp, vp]),
         "xs_subspace_gram": (i, [vp, i, i, C.c_longlong, vp, vp, vp, i]),
         "xs_subspace_combine": (i, [vp, i, i, i, C.c_longlong, vp, vp, vp, i]),
+        "xs_subspace_eig": (i, [vp, i, i, vp, vp, vp]),
         "xs_spectrum": (i, [vp, i, vp, vp, d, i, vp, vp]),
         "xs_gradient": (i, [vp, i, i, vp, C.POINTER(i)]),
         "xs_mlp_nparams": (i, []),
@@ -247,6 +248,17 @@ def xs_subspace_gram(ctx, A, B, emulated=True):
     Cm = np.empty((M, N))
     _check(ctx, load().xs_subspace_gram(ctx, M, N, L, _ptr(A), _ptr(B), _ptr(Cm), int(bool(emulated))))
     return Cm
+
+
+def xs_subspace_eig(ctx, A, k):
+    """k lowest eigenpairs of the symmetric float64 matrix A with the Davidson
+    step's eigensolver: (w ascending, Z with the eigenvectors in columns)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    S = A.shape[0]
+    w = np.empty(k)
+    Z = np.empty((S, k))
+    _check(ctx, load().xs_subspace_eig(ctx, S, int(k), _ptr(A), _ptr(w), _ptr(Z)))
+    return w, Z
 
 
 def xs_subspace_combine(ctx, X, coef, emulated=True):
