@@ -59,7 +59,8 @@ def test_roots_invariant_under_reordering_and_rigid_motion(method, precision):
 
 
 @pytest.mark.parametrize("method", ["CIS", "RPA"])
-def test_separated_fragments_double_every_root(method):
+@pytest.mark.parametrize("batched", [0, 1])
+def test_separated_fragments_double_every_root(method, batched):
     params = molgen.make_params(0)
     Z, xyz = molgen.config_small(5)
     rng = np.random.default_rng(23)
@@ -67,10 +68,22 @@ def test_separated_fragments_double_every_root(method):
     dimer = (np.concatenate([Z, Z]), np.concatenate([xyz, far]))
     meth = xs.XS_CIS if method == "CIS" else xs.XS_TDHF
     k = 5
-    wm, fm = _solve(params, [(Z, xyz)], meth, xs.XS_FP64, k, 1e-9)
-    # 2k + 2 roots: no degenerate pair is cut at the last requested root
-    wd, fd = _solve(params, [dimer], meth, xs.XS_FP64, 2 * k + 2, 1e-9)
-    wd, fd = wd[0][:2 * k], fd[0][:2 * k]
+    # 2k + 2 roots: no degenerate pair is cut at the last requested root;
+    # batched = 1 solves monomer and dimer together in the lock-step batch
+    if batched:
+        ctx = context(params)
+        try:
+            xs.xs_ground_state(ctx.h, [(Z, xyz), dimer], scf_tol=1e-11)
+            out = xs.xs_excited(ctx.h, method=meth, nroots=2 * k + 2, tol=1e-9, precision=xs.XS_FP64, batched=1,
+                                n_mol=2)
+        finally:
+            ctx.close()
+        wm, fm = out["omega"][:1, :k], out["osc"][:1, :k]
+        wd, fd = out["omega"][1][:2 * k], out["osc"][1][:2 * k]
+    else:
+        wm, fm = _solve(params, [(Z, xyz)], meth, xs.XS_FP64, k, 1e-9)
+        wd, fd = _solve(params, [dimer], meth, xs.XS_FP64, 2 * k + 2, 1e-9)
+        wd, fd = wd[0][:2 * k], fd[0][:2 * k]
     # at 1000 Angstrom the other fragment's field and the exciton coupling move
     # the roots by ~1e-7 eV at most
     assert np.abs(wd[0::2] - wm[0]).max() < 1e-6
