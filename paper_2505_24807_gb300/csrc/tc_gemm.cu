@@ -17,7 +17,7 @@
 //
 // Persistent CTAs (one per SM) walk the 128 x BN output tiles (cta_group::1,
 // M = 128):
-//   warp 0      TMA producer: four 128-byte-swizzled boxes per K block of 32
+//   warp 0      TMA producer: four 64-byte-swizzled boxes per K block of 16
 //   warp 1      TMEM allocation and the single-thread MMA issue into a ring
 //               of NSLOT chunk accumulators
 //   warps 2..   epilogue (4, or 8 for 256-wide tiles: two warps per group of
@@ -43,13 +43,16 @@ namespace {
 using namespace tc5;
 
 constexpr int BM = 128;
-constexpr int BK = 32;       // 32 tf32 = 128 bytes = one swizzle atom row
-// stage ring depth: 4 stages of 48 KB for 64-wide tiles, 3 of 64 KB for
-// 128-wide tiles, 2 of 96 KB for 256-wide tiles (which halve the A-tile
-// re-reads per flop)
+constexpr int BK = 16;       // 16 tf32 = 64 bytes = one 64-byte swizzle row
+constexpr int kPadK = 32;    // operands' K padding (a multiple of BK)
+// stage ring depth: 8 stages of 24 KB for 64-wide tiles, 6 of 32 KB for
+// 128-wide tiles, 4 of 48 KB for 256-wide tiles (which halve the A-tile
+// re-reads per flop).  K blocks of 16 rather than 32 keep the same 192 KB of
+// buffers in twice as many stages, so more of them are in flight while the
+// MMAs consume one.
 template <int BN>
-__host__ __device__ constexpr int stages_for() { return BN >= 256 ? 2 : (BN >= 128 ? 3 : 4); }
-constexpr int kChunkBlocks = 4;   // K blocks (of 32 terms) per promoted chunk
+__host__ __device__ constexpr int stages_for() { return BN >= 256 ? 4 : (BN >= 128 ? 6 : 8); }
+constexpr int kChunkBlocks = 8;   // K blocks (of 16 terms) per promoted chunk
 // TMEM chunk slots (BN columns each, at most 512 columns) and epilogue warps
 template <int BN>
 __host__ __device__ constexpr int slots_for() { return BN >= 256 ? 2 : 4; }
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int M, int N,
                    int Kpad, int a3, int b3, int ntm, int ntn, int ntiles, EpiArgs ep, int* err) {
   extern __shared__ uint8_t smem_raw[];
-  // 1024-byte aligned stage buffers (the 128-byte swizzle repeats every 1024 bytes)
+  // 1024-byte aligned stage buffers (the 64-byte swizzle repeats every 512 bytes)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int STAGES = stages_for<BN>();
   constexpr int NSLOT = slots_for<BN>();
@@ -206,9 +209,9 @@ __global__ void __launch_bounds__(threads_for<BN>(), 1)
           for (int kk = 0; kk < BK / 8; ++kk) {
             const uint32_t off = kk * 32;  // 8 tf32 per MMA step
             const uint32_t acc0 = (kb > kc || kk > 0) ? 1u : 0u;
-            mma_tf32(acc, sdesc(ah + off), sdesc(bh + off), idesc, acc0);
-            mma_tf32(acc, sdesc(ah + off), sdesc(bl + off), idesc, 1u);
-            mma_tf32(acc, sdesc(al + off), sdesc(bh + off), idesc, 1u);
+            mma_tf32(acc, sdesc64(ah + off), sdesc64(bh + off), idesc, acc0);
+            mma_tf32(acc, sdesc64(ah + off), sdesc64(bl + off), idesc, 1u);
+            mma_tf32(acc, sdesc64(al + off), sdesc64(bh + off), idesc, 1u);
           }
           mma_commit(&empty[s]);
         }
@@ -366,7 +369,7 @@ CUtensorMap make_map(const float* ptr, int rows, int kpad, int ld, int batch, lo
   if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ld % 4) || (kpad % BK))
     throw Error(XS_EINVAL, "tensor-core operand not 16-byte aligned or not padded");
   CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, r3 ? 3 : 2, const_cast<float*>(ptr), dims, strides,
-                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(XS_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
   return m;
@@ -381,7 +384,7 @@ size_t smem_bytes() {
 
 }  // namespace
 
-int pad32(int k) { return (k + BK - 1) / BK * BK; }
+int pad32(int k) { return (k + kPadK - 1) / kPadK * kPadK; }
 
 template <typename S>
 void split_pad(cudaStream_t s, int rows, int cols, int ld_dst, const S* src, int ld_src, long long sstride,
