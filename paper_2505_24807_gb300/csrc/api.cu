@@ -573,9 +573,10 @@ int xs_mlp_forward(xs_ctx* ctx, int rows, const float* features, float* out) {
     DevBuf<float> F((size_t)rows * xs::kMlpFeatures);
     copy_any(c.stream, F.get(), features, sizeof(float) * F.n);
     std::vector<DevBuf<float>> Z, H;
-    c.mlp->forward(c.stream, rows, F.get(), Z, H);
+    xs::MlpOperands mo;
+    c.mlp->forward(c.stream, rows, F.get(), Z, H, mo);
     copy_any(c.stream, out, H[xs::kMlpLayers - 1].get(), sizeof(float) * rows * xs::kMlpOutputs);
-    XS_CUDA(cudaStreamSynchronize(c.stream));
+    xs::Mlp::check(c.stream, mo);
     return XS_OK;
   });
 }
@@ -589,7 +590,8 @@ int xs_mlp_grad(xs_ctx* ctx, int rows, const float* features, const float* targe
     copy_any(c.stream, T.get(), targets, sizeof(float) * T.n);
     const float cw[2] = {0.01f, 1.0f};
     copy_any(c.stream, colw.get(), cw, sizeof(cw));
-    const float l = c.mlp->gradient(c.stream, rows, F.get(), T.get(), colw.get(), scratch);
+    xs::MlpOperands mo;
+    const float l = c.mlp->gradient(c.stream, rows, F.get(), T.get(), colw.get(), scratch, mo);
     copy_any(c.stream, grad, c.mlp->g.get(), sizeof(float) * c.mlp->nparams());
     XS_CUDA(cudaStreamSynchronize(c.stream));
     if (loss) *loss = l;
@@ -608,13 +610,14 @@ int xs_mlp_train(xs_ctx* ctx, int rows, const float* features, const float* targ
     const float cw[2] = {0.01f, 1.0f};
     copy_any(c.stream, colw.get(), cw, sizeof(cw));
     XS_CUDA(cudaStreamSynchronize(c.stream));
+    xs::MlpOperands mo;
     for (int e = 0; e < epochs; ++e) {
       double sum = 0.0;
       int nb = 0;
       for (int r0 = 0; r0 < rows; r0 += batch) {
         const int rb = std::min(batch, rows - r0);
         sum += c.mlp->train_step(c.stream, rb, F.get() + (size_t)r0 * xs::kMlpFeatures,
-                                 T.get() + (size_t)r0 * xs::kMlpOutputs, colw.get(), lr, scratch);
+                                 T.get() + (size_t)r0 * xs::kMlpOutputs, colw.get(), lr, scratch, mo);
         ++nb;
       }
       if (loss) loss[e] = static_cast<float>(sum / nb);

@@ -1421,6 +1421,7 @@ struct BatchWork {
   DevBuf<float> F, out;
   DevBuf<int> lrow;
   std::vector<DevBuf<float>> Z, H;
+  MlpOperands mo;   // the network's tensor-core operand pairs
   int* hnact = nullptr;    // page-locked copy of the active count
   BatchWork() = default;
   BatchWork(const BatchWork&) = delete;
@@ -1741,10 +1742,11 @@ void solve_group(Ctx& c, BatchWork& bw, const xs_ex_opts& opt, int first, int co
     }
     for (int r = 0; r < total; r += kForwardRows) {
       const int rows = std::min(kForwardRows, total - r);
-      c.mlp->forward(s, rows, bw.F.get() + (size_t)r * kMlpFeatures, bw.Z, bw.H);
+      c.mlp->forward(s, rows, bw.F.get() + (size_t)r * kMlpFeatures, bw.Z, bw.H, bw.mo);
       XS_CUDA(cudaMemcpyAsync(bw.out.get() + (size_t)r * kMlpOutputs, bw.H[kMlpLayers - 1].get(),
                               sizeof(float) * rows * kMlpOutputs, cudaMemcpyDeviceToDevice, s));
     }
+    Mlp::check(s, bw.mo);
     bw.lpairs.ensure(allp.size());
     XS_CUDA(cudaMemcpyAsync(bw.lpairs.get(), allp.data(), sizeof(long long) * allp.size(), cudaMemcpyHostToDevice, s));
     bw.lrow.ensure(2 * (size_t)count);

@@ -76,6 +76,7 @@ struct Work {
   DevBuf<float> F;
   DevBuf<long long> dpairs;
   std::vector<DevBuf<float>> Z, H;
+  MlpOperands mo;   // the network's tensor-core operand pairs
   DevBuf<double> lshift, dsh, fdev;
   // page-locked host staging of the per-iteration read-back
   double* hpin = nullptr;
@@ -512,9 +513,10 @@ int davidson(Ctx& c, DevMol& m, const xs_ex_opts& opt, SolveStats& st) {
     std::vector<long long> pairs = lowest_gap_pairs(c, m, npairs);
     w.F.ensure((size_t)pairs.size() * kMlpFeatures);
     pair_features(c, m, pairs, w.F.get(), w.dpairs, w.fw);
-    c.mlp->forward(s, static_cast<int>(pairs.size()), w.F.get(), w.Z, w.H);
+    c.mlp->forward(s, static_cast<int>(pairs.size()), w.F.get(), w.Z, w.H, w.mo);
     std::vector<float> out(pairs.size() * kMlpOutputs);
     sync_copy(s, out.data(), w.H[kMlpLayers - 1].get(), sizeof(float) * out.size());
+    Mlp::check(s, w.mo);
     // preconditioner shift on the candidate pairs, zero elsewhere
     std::vector<double> sh(pairs.size());
     for (size_t q = 0; q < pairs.size(); ++q) sh[q] = out[q * kMlpOutputs];

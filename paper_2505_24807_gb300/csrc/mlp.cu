@@ -14,7 +14,7 @@
 // Training targets come from the exact diagonal (float64, two-centre part as
 // P W P^T over packed pair densities plus closed-form one-centre terms) and
 // from converged amplitudes.  Training and inference run through the
-// project's own kernels (SIMT GEMM, gelu, Adam); nothing here changes the
+// project's own kernels (split-TF32 tensor-core GEMM, gelu, Adam); nothing here changes the
 // converged roots: the plain Davidson judges the result.
 #include <algorithm>
 #include <cmath>
@@ -23,6 +23,7 @@
 
 #include "kernels.h"
 #include "mlp.h"
+#include "tc_gemm.h"
 
 namespace xs {
 
@@ -353,8 +354,49 @@ void Mlp::get(cudaStream_t s, float* host) const {
 }
 
 // activations: per layer Z (pre-activation) and H (output); H[-1] = input
+namespace {
+
+// D (M x N, row stride ldd) = A B^T on the tensor cores: A is M x K and B is
+// N x K, each row-major with row stride ld, or given as its transpose (K x M,
+// K x N) when ta / tb.  Both are split into TF32 pairs (hi + lo, the K padding
+// zero; the bfloat16-rounded weights have lo = 0) and multiplied as
+// hi*hi + hi*lo + lo*hi with float32 accumulation.
+void tc_mm(cudaStream_t s, MlpOperands& w, int M, int N, int K, const float* A, int lda, bool ta, const float* B,
+           int ldb, bool tb, float* D, int ldd) {
+  if (!w.err.get()) {
+    w.err.alloc(1);
+    XS_CUDA(cudaMemsetAsync(w.err.get(), 0, sizeof(int), s));
+  }
+  const int Kp = pad32(K);
+  w.ah.ensure((size_t)M * Kp);
+  w.al.ensure((size_t)M * Kp);
+  w.bh.ensure((size_t)N * Kp);
+  w.bl.ensure((size_t)N * Kp);
+  split_pad<float>(s, M, K, Kp, A, lda, 0, 0, 1, ta, w.ah.get(), w.al.get());
+  split_pad<float>(s, N, K, Kp, B, ldb, 0, 0, 1, tb, w.bh.get(), w.bl.get());
+  const TcOperand oa{w.ah.get(), w.al.get(), Kp, 0, false}, ob{w.bh.get(), w.bl.get(), Kp, 0, false};
+  TcEpilogue e;
+  e.mode = 0;
+  e.D = D;
+  e.ld = ldd;
+  tc_gemm(s, oa, ob, M, N, Kp, 1, e, w.err.get());
+}
+
+}  // namespace
+
+void Mlp::check(cudaStream_t s, MlpOperands& w) {
+  if (!w.err.get()) return;
+  int h = 0;
+  XS_CUDA(cudaMemcpyAsync(&h, w.err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  XS_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    XS_CUDA(cudaMemsetAsync(w.err.get(), 0, sizeof(int), s));
+    throw Error(XS_ETIMEOUT, "network product: a bounded device wait timed out (code " + std::to_string(h) + ")");
+  }
+}
+
 void Mlp::forward(cudaStream_t s, int rows, const float* X, std::vector<DevBuf<float>>& Z,
-                  std::vector<DevBuf<float>>& H) const {
+                  std::vector<DevBuf<float>>& H, MlpOperands& mo) const {
   Z.resize(kMlpLayers);
   H.resize(kMlpLayers);
   const float* in = X;
@@ -366,7 +408,7 @@ void Mlp::forward(cudaStream_t s, int rows, const float* X, std::vector<DevBuf<f
     const float* W = wq.get() + off;
     const float* b = wq.get() + off + fout * fin;
     // Z = in W^T  (rows x fout)
-    gemm<float>(s, false, true, rows, fout, fin, 1.0f, in, fin, 0, W, fin, 0, 0.0f, Z[l].get(), fout, 0, 1);
+    tc_mm(s, mo, rows, fout, fin, in, fin, false, W, fin, false, Z[l].get(), fout);
     bias_act_kernel<<<grid1((long long)rows * fout, 256), 256, 0, s>>>(rows, fout, Z[l].get(), b, H[l].get(),
                                                                       l < kMlpLayers - 1 ? 1 : 0);
     XS_CHECK_LAUNCH();
@@ -376,9 +418,9 @@ void Mlp::forward(cudaStream_t s, int rows, const float* X, std::vector<DevBuf<f
 }
 
 float Mlp::gradient(cudaStream_t s, int rows, const float* X, const float* T, const float* colw,
-                   DevBuf<float>& scratch) {
+                   DevBuf<float>& scratch, MlpOperands& mo) {
   std::vector<DevBuf<float>> Z, H;
-  forward(s, rows, X, Z, H);
+  forward(s, rows, X, Z, H, mo);
   const int nout = sizes[kMlpLayers];
   scratch.ensure((size_t)rows * kMlpHidden * 2 + 8);
   float* loss = scratch.get();
@@ -399,24 +441,25 @@ float Mlp::gradient(cudaStream_t s, int rows, const float* X, const float* T, co
     }
     const float* hin = (l == 0) ? X : H[l - 1].get();
     // dW = G^T hin (fout x fin), db = column sums of G
-    gemm<float>(s, true, false, fout, fin, rows, 1.0f, G, fout, 0, hin, fin, 0, 0.0f, g.get() + off[l], fin, 0, 1);
+    tc_mm(s, mo, fout, fin, rows, G, fout, true, hin, fin, true, g.get() + off[l], fin);
     colsum_kernel<<<grid1(fout, 128), 128, 0, s>>>(rows, fout, G, g.get() + off[l] + fout * fin);
     XS_CHECK_LAUNCH();
     if (l > 0) {
       // G_prev = G W  (rows x fin), with the bfloat16 weights of the forward pass
-      gemm<float>(s, false, false, rows, fin, fout, 1.0f, G, fout, 0, wq.get() + off[l], fin, 0, 0.0f, G2, fin, 0, 1);
+      tc_mm(s, mo, rows, fin, fout, G, fout, false, wq.get() + off[l], fin, true, G2, fin);
       std::swap(G, G2);
     }
   }
   float hl = 0.0f;
   XS_CUDA(cudaMemcpyAsync(&hl, loss, sizeof(float), cudaMemcpyDeviceToHost, s));
   XS_CUDA(cudaStreamSynchronize(s));
+  check(s, mo);
   return hl;
 }
 
 float Mlp::train_step(cudaStream_t s, int rows, const float* X, const float* T, const float* colw, float lr,
-                      DevBuf<float>& scratch) {
-  const float l = gradient(s, rows, X, T, colw, scratch);
+                      DevBuf<float>& scratch, MlpOperands& mo) {
+  const float l = gradient(s, rows, X, T, colw, scratch, mo);
   ++step;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.0f - std::pow(b1, static_cast<float>(step));

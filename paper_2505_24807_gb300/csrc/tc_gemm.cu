@@ -396,6 +396,8 @@ void split_pad(cudaStream_t s, int rows, int cols, int ld_dst, const S* src, int
                                            lo);
   XS_CHECK_LAUNCH();
 }
+template void split_pad<float>(cudaStream_t, int, int, int, const float*, int, long long, long long, int, bool,
+                               float*, float*);
 template void split_pad<double>(cudaStream_t, int, int, int, const double*, int, long long, long long, int, bool,
                                 float*, float*);
 
